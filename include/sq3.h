@@ -1,0 +1,185 @@
+/*
+ * sq3.h -- C ABI of the GB300 (sm_103a) SQ3 hot path.
+ *
+ * SQ3 is the real-space density-kernel method for Kohn-Sham DFT at high
+ * temperature of arXiv 2112.08639.  One fixed-potential iteration (Sec. 4 of
+ * the paper) is:
+ *
+ *   X  <- p_m(H) X                 Chebyshev filter      sq3_cheb_filter
+ *   X  <- X R^{-1}, X^T X = R^T R  orthonormalisation    sq3_orthonormalise
+ *   Hs  = X^T H X                  projection            sq3_project
+ *   Ds  = g(Hs) ~ sum'_j c_j T_j(Hhat), mu, E_band, E_ent
+ *                                  density kernel        sq3_kernel_from_hs
+ *   rho = 2 sum_i (X Ds)_i X_i / dV                       sq3_density
+ *
+ * with H = -1/2 Lap_12 + V + sum_p gamma_p c_p c_p^T on a periodic grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid index k = i + nx*j + nx*ny*l (x fastest).  N = nx*ny*nz.
+ * - A block X of Ns vectors is N x Ns column-major: vector i occupies
+ *   X[i*N .. i*N+N-1].  Vectors are Euclidean-normalised (u = psi sqrt(dV)).
+ * - Element type of X follows the precision argument: SQ3_FP64 -> double,
+ *   SQ3_MIXED -> float.  Ns x Ns matrices (Hs, Ds) and rho are always double.
+ * - Unless stated otherwise, array pointers are DEVICE pointers to
+ *   caller-owned memory on the context's device; the library never frees or
+ *   retains them after the call returns.
+ * - Work is ordered on the context's CUDA stream.  Every entry point returns
+ *   only after that stream has reached the end of its work, so outputs are
+ *   ready and device-side errors have been checked.
+ * - The context owns its workspace (device memory sized on first use and
+ *   grown when a larger Ns or N is seen); it is released by sq3_destroy.
+ * - Return value: SQ3_OK (0) or a negative SQ3_E* code.  No C++ exception
+ *   crosses the ABI and no kernel traps; device-side failures are reported
+ *   through these codes.  sq3_status_string() names a code.
+ */
+#ifndef SQ3_H
+#define SQ3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sq3_ctx sq3_ctx;
+
+typedef enum {
+  SQ3_FP64 = 0,   /* X double; every step in FP64                           */
+  SQ3_MIXED = 1   /* X float; stencil FP32; Gram/projection/recurrence/XD on
+                     tcgen05 BF16 split products with FP32 accumulation;
+                     Cholesky, bisection, energies and reductions in FP64    */
+} sq3_prec;
+
+enum {
+  SQ3_OK = 0,
+  SQ3_EINVAL = -1,      /* bad argument (null pointer, size, precision)      */
+  SQ3_ENOTSETUP = -2,   /* grid or potential not set                          */
+  SQ3_ECUDA = -3,       /* a CUDA runtime/driver call failed                  */
+  SQ3_ENOTPD = -4,      /* Cholesky pivot <= 0: X^T X not positive definite   */
+  SQ3_ENOCONV = -5,     /* bisection or spectral-bound check failed           */
+  SQ3_ETIMEOUT = -6,    /* a bounded device-side wait ran out                 */
+  SQ3_ENONFINITE = -7,  /* NaN/Inf detected in an output                      */
+  SQ3_ENOMEM = -8       /* workspace allocation failed                        */
+};
+
+/* Create a context on CUDA device `device` whose work is ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the context.  Errors: SQ3_EINVAL, SQ3_ECUDA. */
+int sq3_create(sq3_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and its workspace.  NULL is accepted. */
+void sq3_destroy(sq3_ctx* ctx);
+
+/* Periodic orthorhombic grid nx x ny x nz over a cell Lx x Ly x Lz (bohr)
+ * with a central finite-difference Laplacian of order fd_order (even, 2..12;
+ * the paper uses 12, Sec. 5).  Weights: Fornberg closed form
+ * w_p = 2(-1)^(p+1)(n!)^2/(p^2 (n-p)!(n+p)!), w_0 = -2 sum 1/p^2, n = order/2.
+ * Resets the potential and projectors.  Errors: SQ3_EINVAL. */
+int sq3_setup_grid(sq3_ctx* ctx, int nx, int ny, int nz,
+                   double Lx, double Ly, double Lz, int fd_order);
+
+/* Effective local potential V_eff = V_xc + phi (Sec. 2, Eq. (KSeqn)) on the
+ * grid: device array of N doubles.  Copied into the context.
+ * Errors: SQ3_ENOTSETUP (no grid), SQ3_EINVAL. */
+int sq3_set_potential(sq3_ctx* ctx, const double* V);
+
+/* Kleinman-Bylander projectors (Sec. 2, Eq. (nonlocaloperator)) as a CSR
+ * table in HOST memory: projector p covers grid indices
+ * idx[ptr[p] .. ptr[p+1]-1] with continuum values val (chi_p at those points,
+ * NOT multiplied by sqrt(dV)) and energy gamma[p] (Ha).  The library forms
+ * c_p = chi_p sqrt(dV) and applies V_nl = sum_p gamma_p c_p c_p^T.
+ * Projectors that share an index list (the lm components of one atom) are
+ * grouped internally.  n_proj = 0 removes the projectors.  Copied into the
+ * context.  Errors: SQ3_ENOTSETUP, SQ3_EINVAL (index out of range, ptr not
+ * monotone). */
+int sq3_set_projectors(sq3_ctx* ctx, int n_proj, const int* ptr,
+                       const int* idx, const double* val, const double* gamma);
+
+/* Y = H X for a block of Ns vectors (Sec. 2, Eq. (KSeqn)); X and Y are N x Ns
+ * column-major of the precision's element type and must not overlap.
+ * Errors: SQ3_ENOTSETUP, SQ3_EINVAL. */
+int sq3_hamiltonian_apply(sq3_ctx* ctx, const void* X, void* Y, int Ns,
+                          sq3_prec prec);
+
+/* Chebyshev filter X <- p_m(H) X in place (Sec. 4, first paragraph: the
+ * CheFSI filter of Zhou et al. 2006), p_m(t) = T_m((t-c)/e)/T_m((a0-c)/e)
+ * with c = (b+a)/2, e = (b-a)/2, evaluated by the scaled three-term
+ * recurrence.  a: lower end of the damped interval (cutoff), b: upper bound
+ * of the spectrum of H, a0: lower-bound estimate (p_m(a0) = 1).
+ * Requires a0 < a < b and degree >= 1.  Errors: SQ3_ENOTSETUP, SQ3_EINVAL. */
+int sq3_cheb_filter(sq3_ctx* ctx, void* X, int Ns, int degree,
+                    double a, double b, double a0, sq3_prec prec);
+
+/* Orthonormalise X in place by Cholesky QR: S = X^T X = R^T R (R upper
+ * triangular, FP64 Cholesky on the device), X <- X R^{-1} (Sec. 4: "followed
+ * by orthonormalization"; the method is this library's reading).  In
+ * SQ3_MIXED the step is applied twice (CholQR2).  Errors: SQ3_ENOTPD. */
+int sq3_orthonormalise(sq3_ctx* ctx, void* X, int Ns, sq3_prec prec);
+
+/* Hs = X^T H X, symmetrised, written to the device Ns x Ns double array Hs
+ * (Sec. 3, Eq. (DsHsRelation): H_ij = <phi_i|H|phi_j>). */
+int sq3_project(sq3_ctx* ctx, const void* X, int Ns, sq3_prec prec,
+                double* Hs);
+
+/* Density kernel from a subspace Hamiltonian (Sec. 4):
+ *   Hhat = (Hs - chi I)/xi; T_0 = I, T_1 = Hhat, T_{j+1} = 2 Hhat T_j - T_{j-1}
+ *   (Eq. (ThreeTermRecurrenceRelation)); moments m_j = tr T_j;
+ *   c_j(mu), d_j, e_j by Chebyshev-Gauss quadrature of Eq. (ChebyshevCoeff)
+ *   with M = max(1024, 8(npl+1)) nodes; mu by bisection on
+ *   2 sum'_j c_j(mu) m_j = Ne (Eq. (FermiLevelCalc));
+ *   Ds = sum'_j c_j T_j (Eq. (ChebyshevExpansion));
+ *   E_band = 2 sum'_j d_j m_j; E_ent = 2 sigma sum'_j e_j m_j.
+ * Hs: device Ns x Ns double (symmetric).  kT: sigma in Ha.  bounds_in: HOST
+ * pointer to {chi, xi} to use as given, or NULL to estimate them with a
+ * 40-step Lanczos on Hs (extremal Ritz values widened by their residual
+ * bounds, then xi *= 1.001).  D: device Ns x Ns double output (may be NULL).
+ * out: HOST array of 6 doubles receiving {mu, E_band, E_ent, chi, xi,
+ * 2 tr Ds}.  Requires npl >= 1 and 0 < Ne < 2 Ns.
+ * Errors: SQ3_EINVAL, SQ3_ENOCONV (bisection did not bracket a root, or the
+ * moments exceed the bound |m_j| <= Ns by more than 1e-6 relative, which
+ * means the spectrum left [-1, 1]). */
+int sq3_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+                       double kT, double Ne, const double* bounds_in,
+                       double* D, double* out);
+
+/* sq3_project followed by sq3_kernel_from_hs: the density-kernel step of one
+ * SQ3 iteration.  Hs_out (device, may be NULL) receives Hs. */
+int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
+                       double kT, double Ne, sq3_prec prec,
+                       const double* bounds_in, double* Hs_out, double* D,
+                       double* out);
+
+/* rho_k = (2/dV) sum_i X_ki (X Ds)_ki (Sec. 3, Eq. (phi_tilde) and
+ * Eq. (density:NewForm)); X Ds is formed tile by tile and never stored.
+ * D: device Ns x Ns double; rho: device N doubles (overwritten). */
+int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
+                sq3_prec prec, double* rho);
+
+/* Per-stage timing (tracing).  When enabled, the library records a CUDA
+ * event pair on the context's stream around the launches of each stage of
+ * the path; sq3_profile_read synchronises the stream, writes for each stage
+ * s < n_stages the summed device time ms[s] (milliseconds) and the number of
+ * kernel launches launches[s], clears the records, and returns the number of
+ * stages the library knows (SQ3_N_STAGES).  Stage order:
+ *   0 stencil/filter step, 1 nonlocal projection, 2 Gram X^T X,
+ *   3 Cholesky, 4 triangular inverse, 5 X R^{-1}, 6 X^T (H X),
+ *   7 Lanczos, 8 Chebyshev recurrence GEMM, 9 Fermi level/coefficients,
+ *   10 Ds accumulation, 11 density X Ds row-dot, 12 BF16 split,
+ *   13 device copies.
+ * Host pointers; either may be NULL. */
+#define SQ3_N_STAGES 14
+int sq3_profile_enable(sq3_ctx* ctx, int enable);
+int sq3_profile_read(sq3_ctx* ctx, double* ms, long long* launches,
+                     int n_stages);
+
+/* Human-readable name of a status code (static string). */
+const char* sq3_status_string(int status);
+
+/* Library build string: version and target architecture (static string). */
+const char* sq3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQ3_H */

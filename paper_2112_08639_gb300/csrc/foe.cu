@@ -1,0 +1,262 @@
+// Chebyshev Fermi-operator expansion of the density kernel (Sec. 4).
+//
+//   Hhat = (Hs - chi I)/xi                              Eq. (ChebyshevExpansion)
+//   T_0 = I, T_1 = Hhat, T_{j+1} = 2 Hhat T_j - T_{j-1}  Eq. (ThreeTermRecurrenceRelation)
+//   m_j = sum_n e_n^T t^j_n = tr T_j                     Eq. (FermiLevelCalc)
+//   c_j(mu) = (2/pi) int g(xi l + chi) T_j(l) / sqrt(1 - l^2) dl
+//                                                        Eq. (ChebyshevCoeff)
+//   mu: 2 sum'_j c_j(mu) m_j = Ne ;  Ds = sum'_j c_j T_j
+//   E_band = 2 sum'_j d_j m_j ;  E_ent = 2 sigma sum'_j e_j m_j
+//
+// The integral is evaluated by Chebyshev-Gauss quadrature on M nodes
+// theta_k = (k + 1/2) pi / M, M = max(1024, 8 (npl + 1)).  With that rule the
+// electron count is a double sum over j and k; this implementation sums over
+// j first, w_k = sum'_j m_j T_j(cos theta_k) (independent of mu), so every
+// bisection step costs M Fermi evaluations and one block reduction, all on
+// the GPU in FP64.  All T_j are kept (they fit in HBM for the sizes used), so
+// Ds is a weighted sum of stored matrices instead of a second recurrence.
+#include <math.h>
+
+#include "sq3_internal.cuh"
+
+namespace sq3 {
+
+__global__ void hhat_kernel(const double* __restrict__ Hs, double* T0,
+                            double* T1, int n, const double* bounds,
+                            double* moments, int npl) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long tot = (long long)n * n;
+  if (e == 0) moments[0] = (double)n;
+  if (e >= tot) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const double chi = bounds[0], xi = bounds[1];
+  const double h = (Hs[e] - (i == j ? chi : 0.0)) / xi;
+  T1[e] = h;
+  T0[e] = (i == j) ? 1.0 : 0.0;
+}
+
+__global__ void trace_kernel(const double* __restrict__ A, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += A[i + (long long)i * n];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+__device__ inline double fermi_dev(double eps, double mu, double sigma) {
+  // 1 / (1 + exp(x)), x = (eps - mu)/sigma, without overflow
+  const double x = (eps - mu) / sigma;
+  if (x > 0) {
+    const double t = exp(-x);
+    return t / (1.0 + t);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+// g ln g + (1-g) ln(1-g), even in x; evaluated at t = -|x|.
+__device__ inline double entropy_dev(double eps, double mu, double sigma) {
+  const double t = -fabs((eps - mu) / sigma);
+  const double et = exp(t);
+  return -log1p(et) + t * et / (1.0 + et);
+}
+
+__device__ double bsum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  return s;
+}
+
+// One CTA: quadrature weights, bisection for mu, coefficients, energies.
+// out[0..5] = mu, E_band, E_ent, chi, xi, 2 sum' c_j m_j ; coef[0..npl] = c_j
+__global__ void __launch_bounds__(1024)
+fermi_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
+             double Ne, int n, const double* bounds, double* coef, double* out,
+             int* status) {
+  extern __shared__ double smem[];
+  double* wq = smem;            // M   : w_k = sum'_j m_j T_j(x_k)
+  double* xk = smem + M;        // M   : nodes cos(theta_k)
+  double* f = smem + 2 * M;     // 3M  : g, eps*g, entropy at nodes
+  __shared__ double sh[32];
+  const double chi = bounds[0], xi = bounds[1];
+  const double PI = 3.14159265358979323846;
+
+  // moment sanity: |tr T_j| <= n unless the spectrum left [-1, 1]
+  for (int j = threadIdx.x; j <= npl; j += blockDim.x) {
+    const double mj = moments[j];
+    if (!isfinite(mj)) atomicCAS(status, 0, DEV_NONFINITE);
+    else if (fabs(mj) > n * (1.0 + 1e-6)) atomicCAS(status, 0, DEV_NOCONV);
+  }
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double x = cos((k + 0.5) * PI / M);
+    xk[k] = x;
+    double tp = 1.0, t = x;                  // T_0, T_1 at x
+    double acc = 0.5 * moments[0] + (npl >= 1 ? moments[1] * x : 0.0);
+    for (int j = 2; j <= npl; ++j) {
+      const double tn = 2.0 * x * t - tp;
+      tp = t; t = tn;
+      acc += moments[j] * t;
+    }
+    wq[k] = acc;
+  }
+  __syncthreads();
+
+  auto count = [&](double mu) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x)
+      s += fermi_dev(xi * xk[k] + chi, mu, sigma) * wq[k];
+    return 2.0 * (2.0 / M) * bsum(s, sh);
+  };
+
+  double lo = chi - xi - 40.0 * sigma, hi = chi + xi + 40.0 * sigma;
+  const double clo = count(lo), chi_ = count(hi);
+  if (!(clo < Ne && chi_ > Ne)) {
+    if (threadIdx.x == 0) atomicCAS(status, 0, DEV_NOCONV);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    const double cm = count(mid);
+    if (cm < Ne) lo = mid; else hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double eps = xi * xk[k] + chi;
+    const double g = fermi_dev(eps, mu, sigma);
+    f[k] = g;
+    f[M + k] = eps * g;
+    f[2 * M + k] = entropy_dev(eps, mu, sigma);
+  }
+  __syncthreads();
+  // c_j, d_j, e_j: (2/M) sum_k f(x_k) cos(j theta_k); accumulate the primed
+  // moment sums of the three series at the same time.
+  double sc = 0.0, sd = 0.0, se = 0.0;
+  for (int j = threadIdx.x; j <= npl; j += blockDim.x) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < M; ++k) {
+      const double cj = cos(j * ((k + 0.5) * PI / M));
+      a += f[k] * cj;
+      b += f[M + k] * cj;
+      c += f[2 * M + k] * cj;
+    }
+    a *= 2.0 / M; b *= 2.0 / M; c *= 2.0 / M;
+    coef[j] = a;
+    const double wgt = (j == 0) ? 0.5 : 1.0;
+    sc += wgt * a * moments[j];
+    sd += wgt * b * moments[j];
+    se += wgt * c * moments[j];
+  }
+  sc = bsum(sc, sh);
+  sd = bsum(sd, sh);
+  se = bsum(se, sh);
+  if (threadIdx.x == 0) {
+    out[0] = mu;
+    out[1] = 2.0 * sd;
+    out[2] = 2.0 * sigma * se;
+    out[3] = chi;
+    out[4] = xi;
+    out[5] = 2.0 * sc;
+    if (!isfinite(mu) || !isfinite(sd) || !isfinite(se))
+      atomicCAS(status, 0, DEV_NONFINITE);
+  }
+}
+
+// Ds = c_0/2 I + sum_{j>=1} c_j T_j over the stored T_j.
+__global__ void accumulate_d_kernel(const double* __restrict__ T, long long nn,
+                                    int n, int npl,
+                                    const double* __restrict__ coef,
+                                    double* D) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  double s = (i == j) ? 0.5 * coef[0] : 0.0;
+  for (int t = 1; t <= npl; ++t) s += coef[t] * T[(long long)t * nn + e];
+  D[e] = s;
+}
+
+int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
+                               int npl, double sigma, double Ne,
+                               const double* bounds_in, double* D,
+                               double* out_host) {
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)Ns * Ns;
+  // workspace: T_0..T_npl, then Lanczos work
+  size_t need_T = (size_t)(npl + 1) * nn * sizeof(double);
+  int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
+  if (rc) return rc;
+  const int lsteps = Ns < 40 ? Ns : 40;
+  size_t need_m = ((size_t)(lsteps + 2) * Ns + 2 * lsteps + 8) * sizeof(double);
+  rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes, need_m);
+  if (rc) return rc;
+  if (npl > SQ3_MAX_NPL) return SQ3_EINVAL;
+  double* bounds = ctx->dev_scal;                  // chi, xi
+  double* outd = ctx->dev_scal + 8;                // 6 outputs
+  double* mom = ctx->dev_scal + 64;                // moments m_0..m_npl
+  double* coef = ctx->dev_scal + 64 + SQ3_MAX_NPL + 1;  // c_0..c_npl
+  rc = cuda_err(cudaMemsetAsync(mom, 0, (size_t)(npl + 1) * sizeof(double), st));
+  if (rc) return rc;
+
+  if (bounds_in) {
+    rc = cuda_err(cudaMemcpyAsync(bounds, bounds_in, 2 * sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+  } else {
+    Prof p(ctx, ST_LANCZOS, 2 * lsteps + 2);
+    lanczos_bounds_f64(ctx, Hs, Ns, lsteps, bounds, ctx->wsMat, st);
+  }
+  double* T = ctx->wsT;
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    hhat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
+        Hs, T, T + nn, Ns, bounds, mom, npl);
+    trace_kernel<<<1, 1024, 0, st>>>(T + nn, Ns, mom + 1);
+  }
+  {
+  Prof prec(ctx, ST_CHEB_GEMM, npl - 1);
+  for (int j = 1; j < npl; ++j) {
+    GemmArgs g{};
+    g.M = Ns; g.N = Ns; g.K = Ns;
+    g.A = T + nn; g.lda = Ns; g.a_kcontig = false;             // Hhat
+    g.B = T + (long long)j * nn; g.ldb = Ns; g.b_kcontig = true;  // T_j
+    g.C = T + (long long)(j + 1) * nn; g.ldc = Ns;
+    g.P = T + (long long)(j - 1) * nn; g.ldp = Ns;
+    g.trace = mom + j + 1;
+    g.alpha = 1.0; g.splits = 1;
+    gemm_f64(g, EPI_CHEB, st);
+  }
+  }
+  const int M = (8 * (npl + 1) > 1024) ? 8 * (npl + 1) : 1024;
+  size_t smem = (size_t)5 * M * sizeof(double);
+  cudaFuncSetAttribute(fermi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  {
+    Prof p(ctx, ST_FERMI);
+    fermi_kernel<<<1, 1024, smem, st>>>(mom, npl, M, sigma, Ne, Ns, bounds,
+                                        coef, outd, ctx->dev_status);
+  }
+  Prof pd(ctx, ST_D_ACCUM, D != nullptr ? 1 : 0);
+  if (D != nullptr)
+    accumulate_d_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
+        T, nn, Ns, npl, coef, D);
+  rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  rc = cuda_err(cudaMemcpyAsync(ctx->host_scal, outd, 6 * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+  if (rc) return rc;
+  rc = check_device_status(ctx);
+  if (rc) return rc;
+  for (int i = 0; i < 6; ++i) out_host[i] = ctx->host_scal[i];
+  return SQ3_OK;
+}
+
+}  // namespace sq3

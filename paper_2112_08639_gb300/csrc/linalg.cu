@@ -1,0 +1,337 @@
+// Dense FP64 linear algebra on the device for the orthonormalisation and
+// spectral-bound steps.
+//
+// * Blocked right-looking Cholesky S = L L^T (64-wide panels: one-CTA panel
+//   factorisation, row-parallel triangular solve for the panel below, GEMM
+//   update of the trailing matrix).  Used for Cholesky QR, the
+//   orthonormalisation that follows the Chebyshev filter (Sec. 4).
+// * R^{-1} = L^{-T} by column-parallel forward substitution.
+// * Lanczos extremal eigenvalue estimates of Hs for chi and xi of
+//   Eq. (ChebyshevExpansion) (the paper takes them from lambda_1 and
+//   lambda_Ns of Hs without saying how they are obtained).
+#include <math.h>
+
+#include "sq3_internal.cuh"
+
+namespace sq3 {
+
+constexpr int CH_NB = 64;
+
+__device__ inline void set_status(int* st, int code) {
+  atomicCAS(st, 0, code);
+}
+
+// Factor the kb x kb diagonal block at (k0, k0) of the column-major n x n S.
+__global__ void __launch_bounds__(256)
+potrf_diag_kernel(double* S, int n, int k0, int kb, int* status) {
+  __shared__ double A[CH_NB][CH_NB + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e % kb, j = e / kb;
+    A[i][j] = S[(k0 + i) + (long long)(k0 + j) * n];
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        set_status(status, DEV_NOTPD);
+        d = 1.0;
+      }
+      A[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double djj = A[j][j];
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][j] /= djj;
+    __syncthreads();
+    const int m = kb - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = j + 1 + e % m, l = j + 1 + e / m;
+      if (l <= i) A[i][l] -= A[i][j] * A[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e % kb, j = e / kb;
+    if (i >= j) S[(k0 + i) + (long long)(k0 + j) * n] = A[i][j];
+  }
+}
+
+// L21 = S21 L11^{-T}: each thread solves one row of the panel below the
+// diagonal block by forward substitution.
+__global__ void __launch_bounds__(128)
+trsm_panel_kernel(double* S, int n, int k0, int kb) {
+  __shared__ double L[CH_NB][CH_NB + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    int i = e % kb, j = e / kb;
+    L[i][j] = (i >= j) ? S[(k0 + i) + (long long)(k0 + j) * n] : 0.0;
+  }
+  __syncthreads();
+  const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = i < n;
+  double x[CH_NB];
+#pragma unroll
+  for (int c = 0; c < CH_NB; ++c)
+    x[c] = (ok && c < kb) ? S[i + (long long)(k0 + c) * n] : 0.0;
+#pragma unroll
+  for (int c = 0; c < CH_NB; ++c) {
+    if (c < kb) {
+      double s = x[c];
+#pragma unroll
+      for (int j = 0; j < c; ++j) s -= x[j] * L[c][j];
+      x[c] = s / L[c][c];
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int c = 0; c < CH_NB; ++c)
+      if (c < kb) S[i + (long long)(k0 + c) * n] = x[c];
+  }
+}
+
+int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, cudaStream_t st) {
+  for (int k0 = 0; k0 < n; k0 += CH_NB) {
+    const int kb = (n - k0 < CH_NB) ? n - k0 : CH_NB;
+    potrf_diag_kernel<<<1, 256, 0, st>>>(S, n, k0, kb, ctx->dev_status);
+    const int m2 = n - k0 - kb;
+    if (m2 <= 0) continue;
+    trsm_panel_kernel<<<(m2 + 127) / 128, 128, 0, st>>>(S, n, k0, kb);
+    GemmArgs g{};
+    g.M = m2; g.N = m2; g.K = kb;
+    g.A = S + (k0 + kb) + (long long)k0 * n; g.lda = n; g.a_kcontig = false;
+    g.B = S + (k0 + kb) + (long long)k0 * n; g.ldb = n; g.b_kcontig = false;
+    g.C = S + (k0 + kb) + (long long)(k0 + kb) * n; g.ldc = n;
+    g.alpha = -1.0; g.beta = 1.0; g.splits = 1;
+    gemm_f64(g, EPI_STORE, st);
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+// Column j of W = L^{-1} by forward substitution, written as row j of
+// Rinv = W^T (column-major, upper triangular).
+__global__ void __launch_bounds__(256)
+tri_inv_kernel(const double* __restrict__ L, double* Rinv, int n) {
+  extern __shared__ double r[];
+  const int j = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int i = j; i < n; ++i) {
+    const double wi = r[i] / L[i + (long long)i * n];
+    __syncthreads();
+    if (threadIdx.x == 0) r[i] = wi;
+    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x)
+      r[k] -= L[k + (long long)i * n] * wi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    Rinv[j + (long long)i * n] = (i >= j) ? r[i] : 0.0;
+}
+
+void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
+                               cudaStream_t st) {
+  size_t smem = (size_t)n * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(tri_inv_kernel,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  tri_inv_kernel<<<n, 256, smem, st>>>(L, Rinv, n);
+}
+
+__global__ void symmetrize_kernel(double* A, int n) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e % n), j = (int)(e / n);
+  if (i < j) {
+    double a = A[i + (long long)j * n], b = A[j + (long long)i * n];
+    double s = 0.5 * (a + b);
+    A[i + (long long)j * n] = s;
+    A[j + (long long)i * n] = s;
+  }
+}
+
+void symmetrize_f64(double* A, int n, cudaStream_t st) {
+  long long tot = (long long)n * n;
+  symmetrize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, n);
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos with full reorthogonalisation on the symmetric Hs.
+// work layout: V[(steps+1) * n] | w[n] | alpha[steps] | beta[steps] | k[1]
+// ---------------------------------------------------------------------------
+__device__ inline double hash_unit(unsigned i) {
+  unsigned h = i * 2654435761u + 0x9e3779b9u;
+  h ^= h >> 16; h *= 0x85ebca6bu; h ^= h >> 13; h *= 0xc2b2ae35u; h ^= h >> 16;
+  return (double)h / 4294967296.0 - 0.5;
+}
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) s += sh[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(1024)
+lanczos_init_kernel(double* V, int n, double* kcount) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = hash_unit((unsigned)i) + 0.25;
+    V[i] = v;
+    s += v * v;
+  }
+  s = block_sum(s, sh);
+  const double inv = 1.0 / sqrt(s);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] *= inv;
+  if (threadIdx.x == 0) kcount[0] = 0.0;
+}
+
+// w = Hs v: one warp per output row (Hs symmetric, so row i = column i).
+__global__ void __launch_bounds__(256)
+symv_kernel(const double* __restrict__ Hs, const double* __restrict__ v,
+            double* w, int n, const double* kcount, int j) {
+  if (kcount[0] < j) return;  // Lanczos already terminated
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* col = Hs + (long long)warp * n;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s += col[k] * v[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) w[warp] = s;
+}
+
+__global__ void __launch_bounds__(1024)
+lanczos_update_kernel(double* V, double* w, double* alpha, double* beta,
+                      double* kcount, int n, int j) {
+  __shared__ double sh[32];
+  if (kcount[0] < j) return;
+  const double* vj = V + (long long)j * n;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += w[i] * vj[i];
+  a = block_sum(a, sh);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double t = w[i] - a * vj[i];
+    if (j > 0) t -= beta[j - 1] * V[(long long)(j - 1) * n + i];
+    w[i] = t;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int t = 0; t <= j; ++t) {
+      const double* vt = V + (long long)t * n;
+      double h = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) h += vt[i] * w[i];
+      h = block_sum(h, sh);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] -= h * vt[i];
+      __syncthreads();
+    }
+  }
+  double b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) b += w[i] * w[i];
+  b = sqrt(block_sum(b, sh));
+  if (threadIdx.x == 0) {
+    alpha[j] = a;
+    beta[j] = b;
+    kcount[0] = (double)(j + 1);
+  }
+  double scale = fabs(a) + b;
+  if (b <= 1e-12 * (scale > 0 ? scale : 1.0) || j + 1 >= n) {
+    if (threadIdx.x == 0) kcount[0] = -(double)(j + 1);  // terminated
+    return;
+  }
+  double* vn = V + (long long)(j + 1) * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vn[i] = w[i] / b;
+}
+
+// Number of eigenvalues of the k x k tridiagonal (alpha, beta) below x.
+__device__ int sturm_count(const double* al, const double* be, int k, double x) {
+  int cnt = 0;
+  double d = al[0] - x;
+  if (d < 0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    if (d == 0.0) d = 1e-300;
+    d = al[i] - x - be[i - 1] * be[i - 1] / d;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// |last component| of the normalised eigenvector of T for eigenvalue th.
+__device__ double last_component(const double* al, const double* be, int k,
+                                 double th) {
+  if (k == 1) return 1.0;
+  double sp = 0.0, s = 1.0, nrm2 = 1.0;
+  for (int i = 0; i < k - 1; ++i) {
+    double bi = be[i] != 0.0 ? be[i] : 1e-300;
+    double sn = ((th - al[i]) * s - (i > 0 ? be[i - 1] * sp : 0.0)) / bi;
+    sp = s; s = sn;
+    nrm2 += s * s;
+    if (nrm2 > 1e200) { sp *= 1e-100; s *= 1e-100; nrm2 *= 1e-200; }
+  }
+  double r = fabs(s) / sqrt(nrm2);
+  return r > 1.0 ? 1.0 : r;
+}
+
+__global__ void lanczos_finish_kernel(const double* alpha, const double* beta,
+                                      const double* kcount, double* bounds) {
+  if (threadIdx.x != 0) return;
+  const bool terminated = kcount[0] < 0;
+  const int k = (int)fabs(kcount[0]);
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < k - 1 ? fabs(beta[i]) : 0.0);
+    lo = fmin(lo, alpha[i] - r);
+    hi = fmax(hi, alpha[i] + r);
+  }
+  double tmin, tmax;
+  {
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + b);
+      if (mid <= a || mid >= b) break;
+      if (sturm_count(alpha, beta, k, mid) >= 1) b = mid; else a = mid;
+    }
+    tmin = 0.5 * (a + b);
+    a = lo; b = hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + b);
+      if (mid <= a || mid >= b) break;
+      if (sturm_count(alpha, beta, k, mid) >= k) b = mid; else a = mid;
+    }
+    tmax = 0.5 * (a + b);
+  }
+  double bk = terminated ? 0.0 : fabs(beta[k - 1]);
+  double rmin = bk * last_component(alpha, beta, k, tmin);
+  double rmax = bk * last_component(alpha, beta, k, tmax);
+  double l1 = tmin - rmin, l2 = tmax + rmax;
+  double chi = 0.5 * (l1 + l2);
+  double xi = 0.5 * (l2 - l1) * 1.001;
+  double floor_xi = 1e-6 * fmax(fabs(chi), 1.0);
+  if (!(xi > floor_xi)) xi = floor_xi;
+  bounds[0] = chi;
+  bounds[1] = xi;
+}
+
+void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
+                        double* d_bounds, double* work, cudaStream_t st) {
+  (void)ctx;
+  if (steps > n) steps = n;
+  double* V = work;
+  double* w = V + (long long)(steps + 1) * n;
+  double* alpha = w + n;
+  double* beta = alpha + steps;
+  double* kc = beta + steps;
+  lanczos_init_kernel<<<1, 1024, 0, st>>>(V, n, kc);
+  for (int j = 0; j < steps; ++j) {
+    symv_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(Hs, V + (long long)j * n,
+                                                       w, n, kc, j);
+    lanczos_update_kernel<<<1, 1024, 0, st>>>(V, w, alpha, beta, kc, n, j);
+  }
+  lanczos_finish_kernel<<<1, 32, 0, st>>>(alpha, beta, kc, d_bounds);
+}
+
+}  // namespace sq3

@@ -1,0 +1,600 @@
+// C ABI entry points of libsq3: context, set-up, and the host-side ordering
+// of the kernels of one SQ3 iteration (Sec. 4 of the paper).  Every step of
+// the computation runs in this library's CUDA kernels; the host code here
+// only validates arguments, sizes workspace and enqueues launches.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sq3_internal.cuh"
+
+namespace sq3 {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? SQ3_OK : SQ3_ECUDA; }
+
+int ensure(void** p, size_t* have, size_t need) {
+  if (need <= *have && *p != nullptr) return SQ3_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (need == 0) return SQ3_OK;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return SQ3_ENOMEM;
+  }
+  *have = need;
+  return SQ3_OK;
+}
+
+int check_device_status(sq3_ctx* ctx) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->dev_status, sizeof(int),
+                                  cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return SQ3_ECUDA;
+  if (h != DEV_OK) {
+    cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    switch (h) {
+      case DEV_NOTPD: return SQ3_ENOTPD;
+      case DEV_NOCONV: return SQ3_ENOCONV;
+      case DEV_NONFINITE: return SQ3_ENONFINITE;
+      case DEV_TIMEOUT: return SQ3_ETIMEOUT;
+      default: return SQ3_ECUDA;
+    }
+  }
+  return SQ3_OK;
+}
+
+Prof::Prof(sq3_ctx* c, int st, int n) : ctx(c), stage(st), launches(n) {
+  if (!ctx->prof) return;
+  auto get = [&]() {
+    cudaEvent_t e;
+    if (!ctx->prof_pool.empty()) { e = ctx->prof_pool.back(); ctx->prof_pool.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+  };
+  a = get();
+  b = get();
+  cudaEventRecord(a, ctx->stream);
+}
+
+Prof::~Prof() {
+  if (!a) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->prof_recs.push_back({stage, launches, a, b});
+}
+
+// Central second-derivative weights of order 2n (Fornberg closed form).
+static void fd_weights(int order, double* w) {
+  const int n = order / 2;
+  auto fact = [](int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; };
+  w[0] = 0.0;
+  for (int p = 1; p <= n; ++p) {
+    w[p] = 2.0 * ((p % 2) ? 1.0 : -1.0) * fact(n) * fact(n) /
+           ((double)p * p * fact(n - p) * fact(n + p));
+    w[0] -= 2.0 / ((double)p * p);
+  }
+}
+
+__global__ void to_float_kernel(const double* a, float* b, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+static void free_projectors(Projectors& P) {
+  void* ptrs[] = {P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
+                  P.ball_valoff, P.ball_val, P.ball_valf, P.gamma,
+                  P.pt_ptr, P.pt_proj, P.pt_val, P.pt_valf};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  P = Projectors{};
+}
+
+template <typename T>
+static int upload(T** dst, const T* src, size_t n) {
+  if (n == 0) { *dst = nullptr; return SQ3_OK; }
+  if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return SQ3_ENOMEM;
+  }
+  return cuda_err(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+static int elem_size(sq3_prec p) { return p == SQ3_FP64 ? 8 : 4; }
+
+// gC workspace for the nonlocal projection of one block.
+static int gc_buffer(sq3_ctx* ctx, int Ns, void** out) {
+  *out = nullptr;
+  if (ctx->proj.n_proj == 0) return SQ3_OK;
+  int rc = ensure((void**)&ctx->wsProj, &ctx->wsProj_bytes,
+                  (size_t)ctx->proj.n_proj * Ns * sizeof(double));
+  *out = ctx->wsProj;
+  return rc;
+}
+
+template <typename T>
+static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
+  void* gC;
+  int rc = gc_buffer(ctx, Ns, &gC);
+  if (rc) return rc;
+  if (ctx->proj.n_proj) {
+    Prof p(ctx, ST_NL_PROJECT);
+    launch_nl_project<T>(ctx, X, (T*)gC, Ns, ctx->stream);
+  }
+  {
+    Prof p(ctx, ST_STENCIL);
+    launch_cheb_step<T>(ctx, X, nullptr, Y, (const T*)gC, Ns, 1.0, 0.0, 0.0,
+                        ctx->stream);
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+// Scaled three-term recurrence of the Chebyshev filter (Zhou et al. 2006):
+// with x = (t - c)/e and rho_k = T_k((a0 - c)/e), Y_k = T_k(x) X / rho_k obeys
+// Y_1 = (s_1/e)(H - c) X and Y_{k+1} = (2 s_{k+1}/e)(H - c) Y_k
+// - s_k s_{k+1} Y_{k-1} with s_1 = e/(a0 - c), s_{k+1} = 1/(2/s_1 - s_k).
+template <typename T>
+static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
+                         double b, double a0) {
+  const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
+  int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
+  if (rc) return rc;
+  void* gC;
+  rc = gc_buffer(ctx, Ns, &gC);
+  if (rc) return rc;
+  T* W = (T*)ctx->wsX;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  const double tau = 2.0 / s1;
+  double s = s1;
+  T* cur = W;      // holds Y_1 after the first step
+  T* prev = X;     // holds Y_0
+  const bool nl = ctx->proj.n_proj > 0;
+  if (nl) {
+    Prof p(ctx, ST_NL_PROJECT);
+    launch_nl_project<T>(ctx, X, (T*)gC, Ns, ctx->stream);
+  }
+  {
+    Prof p(ctx, ST_STENCIL);
+    launch_cheb_step<T>(ctx, X, nullptr, W, (const T*)gC, Ns, s1 / e, c, 0.0,
+                        ctx->stream);
+  }
+  for (int k = 2; k <= m; ++k) {
+    const double sn = 1.0 / (tau - s);
+    if (nl) {
+      Prof p(ctx, ST_NL_PROJECT);
+      launch_nl_project<T>(ctx, cur, (T*)gC, Ns, ctx->stream);
+    }
+    {
+      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev)
+      Prof p(ctx, ST_STENCIL);
+      launch_cheb_step<T>(ctx, cur, prev, prev, (const T*)gC, Ns,
+                          2.0 * sn / e, c, -s * sn, ctx->stream);
+    }
+    std::swap(cur, prev);
+    s = sn;
+  }
+  if (cur != X) {
+    Prof p(ctx, ST_COPY, 0);
+    rc = cuda_err(cudaMemcpyAsync(X, cur, blk, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  }
+  if (rc) return rc;
+  return cuda_err(cudaGetLastError());
+}
+
+static int splitk_for(int tiles, long long K) {
+  int want = (4 * 152 + tiles - 1) / tiles;
+  long long maxs = K / 512;
+  if (maxs < 1) maxs = 1;
+  if (want > maxs) want = (int)maxs;
+  return want < 1 ? 1 : want;
+}
+
+// S = A^T B for N x Ns column-major blocks A, B (FP64).
+static void gram_f64(sq3_ctx* ctx, const double* A, const double* B, int Ns,
+                     double* S, int stage) {
+  Prof p(ctx, stage);
+  const long long N = ctx->grid.N;
+  cudaMemsetAsync(S, 0, (size_t)Ns * Ns * sizeof(double), ctx->stream);
+  GemmArgs g{};
+  g.M = Ns; g.N = Ns; g.K = (int)N;
+  g.A = A; g.lda = N; g.a_kcontig = true;
+  g.B = B; g.ldb = N; g.b_kcontig = true;
+  g.C = S; g.ldc = Ns; g.alpha = 1.0;
+  const int tiles = ((Ns + 63) / 64) * ((Ns + 63) / 64);
+  g.splits = splitk_for(tiles, N);
+  gemm_f64(g, EPI_ATOMIC, ctx->stream);
+}
+
+static int orthonormalise_f64(sq3_ctx* ctx, double* X, int Ns) {
+  const long long N = ctx->grid.N;
+  const size_t blk = (size_t)N * Ns * sizeof(double);
+  int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
+  if (rc) return rc;
+  rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes,
+              (size_t)2 * Ns * Ns * sizeof(double));
+  if (rc) return rc;
+  double* S = ctx->wsMat;
+  double* Rinv = ctx->wsMat + (size_t)Ns * Ns;
+  gram_f64(ctx, X, X, Ns, S, ST_GRAM);
+  {
+    const int panels = (Ns + 63) / 64;
+    Prof p(ctx, ST_CHOL, 3 * panels - 2);
+    rc = cholesky_lower_f64(ctx, S, Ns, ctx->stream);
+  }
+  if (rc) return rc;
+  {
+    Prof p(ctx, ST_TRINV);
+    tri_inverse_transpose_f64(S, Rinv, Ns, ctx->stream);
+  }
+  GemmArgs g{};
+  g.M = (int)N; g.N = Ns; g.K = Ns;
+  g.A = X; g.lda = N; g.a_kcontig = false;
+  g.B = Rinv; g.ldb = Ns; g.b_kcontig = true;
+  g.C = (double*)ctx->wsX; g.ldc = N; g.alpha = 1.0; g.beta = 0.0;
+  g.splits = 1;
+  {
+    Prof p(ctx, ST_XRINV);
+    gemm_f64(g, EPI_STORE, ctx->stream);
+  }
+  {
+    Prof p(ctx, ST_COPY, 0);
+    rc = cuda_err(cudaMemcpyAsync(X, ctx->wsX, blk, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  }
+  if (rc) return rc;
+  rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  return check_device_status(ctx);
+}
+
+static int project_f64(sq3_ctx* ctx, const double* X, int Ns, double* Hs) {
+  const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(double);
+  int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
+  if (rc) return rc;
+  rc = hamiltonian_apply_t<double>(ctx, X, (double*)ctx->wsX, Ns);
+  if (rc) return rc;
+  gram_f64(ctx, X, (const double*)ctx->wsX, Ns, Hs, ST_HS_GEMM);
+  {
+    Prof p(ctx, ST_HS_GEMM);
+    symmetrize_f64(Hs, Ns, ctx->stream);
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+static int density_f64(sq3_ctx* ctx, const double* X, const double* D, int Ns,
+                       double* rho) {
+  const long long N = ctx->grid.N;
+  cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), ctx->stream);
+  GemmArgs g{};
+  g.M = (int)N; g.N = Ns; g.K = Ns;
+  g.A = X; g.lda = N; g.a_kcontig = false;
+  g.B = D; g.ldb = Ns; g.b_kcontig = true;
+  g.X = X; g.ldx = N; g.rho = rho;
+  g.alpha = 2.0 / ctx->dV;
+  g.splits = 1;
+  Prof p(ctx, ST_RHO);
+  gemm_f64(g, EPI_RHO, ctx->stream);
+  return cuda_err(cudaGetLastError());
+}
+
+static int finish(sq3_ctx* ctx, int rc) {
+  if (rc) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();
+    return rc;
+  }
+  rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  return check_device_status(ctx);
+}
+
+static bool ready(const sq3_ctx* ctx) { return ctx && ctx->grid_ok && ctx->pot_ok; }
+
+}  // namespace sq3
+
+using namespace sq3;
+
+extern "C" {
+
+const char* sq3_version(void) { return "sq3-gb300 0.1 (sm_103a)"; }
+
+const char* sq3_status_string(int s) {
+  switch (s) {
+    case SQ3_OK: return "ok";
+    case SQ3_EINVAL: return "invalid argument";
+    case SQ3_ENOTSETUP: return "grid or potential not set";
+    case SQ3_ECUDA: return "CUDA error";
+    case SQ3_ENOTPD: return "Cholesky pivot not positive (X^T X not positive definite)";
+    case SQ3_ENOCONV: return "bisection or spectral bound check failed";
+    case SQ3_ETIMEOUT: return "bounded device wait timed out";
+    case SQ3_ENONFINITE: return "non-finite value detected";
+    case SQ3_ENOMEM: return "workspace allocation failed";
+    default: return "unknown status";
+  }
+}
+
+int sq3_create(sq3_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SQ3_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 ? SQ3_EINVAL : SQ3_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return SQ3_ECUDA;
+  sq3_ctx* c = new sq3_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaMalloc((void**)&c->dev_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->dev_scal, SQ3_DEV_SCAL * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->host_scal, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    sq3_destroy(c);
+    return SQ3_ECUDA;
+  }
+  cudaMemset(c->dev_status, 0, sizeof(int));
+  cudaMemset(c->dev_scal, 0, SQ3_DEV_SCAL * sizeof(double));
+  *out = c;
+  return SQ3_OK;
+}
+
+void sq3_destroy(sq3_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_projectors(c->proj);
+  for (auto& r : c->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
+                  c->wsMat, c->wsT, c->wsProj, c->wsSplit};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (c->host_scal) cudaFreeHost(c->host_scal);
+  delete c;
+}
+
+int sq3_setup_grid(sq3_ctx* c, int nx, int ny, int nz, double Lx, double Ly,
+                   double Lz, int fd_order) {
+  if (!c || fd_order < 2 || fd_order > 2 * SQ3_MAX_FD_RADIUS || fd_order % 2)
+    return SQ3_EINVAL;
+  const int R = fd_order / 2;
+  if (nx < R || ny < R || nz < R || nx > 1024 ||
+      !(Lx > 0) || !(Ly > 0) || !(Lz > 0))
+    return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  Grid g{};
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.N = (long long)nx * ny * nz;
+  g.hx = Lx / nx; g.hy = Ly / ny; g.hz = Lz / nz;
+  g.radius = R;
+  fd_weights(fd_order, g.w);
+  c->grid = g;
+  c->Lx = Lx; c->Ly = Ly; c->Lz = Lz;
+  c->dV = g.hx * g.hy * g.hz;
+  c->grid_ok = true;
+  c->pot_ok = false;
+  if (c->V) cudaFree(c->V);
+  if (c->Vf) cudaFree(c->Vf);
+  c->V = nullptr; c->Vf = nullptr;
+  free_projectors(c->proj);
+  return SQ3_OK;
+}
+
+int sq3_set_potential(sq3_ctx* c, const double* V) {
+  if (!c || !c->grid_ok) return SQ3_ENOTSETUP;
+  if (!V) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  const long long N = c->grid.N;
+  if (!c->V) {
+    if (cudaMalloc((void**)&c->V, N * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&c->Vf, N * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return SQ3_ENOMEM;
+    }
+  }
+  int rc = cuda_err(cudaMemcpyAsync(c->V, V, N * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+  if (rc) return rc;
+  to_float_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->V, c->Vf, N);
+  c->pot_ok = true;
+  return finish(c, 0);
+}
+
+int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
+                       const double* val, const double* gamma) {
+  if (!c || !c->grid_ok) return SQ3_ENOTSETUP;
+  if (n_proj < 0) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_projectors(c->proj);
+  if (n_proj == 0) return SQ3_OK;
+  if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
+  const long long N = c->grid.N;
+  for (int p = 0; p < n_proj; ++p)
+    if (ptr[p + 1] < ptr[p]) return SQ3_EINVAL;
+  const long long nnz = ptr[n_proj];
+  for (long long e = 0; e < nnz; ++e)
+    if (idx[e] < 0 || idx[e] >= N) return SQ3_EINVAL;
+  const double sq = sqrt(c->dV);
+  // group consecutive projectors with identical index lists (<= 4 per ball)
+  std::vector<int> bptr{0}, bidx, bp0, bnp, boff;
+  std::vector<double> bval;
+  int p = 0;
+  while (p < n_proj) {
+    int q = p + 1;
+    const int len = ptr[p + 1] - ptr[p];
+    while (q < n_proj && q - p < 4 && ptr[q + 1] - ptr[q] == len &&
+           memcmp(idx + ptr[q], idx + ptr[p], sizeof(int) * len) == 0)
+      ++q;
+    bp0.push_back(p);
+    bnp.push_back(q - p);
+    boff.push_back((int)bval.size());
+    for (int e = 0; e < len; ++e) bidx.push_back(idx[ptr[p] + e]);
+    for (int r = p; r < q; ++r)
+      for (int e = 0; e < len; ++e) bval.push_back(val[ptr[r] + e] * sq);
+    bptr.push_back((int)bidx.size());
+    p = q;
+  }
+  // per-point transposed table (projector, c_p[k])
+  std::vector<int> cnt(N + 1, 0);
+  for (long long e = 0; e < nnz; ++e) cnt[idx[e] + 1]++;
+  for (long long k = 0; k < N; ++k) cnt[k + 1] += cnt[k];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1), tproj(nnz);
+  std::vector<double> tval(nnz);
+  for (int q = 0; q < n_proj; ++q)
+    for (int e = ptr[q]; e < ptr[q + 1]; ++e) {
+      const int k = idx[e];
+      tproj[fill[k]] = q;
+      tval[fill[k]] = val[e] * sq;
+      fill[k]++;
+    }
+  std::vector<float> bvalf(bval.begin(), bval.end()), tvalf(tval.begin(), tval.end());
+  Projectors P;
+  P.n_proj = n_proj;
+  P.n_ball = (int)bp0.size();
+  int rc = SQ3_OK;
+  rc = rc ? rc : upload(&P.ball_ptr, bptr.data(), bptr.size());
+  rc = rc ? rc : upload(&P.ball_idx, bidx.data(), bidx.size());
+  rc = rc ? rc : upload(&P.ball_proj0, bp0.data(), bp0.size());
+  rc = rc ? rc : upload(&P.ball_nproj, bnp.data(), bnp.size());
+  rc = rc ? rc : upload(&P.ball_valoff, boff.data(), boff.size());
+  rc = rc ? rc : upload(&P.ball_val, bval.data(), bval.size());
+  rc = rc ? rc : upload(&P.ball_valf, bvalf.data(), bvalf.size());
+  rc = rc ? rc : upload(&P.gamma, gamma, (size_t)n_proj);
+  rc = rc ? rc : upload(&P.pt_ptr, cnt.data(), cnt.size());
+  rc = rc ? rc : upload(&P.pt_proj, tproj.data(), tproj.size());
+  rc = rc ? rc : upload(&P.pt_val, tval.data(), tval.size());
+  rc = rc ? rc : upload(&P.pt_valf, tvalf.data(), tvalf.size());
+  c->proj = P;
+  if (rc) { free_projectors(c->proj); return rc; }
+  return SQ3_OK;
+}
+
+int sq3_hamiltonian_apply(sq3_ctx* c, const void* X, void* Y, int Ns,
+                          sq3_prec prec) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || !Y || Ns <= 0 || X == Y || Ns > 65535) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc;
+  if (prec == SQ3_FP64) rc = hamiltonian_apply_t<double>(c, (const double*)X, (double*)Y, Ns);
+  else if (prec == SQ3_MIXED) rc = hamiltonian_apply_t<float>(c, (const float*)X, (float*)Y, Ns);
+  else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+int sq3_cheb_filter(sq3_ctx* c, void* X, int Ns, int degree, double a,
+                    double b, double a0, sq3_prec prec) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || Ns <= 0 || Ns > 65535 || degree < 1 || !(a0 < a) || !(a < b))
+    return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc;
+  if (prec == SQ3_FP64) rc = cheb_filter_t<double>(c, (double*)X, Ns, degree, a, b, a0);
+  else if (prec == SQ3_MIXED) rc = cheb_filter_t<float>(c, (float*)X, Ns, degree, a, b, a0);
+  else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+int sq3_orthonormalise(sq3_ctx* c, void* X, int Ns, sq3_prec prec) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || Ns <= 0 || Ns > c->grid.N) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc;
+  if (prec == SQ3_FP64) rc = orthonormalise_f64(c, (double*)X, Ns);
+  else if (prec == SQ3_MIXED) {
+    rc = SQ3_EINVAL;
+#ifdef SQ3_HAVE_MIXED
+    rc = orthonormalise_mixed(c, (float*)X, Ns);
+#endif
+  } else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+int sq3_project(sq3_ctx* c, const void* X, int Ns, sq3_prec prec, double* Hs) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || !Hs || Ns <= 0 || Ns > 65535) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc;
+  if (prec == SQ3_FP64) rc = project_f64(c, (const double*)X, Ns, Hs);
+  else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+int sq3_kernel_from_hs(sq3_ctx* c, const double* Hs, int Ns, int npl,
+                       double kT, double Ne, const double* bounds_in,
+                       double* D, double* out) {
+  if (!c) return SQ3_EINVAL;
+  if (!Hs || !out || Ns <= 0 || npl < 1 || npl > SQ3_MAX_NPL || !(kT > 0) ||
+      !(Ne > 0) || !(Ne < 2.0 * Ns))
+    return SQ3_EINVAL;
+  if (bounds_in && !(bounds_in[1] > 0)) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc = density_kernel_from_hs_f64(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out);
+  return finish(c, rc);
+}
+
+int sq3_density_kernel(sq3_ctx* c, const void* X, int Ns, int npl, double kT,
+                       double Ne, sq3_prec prec, const double* bounds_in,
+                       double* Hs_out, double* D, double* out) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || !out || Ns <= 0) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  double* Hs = Hs_out;
+  int rc;
+  if (!Hs) {
+    rc = ensure(&c->wsX2, &c->wsX2_bytes, (size_t)Ns * Ns * sizeof(double));
+    if (rc) return rc;
+    Hs = (double*)c->wsX2;
+  }
+  rc = sq3_project(c, X, Ns, prec, Hs);
+  if (rc) return rc;
+  return sq3_kernel_from_hs(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out);
+}
+
+int sq3_profile_enable(sq3_ctx* c, int enable) {
+  if (!c) return SQ3_EINVAL;
+  c->prof = enable != 0;
+  return SQ3_OK;
+}
+
+int sq3_profile_read(sq3_ctx* c, double* ms, long long* launches, int n) {
+  if (!c) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ3_ECUDA;
+  std::vector<double> t(ST_COUNT, 0.0);
+  std::vector<long long> l(ST_COUNT, 0);
+  for (auto& r : c->prof_recs) {
+    float x = 0.f;
+    cudaEventElapsedTime(&x, r.a, r.b);
+    t[r.stage] += x;
+    l[r.stage] += r.launches;
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+  for (int s = 0; s < n && s < ST_COUNT; ++s) {
+    if (ms) ms[s] = t[s];
+    if (launches) launches[s] = l[s];
+  }
+  return ST_COUNT;
+}
+
+int sq3_density(sq3_ctx* c, const void* X, const double* D, int Ns,
+                sq3_prec prec, double* rho) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X || !D || !rho || Ns <= 0 || Ns > 65535) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  int rc;
+  if (prec == SQ3_FP64) rc = density_f64(c, (const double*)X, D, Ns, rho);
+  else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libsq3.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "../../include/sq3.h"
+
+#define SQ3_MAX_FD_RADIUS 6
+#define SQ3_MAX_NPL 700
+#define SQ3_DEV_SCAL 2304
+
+namespace sq3 {
+
+// Device-side status word values (first error wins).
+enum DevStatus : int {
+  DEV_OK = 0,
+  DEV_NOTPD = 1,
+  DEV_NOCONV = 2,
+  DEV_NONFINITE = 3,
+  DEV_TIMEOUT = 4,
+};
+
+// Grid and stencil description passed by value to kernels.
+struct Grid {
+  int nx, ny, nz;
+  long long N;
+  double hx, hy, hz;
+  int radius;                        // fd_order / 2
+  double w[SQ3_MAX_FD_RADIUS + 1];   // second-derivative weights (unscaled)
+};
+
+// Projectors grouped into balls: every projector of a ball shares one
+// index list.  Also the transposed (per grid point) table used by the
+// fused apply inside the stencil.
+struct Projectors {
+  int n_proj = 0;
+  int n_ball = 0;
+  int max_per_ball = 0;       // projectors per ball (<= 4 used by kernels)
+  // ball b: points ball_ptr[b]..ball_ptr[b+1]-1 of ball_idx, projectors
+  // ball_proj0[b] .. ball_proj0[b]+ball_nproj[b]-1; values ball_val[p_local
+  // * nnz_ball + e] stored per projector contiguous over the ball points.
+  int* ball_ptr = nullptr;
+  int* ball_idx = nullptr;
+  int* ball_proj0 = nullptr;
+  int* ball_nproj = nullptr;
+  int* ball_valoff = nullptr;   // offset of the ball's value block in val arrays
+  double* ball_val = nullptr;   // c = chi sqrt(dV), FP64
+  float* ball_valf = nullptr;   // same, FP32
+  double* gamma = nullptr;      // n_proj
+  // per point: pt_ptr[k]..pt_ptr[k+1]-1 entries (projector id, value c)
+  int* pt_ptr = nullptr;
+  int* pt_proj = nullptr;
+  double* pt_val = nullptr;
+  float* pt_valf = nullptr;
+};
+
+}  // namespace sq3
+
+namespace sq3 {
+// Stage classes for the optional per-stage CUDA-event timing.
+enum Stage {
+  ST_STENCIL = 0, ST_NL_PROJECT, ST_GRAM, ST_CHOL, ST_TRINV, ST_XRINV,
+  ST_HS_GEMM, ST_LANCZOS, ST_CHEB_GEMM, ST_FERMI, ST_D_ACCUM, ST_RHO,
+  ST_SPLIT, ST_COPY, ST_COUNT
+};
+struct ProfRec { int stage; int launches; cudaEvent_t a, b; };
+}  // namespace sq3
+
+struct sq3_ctx {
+  int device = 0;
+  bool prof = false;
+  std::vector<sq3::ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  cudaStream_t stream = nullptr;
+  bool grid_ok = false, pot_ok = false;
+  sq3::Grid grid{};
+  double Lx = 0, Ly = 0, Lz = 0, dV = 0;
+  double* V = nullptr;      // N doubles
+  float* Vf = nullptr;      // N floats
+  double v_min = 0, v_max = 0;
+  sq3::Projectors proj;
+  int* dev_status = nullptr;      // device status word
+  double* dev_scal = nullptr;     // SQ3_DEV_SCAL device scalars: bounds,
+                                  // outputs, moments, coefficients
+  double* host_scal = nullptr;    // pinned mirror
+  // workspace
+  void* wsX = nullptr; size_t wsX_bytes = 0;        // one N x Ns block
+  void* wsX2 = nullptr; size_t wsX2_bytes = 0;      // second block (mixed)
+  double* wsMat = nullptr; size_t wsMat_bytes = 0;  // Ns x Ns matrices
+  double* wsT = nullptr; size_t wsT_bytes = 0;      // stored T_j
+  double* wsProj = nullptr; size_t wsProj_bytes = 0;  // projection coeffs
+  void* wsSplit = nullptr; size_t wsSplit_bytes = 0;  // bf16 split operands
+};
+
+namespace sq3 {
+
+int ensure(void** p, size_t* have, size_t need);
+
+// Records CUDA events around the launches issued during its lifetime on the
+// context's stream when profiling is enabled; `launches` is how many kernels
+// those are.
+struct Prof {
+  sq3_ctx* ctx; int stage; int launches; cudaEvent_t a = nullptr, b = nullptr;
+  Prof(sq3_ctx* c, int st, int n = 1);
+  ~Prof();
+};
+int cuda_err(cudaError_t e);
+int check_device_status(sq3_ctx* ctx);
+
+// ---- stencil / Hamiltonian (stencil.cu) ----
+// out = s1 * (H y - c y) + s2 * yprev, per vector, for Ns vectors.
+// gC: n_proj x Ns projection coefficients gamma_p c_p^T y (may be null when
+// there are no projectors).  yprev may alias out.
+template <typename T>
+void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                      const T* gC, int Ns, double s1, double c, double s2,
+                      cudaStream_t st);
+// gC[vec * n_proj + p] = gamma_p * sum_k c_p[k] y[k + vec*N]
+template <typename T>
+void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
+                       cudaStream_t st);
+
+// ---- FP64 GEMM (gemm_f64.cu) ----
+enum Epi { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_CHEB = 2, EPI_RHO = 3 };
+struct GemmArgs {
+  int M, N, K;
+  const double* A; long long lda; bool a_kcontig;   // A(m,k)
+  const double* B; long long ldb; bool b_kcontig;   // B(k,n)
+  double* C; long long ldc;
+  double alpha, beta;
+  int splits;                 // split-K factor (EPI_ATOMIC)
+  // EPI_CHEB: C = 2*acc - P, P(m,n) = P[m + n*ldp]; trace of C -> *trace.
+  const double* P; long long ldp; double* trace;
+  // EPI_RHO: rho[m] += alpha * sum_n X(m,n) acc(m,n), X(m,n)=X[m+n*ldx]
+  const double* X; long long ldx; double* rho;
+};
+void gemm_f64(const GemmArgs& g, Epi epi, cudaStream_t st);
+
+// ---- dense linear algebra (linalg.cu) ----
+int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, cudaStream_t st);
+void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
+                               cudaStream_t st);
+void symmetrize_f64(double* A, int n, cudaStream_t st);
+void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
+                        double* d_bounds, double* work, cudaStream_t st);
+
+// ---- Chebyshev Fermi-operator expansion (foe.cu) ----
+int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
+                               int npl, double sigma, double Ne,
+                               const double* bounds_in, double* D,
+                               double* out_host);
+
+// ---- mixed-precision path (mixed.cu) ----
+int mixed_gram(sq3_ctx* ctx, const float* X, const float* Y, int Ns,
+               double* S);
+int mixed_times_upper(sq3_ctx* ctx, const float* X, const double* R, int Ns,
+                      float* out);
+int mixed_rho(sq3_ctx* ctx, const float* X, const double* D, int Ns,
+              double* rho);
+
+}  // namespace sq3

@@ -1,0 +1,276 @@
+// Hamiltonian apply and Chebyshev-filter step on a periodic grid.
+//
+// H y = -1/2 Lap y + V y + sum_p gamma_p c_p (c_p^T y)   (Sec. 2, Eq. (KSeqn),
+// Eq. (nonlocaloperator)), with Lap the central finite-difference Laplacian of
+// order 2R (R <= 6; the paper uses twelfth order, Sec. 5).  One launch
+// computes, for every vector of a block,
+//
+//     out = s1 * (H y - c y) + s2 * yprev,
+//
+// which covers both a plain apply (s1 = 1, c = 0, s2 = 0) and one step of the
+// scaled Chebyshev filter recurrence.
+//
+// Layout: a CTA owns TY full x-rows of one vector and marches along z.  The
+// 2R+1 z-neighbours of each (x, y) column live in a register queue; the
+// current z-plane of the CTA's rows plus R halo rows above and below (wrapped
+// periodically) is staged in shared memory, so x- and y-taps read shared
+// memory and the x wrap costs nothing.  Every element of y is loaded from
+// global memory once per CTA for the queue plus once for each neighbouring
+// tile's y-halo; yprev, V and out stream once.  The nonlocal term is added
+// from a per-point table of (projector, c_p[k]) and the precomputed
+// coefficients gC = gamma (c^T y) of the same vector.
+#include "sq3_internal.cuh"
+
+namespace sq3 {
+
+template <typename T>
+struct StepCoef {
+  T diag;                      // -1/2 w0 (1/hx^2 + 1/hy^2 + 1/hz^2)
+  T ax[SQ3_MAX_FD_RADIUS + 1]; // -1/2 w_p / hx^2
+  T ay[SQ3_MAX_FD_RADIUS + 1];
+  T az[SQ3_MAX_FD_RADIUS + 1];
+};
+
+template <typename T, int R>
+__global__ void __launch_bounds__(1024)
+cheb_step_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
+                 const T* __restrict__ y, const T* yprev, T* out,
+                 const T* __restrict__ V, const T* __restrict__ gC,
+                 const int* __restrict__ pt_ptr, const int* __restrict__ pt_proj,
+                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);          // (TY + 2R) x nx
+  const int tid = threadIdx.x;
+  const int x = tid % nx;
+  const int ty = tid / nx;
+  const int y0 = blockIdx.x * TY;
+  const int yy = y0 + ty;
+  const bool active = (ty < TY) && (yy < ny);
+  const long long N = (long long)nx * ny * nz;
+  const long long plane = (long long)nx * ny;
+  const long long vbase = (long long)blockIdx.y * N;
+  const T* yv = y + vbase;
+  const int col = yy * nx + x;                      // offset inside a plane
+  const int halo_elems = 2 * R * nx;
+  const int rows = TY + 2 * R;
+
+  T q[2 * R + 1];
+#pragma unroll
+  for (int i = 0; i < 2 * R + 1; ++i) q[i] = T(0);
+  if (active) {
+#pragma unroll
+    for (int i = 1; i < 2 * R + 1; ++i) {
+      int zz = i - 1 - R;                           // planes -R .. R-1
+      zz += (zz < 0) ? nz : 0;
+      zz -= (zz >= nz) ? nz : 0;
+      q[i] = __ldg(yv + (long long)zz * plane + col);
+    }
+  }
+
+  for (int z = 0; z < nz; ++z) {
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+    int zl = z + R;
+    zl -= (zl >= nz) ? nz : 0;
+    zl -= (zl >= nz) ? nz : 0;
+    if (active) q[2 * R] = __ldg(yv + (long long)zl * plane + col);
+
+    __syncthreads();  // previous plane fully consumed
+    if (active) sm[(ty + R) * nx + x] = q[R];
+    const T* pz = yv + (long long)z * plane;
+    for (int e = tid; e < halo_elems; e += blockDim.x) {
+      int r = e / nx, xx = e - r * nx;
+      int srow = (r < R) ? r : (r + TY);            // smem row
+      int gy = y0 - R + srow;
+      gy %= ny;
+      gy += (gy < 0) ? ny : 0;
+      sm[srow * nx + xx] = __ldg(pz + gy * nx + xx);
+    }
+    // rows of a partial last tile that have no owner thread
+    for (int e = tid; e < TY * nx; e += blockDim.x) {
+      int r = e / nx;
+      if (y0 + r >= ny) {
+        int gy = (y0 + r) % ny;
+        sm[(r + R) * nx + (e - r * nx)] = __ldg(pz + gy * nx + (e - r * nx));
+      }
+    }
+    __syncthreads();
+
+    if (active) {
+      const long long gidx = (long long)z * plane + col;
+      const T u = q[R];
+      const T* row = sm + (ty + R) * nx;
+      T acc = (k.diag + __ldg(V + gidx) - c) * u;
+#pragma unroll
+      for (int p = 1; p <= R; ++p) {
+        int xp = x + p; xp -= (xp >= nx) ? nx : 0;
+        int xm = x - p; xm += (xm < 0) ? nx : 0;
+        acc += k.ax[p] * (row[xp] + row[xm]);
+        acc += k.ay[p] * (row[p * nx + x] + row[-p * nx + x]);
+        acc += k.az[p] * (q[R + p] + q[R - p]);
+      }
+      if (gC != nullptr) {
+        const int e0 = __ldg(pt_ptr + gidx), e1 = __ldg(pt_ptr + gidx + 1);
+        const T* gv = gC + (long long)blockIdx.y * n_proj;
+        for (int e = e0; e < e1; ++e)
+          acc += __ldg(pt_val + e) * __ldg(gv + __ldg(pt_proj + e));
+      }
+      T r = s1 * acc;
+      if (s2 != T(0)) r += s2 * yprev[vbase + gidx];
+      out[vbase + gidx] = r;
+    }
+  }
+}
+
+static int pick_ty(int nx, int ny) {
+  int best = 1;
+  for (int t = 1; t <= ny; ++t)
+    if (ny % t == 0 && nx * t <= 512) best = t;
+  if (nx * best < 128) {  // tiny rows: allow a ragged last tile
+    best = 512 / nx;
+    if (best > ny) best = ny;
+    if (best < 1) best = 1;
+  }
+  return best;
+}
+
+template <typename T, int R>
+static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                     const T* gC, int Ns, double s1, double c, double s2,
+                     cudaStream_t st) {
+  const Grid& g = ctx->grid;
+  StepCoef<T> k{};
+  double ix = 1.0 / (g.hx * g.hx), iy = 1.0 / (g.hy * g.hy),
+         iz = 1.0 / (g.hz * g.hz);
+  k.diag = T(-0.5 * g.w[0] * (ix + iy + iz));
+  for (int p = 1; p <= R; ++p) {
+    k.ax[p] = T(-0.5 * g.w[p] * ix);
+    k.ay[p] = T(-0.5 * g.w[p] * iy);
+    k.az[p] = T(-0.5 * g.w[p] * iz);
+  }
+  const int TY = pick_ty(g.nx, g.ny);
+  dim3 grid((g.ny + TY - 1) / TY, Ns);
+  dim3 block(g.nx * TY);
+  size_t smem = (size_t)(TY + 2 * R) * g.nx * sizeof(T);
+  const T* V = nullptr;
+  const T* pv = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    V = reinterpret_cast<const T*>(ctx->V);
+    pv = reinterpret_cast<const T*>(ctx->proj.pt_val);
+  } else {
+    V = reinterpret_cast<const T*>(ctx->Vf);
+    pv = reinterpret_cast<const T*>(ctx->proj.pt_valf);
+  }
+  const bool nl = (ctx->proj.n_proj > 0) && gC != nullptr;
+  cheb_step_kernel<T, R><<<grid, block, smem, st>>>(
+      g.nx, g.ny, g.nz, TY, k, y, yprev, out, V, nl ? gC : nullptr,
+      ctx->proj.pt_ptr, ctx->proj.pt_proj, pv, ctx->proj.n_proj, T(s1), T(c),
+      T(s2));
+}
+
+template <typename T>
+void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                      const T* gC, int Ns, double s1, double c, double s2,
+                      cudaStream_t st) {
+  switch (ctx->grid.radius) {
+    case 1: launch_r<T, 1>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    case 2: launch_r<T, 2>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    case 3: launch_r<T, 3>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    case 4: launch_r<T, 4>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    case 5: launch_r<T, 5>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    default: launch_r<T, 6>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Nonlocal projection gC[v * n_proj + p] = gamma_p * sum_k c_p[k] y[k + v N].
+// One CTA per (ball, group of VB vectors); a ball's points are read once per
+// group and its (<= 4) projectors are accumulated together.
+// ---------------------------------------------------------------------------
+template <typename T, int VB>
+__global__ void __launch_bounds__(256)
+nl_project_kernel(long long N, int Ns, const T* __restrict__ y,
+                  const int* __restrict__ ball_ptr,
+                  const int* __restrict__ ball_idx,
+                  const int* __restrict__ ball_proj0,
+                  const int* __restrict__ ball_nproj,
+                  const int* __restrict__ ball_valoff,
+                  const T* __restrict__ ball_val,
+                  const double* __restrict__ gamma, int n_proj, T* gC) {
+  const int b = blockIdx.x;
+  const int v0 = blockIdx.y * VB;
+  const int e0 = ball_ptr[b], e1 = ball_ptr[b + 1];
+  const int nnz = e1 - e0;
+  const int np = ball_nproj[b];
+  const T* val = ball_val + ball_valoff[b];
+  T acc[VB][4];
+#pragma unroll
+  for (int v = 0; v < VB; ++v)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[v][p] = T(0);
+  for (int e = threadIdx.x; e < nnz; e += blockDim.x) {
+    const long long k = __ldg(ball_idx + e0 + e);
+    T cv[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) cv[p] = (p < np) ? __ldg(val + p * nnz + e) : T(0);
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      if (v0 + v < Ns) {
+        const T yk = __ldg(y + (long long)(v0 + v) * N + k);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[v][p] += cv[p] * yk;
+      }
+    }
+  }
+  // block reduction of VB*4 sums
+  __shared__ T red[32][VB * 4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < VB; ++v)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      T s = acc[v][p];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[warp][v * 4 + p] = s;
+    }
+  __syncthreads();
+  const int nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < VB * 4; t += blockDim.x) {
+    T s = T(0);
+    for (int w = 0; w < nwarps; ++w) s += red[w][t];
+    const int v = t / 4, p = t % 4;
+    if (p < np && v0 + v < Ns) {
+      const int pid = ball_proj0[b] + p;
+      gC[(long long)(v0 + v) * n_proj + pid] = T(gamma[pid]) * s;
+    }
+  }
+}
+
+template <typename T>
+void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
+                       cudaStream_t st) {
+  const Projectors& P = ctx->proj;
+  if (P.n_proj == 0) return;
+  constexpr int VB = 8;
+  dim3 grid(P.n_ball, (Ns + VB - 1) / VB);
+  const T* val;
+  if constexpr (sizeof(T) == 8) val = reinterpret_cast<const T*>(P.ball_val);
+  else val = reinterpret_cast<const T*>(P.ball_valf);
+  nl_project_kernel<T, VB><<<grid, 256, 0, st>>>(
+      ctx->grid.N, Ns, y, P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
+      P.ball_valoff, val, P.gamma, P.n_proj, gC);
+}
+
+template void launch_cheb_step<double>(const sq3_ctx*, const double*,
+                                       const double*, double*, const double*,
+                                       int, double, double, double,
+                                       cudaStream_t);
+template void launch_cheb_step<float>(const sq3_ctx*, const float*,
+                                      const float*, float*, const float*, int,
+                                      double, double, double, cudaStream_t);
+template void launch_nl_project<double>(const sq3_ctx*, const double*, double*,
+                                        int, cudaStream_t);
+template void launch_nl_project<float>(const sq3_ctx*, const float*, float*,
+                                       int, cudaStream_t);
+
+}  // namespace sq3

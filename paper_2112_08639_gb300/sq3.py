@@ -1,0 +1,198 @@
+"""Thin ctypes binding of the libsq3 C ABI (``include/sq3.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays are torch CUDA tensors; a block of Ns vectors is a
+contiguous tensor of shape (Ns, N), which is the library's N x Ns
+column-major layout.  Importing this module loads ``_build/libsq3.so`` and
+raises if it has not been built (``paper_2112_08639_gb300.build.build()``):
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FP64 = 0
+MIXED = 1
+
+OK, EINVAL, ENOTSETUP, ECUDA, ENOTPD, ENOCONV, ETIMEOUT, ENONFINITE, ENOMEM = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(f"libsq3.so is not built ({_build.LIB}); run "
+                      "paper_2112_08639_gb300.build.build() first")
+lib = ctypes.CDLL(_build.LIB)
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_sigs = {
+    "sq3_create": (_i, [ctypes.POINTER(_p), _i, _p]),
+    "sq3_destroy": (None, [_p]),
+    "sq3_setup_grid": (_i, [_p, _i, _i, _i, _d, _d, _d, _i]),
+    "sq3_set_potential": (_i, [_p, _p]),
+    "sq3_set_projectors": (_i, [_p, _i, _p, _p, _p, _p]),
+    "sq3_hamiltonian_apply": (_i, [_p, _p, _p, _i, _i]),
+    "sq3_cheb_filter": (_i, [_p, _p, _i, _i, _d, _d, _d, _i]),
+    "sq3_orthonormalise": (_i, [_p, _p, _i, _i]),
+    "sq3_project": (_i, [_p, _p, _i, _i, _p]),
+    "sq3_kernel_from_hs": (_i, [_p, _p, _i, _i, _d, _d, _p, _p, _p]),
+    "sq3_density_kernel": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p, _p]),
+    "sq3_density": (_i, [_p, _p, _p, _i, _i, _p]),
+    "sq3_status_string": (ctypes.c_char_p, [_i]),
+    "sq3_version": (ctypes.c_char_p, []),
+    "sq3_profile_enable": (_i, [_p, _i]),
+    "sq3_profile_read": (_i, [_p, _p, _p, _i]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class SQ3Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib.sq3_status_string(code).decode()} ({code})")
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise SQ3Error(code, where)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec_dtype(prec: int):
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+def version() -> str:
+    return lib.sq3_version().decode()
+
+
+class Context:
+    """Owns one sq3_ctx bound to a device and a stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(lib.sq3_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)),
+               "sq3_create")
+        self._h = h
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sq3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup_grid(self, nx, ny, nz, Lx, Ly, Lz, fd_order=12):
+        _check(lib.sq3_setup_grid(self._h, nx, ny, nz, Lx, Ly, Lz, fd_order), "sq3_setup_grid")
+        self.N = nx * ny * nz
+        self.dV = (Lx / nx) * (Ly / ny) * (Lz / nz)
+
+    def set_potential(self, V: torch.Tensor):
+        V = V.to(device=self.device, dtype=torch.float64).contiguous()
+        _check(lib.sq3_set_potential(self._h, _ptr(V)), "sq3_set_potential")
+
+    def set_projectors(self, ptr, idx, val, gamma):
+        ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+        n = len(gamma)
+        _check(lib.sq3_set_projectors(self._h, n, ptr.ctypes.data, idx.ctypes.data,
+                                      val.ctypes.data, gamma.ctypes.data),
+               "sq3_set_projectors")
+
+    def hamiltonian_apply(self, X: torch.Tensor, Y: torch.Tensor | None = None, prec=FP64):
+        if Y is None:
+            Y = torch.empty_like(X)
+        _check(lib.sq3_hamiltonian_apply(self._h, _ptr(X), _ptr(Y), X.shape[0], prec),
+               "sq3_hamiltonian_apply")
+        return Y
+
+    def cheb_filter(self, X: torch.Tensor, degree: int, a: float, b: float, a0: float, prec=FP64):
+        _check(lib.sq3_cheb_filter(self._h, _ptr(X), X.shape[0], degree, a, b, a0, prec),
+               "sq3_cheb_filter")
+        return X
+
+    def orthonormalise(self, X: torch.Tensor, prec=FP64):
+        _check(lib.sq3_orthonormalise(self._h, _ptr(X), X.shape[0], prec), "sq3_orthonormalise")
+        return X
+
+    def project(self, X: torch.Tensor, prec=FP64, Hs: torch.Tensor | None = None):
+        Ns = X.shape[0]
+        if Hs is None:
+            Hs = torch.empty((Ns, Ns), dtype=torch.float64, device=self.device)
+        _check(lib.sq3_project(self._h, _ptr(X), Ns, prec, _ptr(Hs)), "sq3_project")
+        return Hs
+
+    @staticmethod
+    def _unpack(out):
+        return {"mu": out[0], "e_band": out[1], "e_ent": out[2], "chi": out[3],
+                "xi": out[4], "two_tr_D": out[5]}
+
+    def kernel_from_hs(self, Hs: torch.Tensor, npl: int, kT: float, Ne: float,
+                       bounds=None, D: torch.Tensor | None = None, want_D=True):
+        Ns = Hs.shape[0]
+        if D is None and want_D:
+            D = torch.empty((Ns, Ns), dtype=torch.float64, device=self.device)
+        out = (ctypes.c_double * 6)()
+        b = (ctypes.c_double * 2)(*bounds) if bounds is not None else None
+        _check(lib.sq3_kernel_from_hs(self._h, _ptr(Hs), Ns, npl, kT, Ne, b, _ptr(D), out),
+               "sq3_kernel_from_hs")
+        return D, self._unpack(out)
+
+    def density_kernel(self, X: torch.Tensor, npl: int, kT: float, Ne: float, prec=FP64,
+                       bounds=None, Hs: torch.Tensor | None = None,
+                       D: torch.Tensor | None = None):
+        Ns = X.shape[0]
+        if D is None:
+            D = torch.empty((Ns, Ns), dtype=torch.float64, device=self.device)
+        out = (ctypes.c_double * 6)()
+        b = (ctypes.c_double * 2)(*bounds) if bounds is not None else None
+        _check(lib.sq3_density_kernel(self._h, _ptr(X), Ns, npl, kT, Ne, prec, b, _ptr(Hs),
+                                      _ptr(D), out), "sq3_density_kernel")
+        return D, self._unpack(out)
+
+    def density(self, X: torch.Tensor, D: torch.Tensor, prec=FP64, rho: torch.Tensor | None = None):
+        if rho is None:
+            rho = torch.empty(X.shape[1], dtype=torch.float64, device=self.device)
+        _check(lib.sq3_density(self._h, _ptr(X), _ptr(D), X.shape[0], prec, _ptr(rho)),
+               "sq3_density")
+        return rho
+
+    STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
+              "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy")
+
+    def profile(self, enable: bool = True):
+        _check(lib.sq3_profile_enable(self._h, int(enable)), "sq3_profile_enable")
+
+    def profile_read(self) -> dict:
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_longlong * n)()
+        r = lib.sq3_profile_read(self._h, ms, la, n)
+        if r < 0:
+            raise SQ3Error(r, "sq3_profile_read")
+        return {s: (ms[i], la[i]) for i, s in enumerate(self.STAGES)}
