@@ -23,10 +23,12 @@ gemm_f64_kernel(GemmArgs g) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  int kchunk = (g.K + g.splits - 1) / g.splits;
+  if (g.tri == 1 && n0 + BN <= m0) return;       // tile strictly below diagonal
+  const int Keff = (g.tri == 2) ? min(g.K, n0 + BN) : g.K;
+  int kchunk = (Keff + g.splits - 1) / g.splits;
   kchunk = (kchunk + BK - 1) / BK * BK;
   const int kbeg = blockIdx.z * kchunk;
-  const int kend = min(g.K, kbeg + kchunk);
+  const int kend = min(Keff, kbeg + kchunk);
 
   double ra[4], rb[4];
   auto load = [&](int k0) {

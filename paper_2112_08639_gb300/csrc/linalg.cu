@@ -21,9 +21,17 @@ __device__ inline void set_status(int* st, int code) {
   atomicCAS(st, 0, code);
 }
 
+__global__ void copy_diag_kernel(const double* S, int n, double* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = S[i + (long long)i * n];
+}
+
 // Factor the kb x kb diagonal block at (k0, k0) of the column-major n x n S.
+// A pivot that is not above 1e-13 times the original diagonal entry diag0
+// (numerically rank-deficient X) or is not finite sets DEV_NOTPD.
 __global__ void __launch_bounds__(256)
-potrf_diag_kernel(double* S, int n, int k0, int kb, int* status) {
+potrf_diag_kernel(double* S, int n, int k0, int kb, const double* diag0,
+                  int* status) {
   __shared__ double A[CH_NB][CH_NB + 1];
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     int i = e % kb, j = e / kb;
@@ -33,7 +41,7 @@ potrf_diag_kernel(double* S, int n, int k0, int kb, int* status) {
   for (int j = 0; j < kb; ++j) {
     if (threadIdx.x == 0) {
       double d = A[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
+      if (!(d > 1e-13 * diag0[k0 + j]) || !isfinite(d)) {
         set_status(status, DEV_NOTPD);
         d = 1.0;
       }
@@ -88,10 +96,13 @@ trsm_panel_kernel(double* S, int n, int k0, int kb) {
   }
 }
 
-int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, cudaStream_t st) {
+int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, double* diag_ws,
+                       cudaStream_t st) {
+  copy_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, n, diag_ws);
   for (int k0 = 0; k0 < n; k0 += CH_NB) {
     const int kb = (n - k0 < CH_NB) ? n - k0 : CH_NB;
-    potrf_diag_kernel<<<1, 256, 0, st>>>(S, n, k0, kb, ctx->dev_status);
+    potrf_diag_kernel<<<1, 256, 0, st>>>(S, n, k0, kb, diag_ws,
+                                         ctx->dev_status);
     const int m2 = n - k0 - kb;
     if (m2 <= 0) continue;
     trsm_panel_kernel<<<(m2 + 127) / 128, 128, 0, st>>>(S, n, k0, kb);
@@ -146,6 +157,18 @@ __global__ void symmetrize_kernel(double* A, int n) {
     A[i + (long long)j * n] = s;
     A[j + (long long)i * n] = s;
   }
+}
+
+__global__ void mirror_upper_kernel(double* A, int n) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e % n), j = (int)(e / n);
+  if (i > j) A[e] = A[j + (long long)i * n];
+}
+
+void mirror_upper_f64(double* A, int n, cudaStream_t st) {
+  long long tot = (long long)n * n;
+  mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, n);
 }
 
 void symmetrize_f64(double* A, int n, cudaStream_t st) {

@@ -207,9 +207,11 @@ static void gram_f64(sq3_ctx* ctx, const double* A, const double* B, int Ns,
   g.A = A; g.lda = N; g.a_kcontig = true;
   g.B = B; g.ldb = N; g.b_kcontig = true;
   g.C = S; g.ldc = Ns; g.alpha = 1.0;
-  const int tiles = ((Ns + 63) / 64) * ((Ns + 63) / 64);
-  g.splits = splitk_for(tiles, N);
+  const int nt = (Ns + 63) / 64;
+  g.splits = splitk_for(nt * (nt + 1) / 2, N);
+  g.tri = 1;                       // S is symmetric: upper tiles only
   gemm_f64(g, EPI_ATOMIC, ctx->stream);
+  mirror_upper_f64(S, Ns, ctx->stream);
 }
 
 static int orthonormalise_f64(sq3_ctx* ctx, double* X, int Ns) {
@@ -218,15 +220,16 @@ static int orthonormalise_f64(sq3_ctx* ctx, double* X, int Ns) {
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
   rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes,
-              (size_t)2 * Ns * Ns * sizeof(double));
+              ((size_t)2 * Ns * Ns + Ns) * sizeof(double));
   if (rc) return rc;
   double* S = ctx->wsMat;
   double* Rinv = ctx->wsMat + (size_t)Ns * Ns;
+  double* diag = Rinv + (size_t)Ns * Ns;
   gram_f64(ctx, X, X, Ns, S, ST_GRAM);
   {
     const int panels = (Ns + 63) / 64;
-    Prof p(ctx, ST_CHOL, 3 * panels - 2);
-    rc = cholesky_lower_f64(ctx, S, Ns, ctx->stream);
+    Prof p(ctx, ST_CHOL, 3 * panels - 1);
+    rc = cholesky_lower_f64(ctx, S, Ns, diag, ctx->stream);
   }
   if (rc) return rc;
   {
@@ -239,6 +242,7 @@ static int orthonormalise_f64(sq3_ctx* ctx, double* X, int Ns) {
   g.B = Rinv; g.ldb = Ns; g.b_kcontig = true;
   g.C = (double*)ctx->wsX; g.ldc = N; g.alpha = 1.0; g.beta = 0.0;
   g.splits = 1;
+  g.tri = 2;                       // R^{-1} is upper triangular
   {
     Prof p(ctx, ST_XRINV);
     gemm_f64(g, EPI_STORE, ctx->stream);
@@ -260,11 +264,8 @@ static int project_f64(sq3_ctx* ctx, const double* X, int Ns, double* Hs) {
   if (rc) return rc;
   rc = hamiltonian_apply_t<double>(ctx, X, (double*)ctx->wsX, Ns);
   if (rc) return rc;
+  // upper triangle of X^T (H X), mirrored: H is symmetric
   gram_f64(ctx, X, (const double*)ctx->wsX, Ns, Hs, ST_HS_GEMM);
-  {
-    Prof p(ctx, ST_HS_GEMM);
-    symmetrize_f64(Hs, Ns, ctx->stream);
-  }
   return cuda_err(cudaGetLastError());
 }
 

@@ -133,6 +133,10 @@ struct GemmArgs {
   double* C; long long ldc;
   double alpha, beta;
   int splits;                 // split-K factor (EPI_ATOMIC)
+  // 1: only tiles on or above the diagonal are computed (C symmetric);
+  // 2: B is upper triangular (B(k,n) = 0 for k > n), so K stops at the
+  //    tile's last column.
+  int tri;
   // EPI_CHEB: C = 2*acc - P, P(m,n) = P[m + n*ldp]; trace of C -> *trace.
   const double* P; long long ldp; double* trace;
   // EPI_RHO: rho[m] += alpha * sum_n X(m,n) acc(m,n), X(m,n)=X[m+n*ldx]
@@ -141,10 +145,12 @@ struct GemmArgs {
 void gemm_f64(const GemmArgs& g, Epi epi, cudaStream_t st);
 
 // ---- dense linear algebra (linalg.cu) ----
-int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, cudaStream_t st);
+int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, double* diag_ws,
+                       cudaStream_t st);
 void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
                                cudaStream_t st);
 void symmetrize_f64(double* A, int n, cudaStream_t st);
+void mirror_upper_f64(double* A, int n, cudaStream_t st);
 void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st);
 
