@@ -130,6 +130,8 @@ int sq3_project(sq3_ctx* ctx, const void* X, int Ns, sq3_prec prec,
  *   2 sum'_j c_j(mu) m_j = Ne (Eq. (FermiLevelCalc));
  *   Ds = sum'_j c_j T_j (Eq. (ChebyshevExpansion));
  *   E_band = 2 sum'_j d_j m_j; E_ent = 2 sigma sum'_j e_j m_j.
+ * prec: SQ3_FP64 runs the recurrence in FP64; SQ3_MIXED keeps T_j in FP32
+ * with BF16-split tensor-core products (traces, bisection and Ds in FP64).
  * Hs: device Ns x Ns double (symmetric).  kT: sigma in Ha.  bounds_in: HOST
  * pointer to {chi, xi} to use as given, or NULL to estimate them with a
  * 40-step Lanczos on Hs (extremal Ritz values widened by their residual
@@ -140,8 +142,8 @@ int sq3_project(sq3_ctx* ctx, const void* X, int Ns, sq3_prec prec,
  * moments exceed the bound |m_j| <= Ns by more than 1e-6 relative, which
  * means the spectrum left [-1, 1]). */
 int sq3_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
-                       double kT, double Ne, const double* bounds_in,
-                       double* D, double* out);
+                       double kT, double Ne, sq3_prec prec,
+                       const double* bounds_in, double* D, double* out);
 
 /* sq3_project followed by sq3_kernel_from_hs: the density-kernel step of one
  * SQ3 iteration.  Hs_out (device, may be NULL) receives Hs. */

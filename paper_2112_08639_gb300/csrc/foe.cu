@@ -184,14 +184,13 @@ __global__ void accumulate_d_kernel(const double* __restrict__ T, long long nn,
   D[e] = s;
 }
 
-int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
-                               int npl, double sigma, double Ne,
-                               const double* bounds_in, double* D,
-                               double* out_host) {
+int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+                           double sigma, double Ne, const double* bounds_in,
+                           double* D, double* out_host, bool mixed) {
   cudaStream_t st = ctx->stream;
   const long long nn = (long long)Ns * Ns;
-  // workspace: T_0..T_npl, then Lanczos work
-  size_t need_T = (size_t)(npl + 1) * nn * sizeof(double);
+  // workspace: T_0..T_npl (FP64, or FP32 in the mixed path), Lanczos work
+  size_t need_T = (size_t)(npl + 1) * nn * (mixed ? sizeof(float) : sizeof(double));
   int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
   if (rc) return rc;
   const int lsteps = Ns < 40 ? Ns : 40;
@@ -215,6 +214,10 @@ int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
     lanczos_bounds_f64(ctx, Hs, Ns, lsteps, bounds, ctx->wsMat, st);
   }
   double* T = ctx->wsT;
+  if (mixed) {
+    rc = cheb_recurrence_mixed(ctx, Hs, Ns, npl, bounds, mom, (float*)ctx->wsT);
+    if (rc) return rc;
+  } else {
   {
     Prof p(ctx, ST_CHEB_GEMM, 2);
     hhat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
@@ -235,6 +238,7 @@ int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
     gemm_f64(g, EPI_CHEB, st);
   }
   }
+  }
   const int M = (8 * (npl + 1) > 1024) ? 8 * (npl + 1) : 1024;
   size_t smem = (size_t)5 * M * sizeof(double);
   cudaFuncSetAttribute(fermi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -245,7 +249,9 @@ int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
                                         coef, outd, ctx->dev_status);
   }
   Prof pd(ctx, ST_D_ACCUM, D != nullptr ? 1 : 0);
-  if (D != nullptr)
+  if (D != nullptr && mixed)
+    accumulate_d_mixed(ctx, (const float*)ctx->wsT, Ns, npl, coef, D);
+  else if (D != nullptr)
     accumulate_d_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
         T, nn, Ns, npl, coef, D);
   rc = cuda_err(cudaGetLastError());

@@ -1,0 +1,408 @@
+// Mixed-precision path: FP32 block X, BF16-split tcgen05 GEMMs with FP32
+// accumulation, FP64 Cholesky / Fermi level / energies / reductions.
+//
+// Steps (Sec. 4 of the paper, same order as the FP64 path):
+//   orthonormalise   S = X^T X (tcgen05, FP64 accumulation across K-splits),
+//                    FP64 Cholesky, R^{-1}, X <- X R^{-1} (tcgen05); applied
+//                    twice (Cholesky QR 2); when the first Cholesky meets a
+//                    non-positive pivot the pass is repeated on S + s I
+//                    (shifted Cholesky QR) before the two plain passes.
+//   project          H X by the FP32 stencil, Hs = X^T (H X) (tcgen05)
+//   kernel           Hhat and T_j in FP32 with BF16-split products, traces
+//                    and the Fermi-level bisection in FP64, Ds in FP64
+//   density          X Ds (tcgen05) with the FP64 row-dot epilogue
+// The split of an FP32 value x into bf16 pieces is x_0 = bf16(x),
+// x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1), all round-to-nearest-even.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "sq3_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace sq3 {
+
+static inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
+
+template <typename T>
+__device__ __forceinline__ void split3(T xv, __nv_bfloat16* out, long long e,
+                                       long long ps, int pieces) {
+  const float x = (float)xv;
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  out[e] = h;
+  if (pieces > 1) {
+    const float r = x - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r);
+    out[e + ps] = l;
+    if (pieces > 2) out[e + 2 * ps] = __float2bfloat16_rn(r - __bfloat162float(l));
+  }
+}
+
+// Column-major rows x cols source (leading dimension lds) -> pieces with the
+// source column as operand row: out[q][c * ld + r].
+template <typename T>
+__global__ void split_cols_kernel(const T* __restrict__ src, long long lds, int rows,
+                                  int cols, __nv_bfloat16* out, long long ld,
+                                  long long ps, int pieces) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / rows, r = e - c * rows;
+    split3(src[r + c * lds], out, c * ld + r, ps, pieces);
+  }
+}
+
+// Column-major rows x cols source -> pieces with the source ROW as operand
+// row: out[q][r * ld + c] (a transpose through shared memory).
+__global__ void split_rows_kernel(const float* __restrict__ src, long long lds, int rows,
+                                  int cols, __nv_bfloat16* out, long long ld,
+                                  long long ps, int pieces) {
+  __shared__ float tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const long long r = r0 + tx;
+    const int c = c0 + j;
+    tile[j][tx] = (r < rows && c < cols) ? src[r + (long long)c * lds] : 0.f;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const long long r = r0 + j;
+    const int c = c0 + tx;
+    if (r < rows && c < cols) split3(tile[tx][j], out, r * ld + c, ps, pieces);
+  }
+}
+
+__global__ void hhat_f32_kernel(const double* __restrict__ Hs, int n, const double* bounds,
+                                float* T0, float* T1, double* moments) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e == 0) moments[0] = (double)n;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const double h = (Hs[e] - (i == j ? bounds[0] : 0.0)) / bounds[1];
+  T1[e] = (float)h;
+  T0[e] = (i == j) ? 1.f : 0.f;
+}
+
+__global__ void trace_f32_kernel(const float* __restrict__ A, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += A[i + (long long)i * n];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+__global__ void accumulate_d_f32_kernel(const float* __restrict__ T, long long nn, int n,
+                                        int npl, const double* __restrict__ coef,
+                                        double* D) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  double s = (i == j) ? 0.5 * coef[0] : 0.0;
+  for (int t = 1; t <= npl; ++t) s += coef[t] * (double)T[(long long)t * nn + e];
+  D[e] = s;
+}
+
+__global__ void add_shift_kernel(double* S, int n, double rel) {
+  // S += rel * (trace(S)/n) I, computed from the diagonal in one CTA
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += S[i + (long long)i * n];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  const double shift = rel * t / n;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S[i + (long long)i * n] += shift;
+}
+
+// ---------------------------------------------------------------------------
+// piece buffers inside ctx->wsSplit
+// ---------------------------------------------------------------------------
+struct MixedBuffers {
+  __nv_bfloat16* colX;   // X as K-major over the grid: rows = vectors
+  __nv_bfloat16* colY;   // second block (H X) in the same layout
+  __nv_bfloat16* rowX;   // X as K-major over vectors: rows = grid points
+  __nv_bfloat16* matA;   // Ns x Ns operands
+  __nv_bfloat16* matB;
+  __nv_bfloat16* matC;
+  long long ldN, ldS, psN, psS;
+};
+
+static int mixed_buffers(sq3_ctx* ctx, int Ns, MixedBuffers* b) {
+  const long long N = ctx->grid.N;
+  b->ldN = pad8(N);
+  b->ldS = pad8(Ns);
+  b->psN = (long long)Ns * b->ldN;          // colX: Ns rows of ldN
+  const long long psR = N * b->ldS;         // rowX: N rows of ldS
+  b->psS = (long long)Ns * b->ldS;
+  const size_t need = (size_t)MIXED_PIECES * (2 * b->psN + psR + 3 * b->psS) * 2 + 4096;
+  int rc = ensure(&ctx->wsSplit, &ctx->wsSplit_bytes, need);
+  if (rc) return rc;
+  __nv_bfloat16* p = (__nv_bfloat16*)ctx->wsSplit;
+  b->colX = p; p += MIXED_PIECES * b->psN;
+  b->colY = p; p += MIXED_PIECES * b->psN;
+  b->rowX = p; p += MIXED_PIECES * psR;
+  b->matA = p; p += MIXED_PIECES * b->psS;
+  b->matB = p; p += MIXED_PIECES * b->psS;
+  b->matC = p;
+  return SQ3_OK;
+}
+
+static Products products(int pieces) {
+  Products pr{};
+  if (pieces == 3) {
+    // terms down to 2^-16 relative: x0y0, x0y1, x1y0, x0y2, x1y1, x2y0
+    const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+    pr.n = 6;
+    for (int i = 0; i < 6; ++i) { pr.a[i] = a[i]; pr.b[i] = b[i]; }
+  } else {
+    const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+    pr.n = 3;
+    for (int i = 0; i < 3; ++i) { pr.a[i] = a[i]; pr.b[i] = b[i]; }
+  }
+  return pr;
+}
+
+static unsigned grid_for(long long tot) {
+  long long g = (tot + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+static void split_block_cols(sq3_ctx* ctx, const float* X, int Ns, __nv_bfloat16* out,
+                             const MixedBuffers& b) {
+  Prof p(ctx, ST_SPLIT);
+  const long long N = ctx->grid.N;
+  split_cols_kernel<float><<<grid_for(N * Ns), 256, 0, ctx->stream>>>(
+      X, N, (int)N, Ns, out, b.ldN, b.psN, MIXED_PIECES);
+}
+
+static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBuffers& b) {
+  Prof p(ctx, ST_SPLIT);
+  const long long N = ctx->grid.N;
+  dim3 grid((unsigned)((N + 31) / 32), (Ns + 31) / 32);
+  split_rows_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
+                                                           N * b.ldS, MIXED_PIECES);
+}
+
+template <typename T>
+static void split_matrix(sq3_ctx* ctx, const T* A, int Ns, __nv_bfloat16* out,
+                         const MixedBuffers& b) {
+  Prof p(ctx, ST_SPLIT);
+  split_cols_kernel<T><<<grid_for((long long)Ns * Ns), 256, 0, ctx->stream>>>(
+      A, Ns, Ns, Ns, out, b.ldS, b.psS, MIXED_PIECES);
+}
+
+static Operand op_cols(const __nv_bfloat16* base, int Ns, long long N, const MixedBuffers& b) {
+  return Operand{base, Ns, (int)N, b.ldN, b.psN, MIXED_PIECES};
+}
+static Operand op_rows(const MixedBuffers& b, long long N, int Ns) {
+  return Operand{b.rowX, (int)N, Ns, b.ldS, N * b.ldS, MIXED_PIECES};
+}
+static Operand op_mat(const __nv_bfloat16* base, int Ns, const MixedBuffers& b) {
+  return Operand{base, Ns, Ns, b.ldS, b.psS, MIXED_PIECES};
+}
+
+static int splits_for(int tiles, long long K) {
+  int want = (2 * 152 + tiles - 1) / tiles;
+  long long maxs = K / 4096;           // keep >= 4096 of K per CTA
+  if (maxs < 1) maxs = 1;
+  if (want > maxs) want = (int)maxs;
+  return want < 1 ? 1 : want;
+}
+
+// S = A^T B over the grid for two split blocks (upper tiles, mirrored).
+static int gram_mixed(sq3_ctx* ctx, const __nv_bfloat16* a, const __nv_bfloat16* bb,
+                      int Ns, double* S, const MixedBuffers& b, int stage) {
+  const long long N = ctx->grid.N;
+  int rc;
+  {
+    Prof p(ctx, stage);
+    cudaMemsetAsync(S, 0, (size_t)Ns * Ns * sizeof(double), ctx->stream);
+    TcParams t{};
+    t.tri = 1;
+    t.C64 = S;
+    t.ldc = Ns;
+    const int nt = (Ns + 127) / 128;
+    rc = tc_gemm(ctx, op_cols(a, Ns, N, b), op_cols(bb, Ns, N, b), products(MIXED_PIECES), t,
+                 EPI_TC_ATOMIC, splits_for(nt * (nt + 1) / 2, N), ctx->stream);
+  }
+  if (rc) return rc;
+  mirror_upper_f64(S, Ns, ctx->stream);
+  return SQ3_OK;
+}
+
+__global__ void add_shift_maxdiag_kernel(double* S, int n, double rel) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, S[i + (long long)i * n]);
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, sh[w]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S[i + (long long)i * n] += rel * t;
+}
+
+// Cholesky QR 2 in mixed precision.  If the first Cholesky meets a
+// non-positive pivot (the Gram matrix of an ill-conditioned filtered block
+// carries rounding errors near its smallest eigenvalues), that pass is
+// redone on S + s I with s = 1e-6 max_i S_ii (shifted Cholesky QR, Fukaya et
+// al. 2020), after which two plain passes follow.
+int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
+  const long long N = ctx->grid.N;
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  rc = ensure(&ctx->wsX, &ctx->wsX_bytes, (size_t)N * Ns * sizeof(float));
+  if (rc) return rc;
+  rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes,
+              ((size_t)2 * Ns * Ns + Ns) * sizeof(double));
+  if (rc) return rc;
+  double* S = ctx->wsMat;
+  double* Rinv = S + (size_t)Ns * Ns;
+  double* diag = Rinv + (size_t)Ns * Ns;
+  float* W = (float*)ctx->wsX;
+  bool shift_now = false, shifted = false;
+  int plain_left = 2;
+  while (plain_left > 0) {
+    split_block_cols(ctx, X, Ns, b.colX, b);
+    rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
+    if (rc) return rc;
+    if (shift_now) {
+      Prof p(ctx, ST_CHOL);
+      add_shift_maxdiag_kernel<<<1, 1024, 0, ctx->stream>>>(S, Ns, 1e-6);
+    }
+    {
+      const int panels = (Ns + 63) / 64;
+      Prof p(ctx, ST_CHOL, 3 * panels - 1);
+      rc = cholesky_lower_f64(ctx, S, Ns, diag, ctx->stream);
+    }
+    if (rc) return rc;
+    rc = check_device_status(ctx);
+    if (rc == SQ3_ENOTPD && !shifted) {
+      shifted = shift_now = true;
+      continue;
+    }
+    if (rc) return rc;
+    {
+      Prof p(ctx, ST_TRINV);
+      tri_inverse_transpose_f64(S, Rinv, Ns, ctx->stream);
+    }
+    split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
+    split_block_rows(ctx, X, Ns, b);
+    {
+      Prof p(ctx, ST_XRINV);
+      TcParams t{};
+      t.tri = 2;
+      t.C32 = W;
+      t.ldc = N;
+      t.alpha = 1.f;
+      rc = tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
+                   EPI_TC_STORE, 1, ctx->stream);
+    }
+    if (rc) return rc;
+    {
+      Prof p(ctx, ST_COPY, 0);
+      rc = cuda_err(cudaMemcpyAsync(X, W, (size_t)N * Ns * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (rc) return rc;
+    if (shift_now) shift_now = false;
+    else --plain_left;
+  }
+  return check_device_status(ctx);
+}
+
+int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs) {
+  const long long N = ctx->grid.N;
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  rc = ensure(&ctx->wsX, &ctx->wsX_bytes, (size_t)N * Ns * sizeof(float));
+  if (rc) return rc;
+  float* HX = (float*)ctx->wsX;
+  rc = hamiltonian_apply_f32(ctx, X, HX, Ns);
+  if (rc) return rc;
+  split_block_cols(ctx, X, Ns, b.colX, b);
+  split_block_cols(ctx, HX, Ns, b.colY, b);
+  return gram_mixed(ctx, b.colX, b.colY, Ns, Hs, b, ST_HS_GEMM);
+}
+
+// Recurrence of Eq. (ThreeTermRecurrenceRelation) on the tensor cores; fills
+// the FP32 T_j array (npl+1 slots) and the moments m_j (FP64).
+int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+                          const double* bounds, double* mom, float* T) {
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  const long long nn = (long long)Ns * Ns;
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    hhat_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(
+        Hs, Ns, bounds, T, T + nn, mom);
+    trace_f32_kernel<<<1, 1024, 0, ctx->stream>>>(T + nn, Ns, mom + 1);
+  }
+  split_matrix<float>(ctx, T + nn, Ns, b.matA, b);          // Hhat (A operand)
+  {
+    Prof p(ctx, ST_SPLIT);
+    cudaMemcpyAsync(b.matB, b.matA, (size_t)MIXED_PIECES * b.psS * 2,
+                    cudaMemcpyDeviceToDevice, ctx->stream);  // T_1 pieces
+  }
+  __nv_bfloat16* cur = b.matB;
+  __nv_bfloat16* nxt = b.matC;
+  Prof p(ctx, ST_CHEB_GEMM, npl > 1 ? npl - 1 : 0);
+  for (int j = 1; j < npl; ++j) {
+    TcParams t{};
+    t.C32 = T + (long long)(j + 1) * nn;
+    t.ldc = Ns;
+    t.Tprev = T + (long long)(j - 1) * nn;
+    t.Bnext = nxt;
+    t.ld_next = b.ldS;
+    t.next_piece_stride = b.psS;
+    t.next_pieces = MIXED_PIECES;
+    t.trace = mom + j + 1;
+    rc = tc_gemm(ctx, op_mat(b.matA, Ns, b), op_mat(cur, Ns, b), products(MIXED_PIECES), t,
+                 EPI_TC_CHEB, 1, ctx->stream);
+    if (rc) return rc;
+    __nv_bfloat16* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  return SQ3_OK;
+}
+
+void accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, const double* coef,
+                        double* D) {
+  const long long nn = (long long)Ns * Ns;
+  accumulate_d_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(
+      T, nn, Ns, npl, coef, D);
+}
+
+int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double* rho) {
+  const long long N = ctx->grid.N;
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  split_matrix<double>(ctx, D, Ns, b.matA, b);
+  split_block_rows(ctx, X, Ns, b);
+  Prof p(ctx, ST_RHO);
+  cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), ctx->stream);
+  TcParams t{};
+  t.X = X;
+  t.ldx = N;
+  t.rho = rho;
+  t.rho_alpha = 2.0 / ctx->dV;
+  return tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
+                 EPI_TC_RHO, 1, ctx->stream);
+}
+
+}  // namespace sq3

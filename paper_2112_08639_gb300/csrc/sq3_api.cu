@@ -134,6 +134,10 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   return cuda_err(cudaGetLastError());
 }
 
+int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns) {
+  return hamiltonian_apply_t<float>(ctx, X, Y, Ns);
+}
+
 // Scaled three-term recurrence of the Chebyshev filter (Zhou et al. 2006):
 // with x = (t - c)/e and rho_k = T_k((a0 - c)/e), Y_k = T_k(x) X / rho_k obeys
 // Y_1 = (s_1/e)(H - c) X and Y_{k+1} = (2 s_{k+1}/e)(H - c) Y_k
@@ -509,12 +513,8 @@ int sq3_orthonormalise(sq3_ctx* c, void* X, int Ns, sq3_prec prec) {
   cudaSetDevice(c->device);
   int rc;
   if (prec == SQ3_FP64) rc = orthonormalise_f64(c, (double*)X, Ns);
-  else if (prec == SQ3_MIXED) {
-    rc = SQ3_EINVAL;
-#ifdef SQ3_HAVE_MIXED
-    rc = orthonormalise_mixed(c, (float*)X, Ns);
-#endif
-  } else return SQ3_EINVAL;
+  else if (prec == SQ3_MIXED) rc = orthonormalise_mixed(c, (float*)X, Ns);
+  else return SQ3_EINVAL;
   return finish(c, rc);
 }
 
@@ -524,20 +524,23 @@ int sq3_project(sq3_ctx* c, const void* X, int Ns, sq3_prec prec, double* Hs) {
   cudaSetDevice(c->device);
   int rc;
   if (prec == SQ3_FP64) rc = project_f64(c, (const double*)X, Ns, Hs);
+  else if (prec == SQ3_MIXED) rc = project_mixed(c, (const float*)X, Ns, Hs);
   else return SQ3_EINVAL;
   return finish(c, rc);
 }
 
 int sq3_kernel_from_hs(sq3_ctx* c, const double* Hs, int Ns, int npl,
-                       double kT, double Ne, const double* bounds_in,
-                       double* D, double* out) {
+                       double kT, double Ne, sq3_prec prec,
+                       const double* bounds_in, double* D, double* out) {
   if (!c) return SQ3_EINVAL;
   if (!Hs || !out || Ns <= 0 || npl < 1 || npl > SQ3_MAX_NPL || !(kT > 0) ||
       !(Ne > 0) || !(Ne < 2.0 * Ns))
     return SQ3_EINVAL;
   if (bounds_in && !(bounds_in[1] > 0)) return SQ3_EINVAL;
+  if (prec != SQ3_FP64 && prec != SQ3_MIXED) return SQ3_EINVAL;
   cudaSetDevice(c->device);
-  int rc = density_kernel_from_hs_f64(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out);
+  int rc = density_kernel_from_hs(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out,
+                                  prec == SQ3_MIXED);
   return finish(c, rc);
 }
 
@@ -556,7 +559,7 @@ int sq3_density_kernel(sq3_ctx* c, const void* X, int Ns, int npl, double kT,
   }
   rc = sq3_project(c, X, Ns, prec, Hs);
   if (rc) return rc;
-  return sq3_kernel_from_hs(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out);
+  return sq3_kernel_from_hs(c, Hs, Ns, npl, kT, Ne, prec, bounds_in, D, out);
 }
 
 int sq3_profile_enable(sq3_ctx* c, int enable) {
@@ -594,6 +597,7 @@ int sq3_density(sq3_ctx* c, const void* X, const double* D, int Ns,
   cudaSetDevice(c->device);
   int rc;
   if (prec == SQ3_FP64) rc = density_f64(c, (const double*)X, D, Ns, rho);
+  else if (prec == SQ3_MIXED) rc = density_mixed(c, (const float*)X, D, Ns, rho);
   else return SQ3_EINVAL;
   return finish(c, rc);
 }

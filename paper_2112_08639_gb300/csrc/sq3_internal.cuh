@@ -12,6 +12,8 @@
 #define SQ3_MAX_FD_RADIUS 6
 #define SQ3_MAX_NPL 700
 #define SQ3_DEV_SCAL 2304
+// bf16 pieces per FP32 operand in the mixed path (3 pieces, 6 products)
+#define MIXED_PIECES 3
 
 namespace sq3 {
 
@@ -155,17 +157,19 @@ void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st);
 
 // ---- Chebyshev Fermi-operator expansion (foe.cu) ----
-int density_kernel_from_hs_f64(sq3_ctx* ctx, const double* Hs, int Ns,
-                               int npl, double sigma, double Ne,
-                               const double* bounds_in, double* D,
-                               double* out_host);
+int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+                           double sigma, double Ne, const double* bounds_in,
+                           double* D, double* out_host, bool mixed);
 
 // ---- mixed-precision path (mixed.cu) ----
-int mixed_gram(sq3_ctx* ctx, const float* X, const float* Y, int Ns,
-               double* S);
-int mixed_times_upper(sq3_ctx* ctx, const float* X, const double* R, int Ns,
-                      float* out);
-int mixed_rho(sq3_ctx* ctx, const float* X, const double* D, int Ns,
-              double* rho);
+int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns);
+int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns);
+int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs);
+int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+                          const double* bounds, double* mom, float* T);
+void accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl,
+                        const double* coef, double* D);
+int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns,
+                  double* rho);
 
 }  // namespace sq3

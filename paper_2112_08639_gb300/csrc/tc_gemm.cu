@@ -1,0 +1,409 @@
+// tcgen05 (5th-generation tensor core) GEMM on BF16 split operands for the
+// mixed-precision path.
+//
+// Every FP32 operand x is carried as P bf16 pieces, x ~ x_0 + x_1 (+ x_2),
+// x_0 = bf16(x), x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1) (round to
+// nearest even).  A product A B is then a short sum of piece products
+// sum_(p,q) A_p B_q, each issued as tcgen05.mma kind::f16 with BF16 inputs
+// and FP32 accumulation in tensor memory (TMEM).
+//
+// Tile: 128 x 128 output, K stepped by 64 (one 128-byte swizzle row of
+// bf16).  Operands are K-major; each stage holds all pieces of a 128 x 64 A
+// tile and a 128 x 64 B tile, loaded by one 3-D TMA copy per operand with
+// 128-byte swizzle.  One thread issues the TMA copies and the MMAs; a
+// multi-stage mbarrier ring overlaps the copies of later K-blocks with the
+// MMAs of the current one.  The accumulator (128 lanes x 128 FP32 columns)
+// is read back by four warps with tcgen05.ld, each warp owning 32 rows, and
+// fed to a fused epilogue:
+//   EPI_TC_ATOMIC  C(m,n) += acc (FP64 atomics; split-K Gram and X^T (H X))
+//   EPI_TC_STORE   C(m,n)  = alpha acc (FP32)
+//   EPI_TC_CHEB    T_{j+1} = 2 acc - T_{j-1}; stores T_{j+1} (FP32), its bf16
+//                  pieces for the next product, and its trace
+//   EPI_TC_RHO     rho(m) += alpha sum_n X(m,n) acc(m,n)   (FP64 atomics)
+// Every mbarrier wait is bounded (about one second of wall time); on
+// timeout the kernel records DEV_TIMEOUT, drains its outstanding copies with
+// the same bound, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "sq3_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace sq3 {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int TILE_BYTES = 128 * BK * 2;          // one piece of a 128 x 64 tile
+constexpr int SMEM_BUDGET = 196608;               // bytes of tile stages
+constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map,
+                                            uint32_t bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), version 1, base offset 0.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused, SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
+// N = BN, M = BM.
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+        "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+        "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long long e,
+                                            long long piece_stride, int pieces) {
+  __nv_bfloat16 h = __float2bfloat16_rn(t);
+  out[e] = h;
+  if (pieces > 1) {
+    const float r1 = t - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    out[e + piece_stride] = l;
+    if (pieces > 2) out[e + 2 * piece_stride] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+  }
+}
+
+template <int PA, int PB, int EPI>
+__global__ void __launch_bounds__(128, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+               const __grid_constant__ CUtensorMap mapB, TcParams p) {
+  constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
+  constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
+  __shared__ uint32_t tmem_slot;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.y, nt = blockIdx.x;
+  const int m0 = mt * BM, n0 = nt * BN;
+  if (p.tri == 1 && nt < mt) return;   // symmetric output: upper tiles only
+
+  // K range of this CTA
+  const int Keff = (p.tri == 2) ? min(p.K, n0 + BN) : p.K;
+  int kchunk = (Keff + (int)gridDim.z - 1) / (int)gridDim.z;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(Keff, kbeg + kchunk);
+  const int nk = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t full0 = smem_u32(&bars[0]);
+  const uint32_t empty0 = smem_u32(&bars[STAGES]);
+  const uint32_t done = smem_u32(&bars[2 * STAGES]);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  __shared__ int failed;
+  if (threadIdx.x == 0) failed = 0;
+  __syncthreads();
+
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16();
+    int issued = 0;      // K-blocks whose copies were issued
+    bool ok = true;
+    auto issue = [&](int kb) {
+      const int s = kb % STAGES;
+      const uint32_t sa = base + s * STAGE_BYTES;
+      const uint32_t sb = sa + PA * TILE_BYTES;
+      const uint32_t fb = full0 + 8 * s;
+      mbar_expect_tx(fb, STAGE_BYTES);
+      tma_load_3d(sa, &mapA, fb, kbeg + kb * BK, m0, 0);
+      tma_load_3d(sb, &mapB, fb, kbeg + kb * BK, n0, 0);
+    };
+    for (; issued < nk && issued < STAGES; ++issued) issue(issued);
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + s * STAGE_BYTES;
+      const uint32_t sb = sa + PA * TILE_BYTES;
+      for (int q = 0; q < p.nprod; ++q) {
+        const uint32_t pa = sa + p.prod_a[q] * TILE_BYTES;
+        const uint32_t pb = sb + p.prod_b[q] * TILE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || q > 0 || kk > 0) ? 1u : 0u;
+          mma_bf16(tmem, sw128_desc(pa + kk * 32), sw128_desc(pb + kk * 32), idesc, acc);
+        }
+      }
+      mma_commit(empty0 + 8 * s);
+      // refill the stage consumed one step earlier once its MMAs are done
+      if (kb >= 1 && issued < nk) {
+        const int sp = (kb - 1) % STAGES;
+        if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / STAGES) & 1)) { ok = false; break; }
+        issue(issued);
+        ++issued;
+      }
+    }
+    if (ok) {
+      mma_commit(done);
+    } else {
+      failed = 1;
+      atomicCAS(p.status, 0, DEV_TIMEOUT);
+      // drain: the last copy issued into each stage must land before the CTA
+      // exits (each wait bounded)
+      for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
+        mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  bool have = (failed == 0) && nk > 0;
+  if (have) {
+    if (!mbar_wait(done, 0)) {
+      atomicCAS(p.status, 0, DEV_TIMEOUT);
+      have = false;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // ---------------- epilogue: warp w owns rows m0 + 32 w .. + 31 ----------
+  const int m = m0 + warp * 32 + lane;
+  const bool mrow = m < p.M;
+  double rsum = 0.0;
+  if (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      if (have) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (!mrow) continue;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int n = n0 + c0 + i;
+        if (n >= p.N) continue;
+        const long long e = (long long)m + (long long)n * p.ldc;
+        if (EPI == EPI_TC_ATOMIC) {
+          atomicAdd(p.C64 + e, (double)v[i]);
+        } else if (EPI == EPI_TC_STORE) {
+          p.C32[e] = p.alpha * v[i];
+        } else if (EPI == EPI_TC_CHEB) {
+          const float t = 2.f * v[i] - p.Tprev[e];
+          p.C32[e] = t;
+          split_store(t, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
+                      p.next_pieces);
+          if (m == n) atomicAdd(p.trace, (double)t);
+        } else {  // EPI_TC_RHO
+          rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * (double)v[i];
+        }
+      }
+    }
+  }
+  if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(BN));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static int make_map(CUtensorMap* map, const Operand& o, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return SQ3_ECUDA;
+  if (((uintptr_t)o.base & 15) || (o.ld * 2) % 16 || (o.piece_stride * 2) % 16)
+    return SQ3_EINVAL;
+  cuuint64_t dims[3] = {(cuuint64_t)o.K, (cuuint64_t)o.rows, (cuuint64_t)o.pieces};
+  cuuint64_t strides[2] = {(cuuint64_t)o.ld * 2, (cuuint64_t)o.piece_stride * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)o.pieces};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)o.base, dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SQ3_OK : SQ3_ECUDA;
+}
+
+template <int PA, int PB, int EPI>
+static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p,
+                    dim3 grid, cudaStream_t st) {
+  constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
+  constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
+  const int smem = STAGES * STAGE_BYTES + 1024;
+  auto k = tc_gemm_kernel<PA, PB, EPI>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+      return SQ3_ECUDA;
+    attr = true;
+  }
+  k<<<grid, 128, smem, st>>>(a, b, p);
+  return cuda_err(cudaGetLastError());
+}
+
+template <int EPI>
+static int launch_e(int PA, int PB, const CUtensorMap& a, const CUtensorMap& b,
+                    const TcParams& p, dim3 grid, cudaStream_t st) {
+  if (PA == 2 && PB == 2) return launch_t<2, 2, EPI>(a, b, p, grid, st);
+  if (PA == 3 && PB == 3) return launch_t<3, 3, EPI>(a, b, p, grid, st);
+  return SQ3_EINVAL;
+}
+
+}  // namespace tc
+
+int tc_gemm(sq3_ctx* ctx, const Operand& A, const Operand& B, const Products& pr,
+            TcParams p, int epi, int splits, cudaStream_t st) {
+  using namespace tc;
+  if (A.K != B.K || A.pieces != B.pieces || pr.n < 1 || pr.n > 6) return SQ3_EINVAL;
+  for (int i = 0; i < pr.n; ++i) {
+    if (pr.a[i] >= A.pieces || pr.b[i] >= B.pieces) return SQ3_EINVAL;
+    p.prod_a[i] = pr.a[i];
+    p.prod_b[i] = pr.b[i];
+  }
+  p.nprod = pr.n;
+  p.M = A.rows;
+  p.N = B.rows;
+  p.K = A.K;
+  p.status = ctx->dev_status;
+  CUtensorMap ma, mb;
+  int rc = make_map(&ma, A, BM);
+  if (rc) return rc;
+  rc = make_map(&mb, B, BN);
+  if (rc) return rc;
+  if (splits < 1) splits = 1;
+  dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, splits);
+  switch (epi) {
+    case EPI_TC_ATOMIC: return launch_e<EPI_TC_ATOMIC>(A.pieces, B.pieces, ma, mb, p, grid, st);
+    case EPI_TC_STORE: return launch_e<EPI_TC_STORE>(A.pieces, B.pieces, ma, mb, p, grid, st);
+    case EPI_TC_CHEB: return launch_e<EPI_TC_CHEB>(A.pieces, B.pieces, ma, mb, p, grid, st);
+    case EPI_TC_RHO: return launch_e<EPI_TC_RHO>(A.pieces, B.pieces, ma, mb, p, grid, st);
+  }
+  return SQ3_EINVAL;
+}
+
+}  // namespace sq3

@@ -41,7 +41,7 @@ _sigs = {
     "sq3_cheb_filter": (_i, [_p, _p, _i, _i, _d, _d, _d, _i]),
     "sq3_orthonormalise": (_i, [_p, _p, _i, _i]),
     "sq3_project": (_i, [_p, _p, _i, _i, _p]),
-    "sq3_kernel_from_hs": (_i, [_p, _p, _i, _i, _d, _d, _p, _p, _p]),
+    "sq3_kernel_from_hs": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p]),
     "sq3_density_kernel": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p, _p]),
     "sq3_density": (_i, [_p, _p, _p, _i, _i, _p]),
     "sq3_status_string": (ctypes.c_char_p, [_i]),
@@ -153,13 +153,13 @@ class Context:
                 "xi": out[4], "two_tr_D": out[5]}
 
     def kernel_from_hs(self, Hs: torch.Tensor, npl: int, kT: float, Ne: float,
-                       bounds=None, D: torch.Tensor | None = None, want_D=True):
+                       bounds=None, D: torch.Tensor | None = None, want_D=True, prec=FP64):
         Ns = Hs.shape[0]
         if D is None and want_D:
             D = torch.empty((Ns, Ns), dtype=torch.float64, device=self.device)
         out = (ctypes.c_double * 6)()
         b = (ctypes.c_double * 2)(*bounds) if bounds is not None else None
-        _check(lib.sq3_kernel_from_hs(self._h, _ptr(Hs), Ns, npl, kT, Ne, b, _ptr(D), out),
+        _check(lib.sq3_kernel_from_hs(self._h, _ptr(Hs), Ns, npl, kT, Ne, prec, b, _ptr(D), out),
                "sq3_kernel_from_hs")
         return D, self._unpack(out)
 
