@@ -76,19 +76,19 @@ __device__ double bsum(double v, double* sh) {
   return s;
 }
 
-// One CTA: quadrature weights, bisection for mu, coefficients, energies.
-// out[0..5] = mu, E_band, E_ent, chi, xi, 2 sum' c_j m_j ; coef[0..npl] = c_j
+// One CTA: moment-weighted node sums w_k = sum'_j m_j T_j(x_k), bisection for
+// mu on 2 (2/M) sum_k g(xi x_k + chi; mu) w_k = Ne, then the three functions
+// at the nodes for the coefficient kernel.
+// out[0] = mu, out[3] = chi, out[4] = xi; fvals[0..3M) = g, eps g, entropy.
 __global__ void __launch_bounds__(1024)
-fermi_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
-             double Ne, int n, const double* bounds, double* coef, double* out,
-             int* status) {
+fermi_level_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
+                   double Ne, int n, const double* bounds, double* fvals, double* out,
+                   int* status) {
   extern __shared__ double smem[];
-  double* wq = smem;            // M   : w_k = sum'_j m_j T_j(x_k)
-  double* xk = smem + M;        // M   : nodes cos(theta_k)
-  double* f = smem + 2 * M;     // 3M  : g, eps*g, entropy at nodes
+  double* wq = smem;            // M : w_k
+  double* xk = smem + M;        // M : nodes cos(theta_k)
   __shared__ double sh[32];
   const double chi = bounds[0], xi = bounds[1];
-  const double PI = 3.14159265358979323846;
 
   // moment sanity: |tr T_j| <= n unless the spectrum left [-1, 1]
   for (int j = threadIdx.x; j <= npl; j += blockDim.x) {
@@ -97,7 +97,7 @@ fermi_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
     else if (fabs(mj) > n * (1.0 + 1e-6)) atomicCAS(status, 0, DEV_NOCONV);
   }
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    const double x = cos((k + 0.5) * PI / M);
+    const double x = cospi((2.0 * k + 1.0) / (2.0 * M));
     xk[k] = x;
     double tp = 1.0, t = x;                  // T_0, T_1 at x
     double acc = 0.5 * moments[0] + (npl >= 1 ? moments[1] * x : 0.0);
@@ -129,46 +129,70 @@ fermi_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
     if (cm < Ne) lo = mid; else hi = mid;
   }
   const double mu = 0.5 * (lo + hi);
-
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     const double eps = xi * xk[k] + chi;
     const double g = fermi_dev(eps, mu, sigma);
-    f[k] = g;
-    f[M + k] = eps * g;
-    f[2 * M + k] = entropy_dev(eps, mu, sigma);
+    fvals[k] = g;
+    fvals[M + k] = eps * g;
+    fvals[2 * M + k] = entropy_dev(eps, mu, sigma);
   }
-  __syncthreads();
-  // c_j, d_j, e_j: (2/M) sum_k f(x_k) cos(j theta_k); accumulate the primed
-  // moment sums of the three series at the same time.
-  double sc = 0.0, sd = 0.0, se = 0.0;
-  for (int j = threadIdx.x; j <= npl; j += blockDim.x) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int k = 0; k < M; ++k) {
-      const double cj = cos(j * ((k + 0.5) * PI / M));
-      a += f[k] * cj;
-      b += f[M + k] * cj;
-      c += f[2 * M + k] * cj;
-    }
+  if (threadIdx.x == 0) {
+    out[0] = mu;
+    out[3] = chi;
+    out[4] = xi;
+    if (!isfinite(mu)) atomicCAS(status, 0, DEV_NONFINITE);
+  }
+}
+
+// One warp per degree j: c_j, d_j, e_j = (2/M) sum_k f(x_k) cos(j theta_k)
+// for the three functions, with cos(j theta_k) = cospi(j (2k+1) / (2M))
+// evaluated after reducing the integer j (2k+1) modulo 4M.  Writes c_j and
+// the primed products with the moments into terms[3][npl+1].
+__global__ void __launch_bounds__(256)
+cheb_coeff_kernel(const double* __restrict__ fvals, const double* __restrict__ moments,
+                  int npl, int M, double* coef, double* terms) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j > npl) return;
+  double a = 0.0, b = 0.0, c = 0.0;
+  const long long fourM = 4LL * M;
+  for (int k = lane; k < M; k += 32) {
+    const long long q = ((long long)j * (2 * k + 1)) % fourM;
+    const double cj = cospi((double)q / (2.0 * M));
+    a += fvals[k] * cj;
+    b += fvals[M + k] * cj;
+    c += fvals[2 * M + k] * cj;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) {
     a *= 2.0 / M; b *= 2.0 / M; c *= 2.0 / M;
     coef[j] = a;
     const double wgt = (j == 0) ? 0.5 : 1.0;
-    sc += wgt * a * moments[j];
-    sd += wgt * b * moments[j];
-    se += wgt * c * moments[j];
+    terms[j] = wgt * a * moments[j];
+    terms[(npl + 1) + j] = wgt * b * moments[j];
+    terms[2 * (npl + 1) + j] = wgt * c * moments[j];
   }
-  sc = bsum(sc, sh);
-  sd = bsum(sd, sh);
-  se = bsum(se, sh);
-  if (threadIdx.x == 0) {
-    out[0] = mu;
-    out[1] = 2.0 * sd;
-    out[2] = 2.0 * sigma * se;
-    out[3] = chi;
-    out[4] = xi;
-    out[5] = 2.0 * sc;
-    if (!isfinite(mu) || !isfinite(sd) || !isfinite(se))
-      atomicCAS(status, 0, DEV_NONFINITE);
+}
+
+// In-order sums of the primed series: out[1] = E_band, out[2] = E_ent,
+// out[5] = 2 sum'_j c_j m_j.
+__global__ void fermi_finish_kernel(const double* __restrict__ terms, int npl, double sigma,
+                                    double* out, int* status) {
+  if (threadIdx.x != 0) return;
+  double sc = 0.0, sd = 0.0, se = 0.0;
+  for (int j = 0; j <= npl; ++j) {
+    sc += terms[j];
+    sd += terms[(npl + 1) + j];
+    se += terms[2 * (npl + 1) + j];
   }
+  out[1] = 2.0 * sd;
+  out[2] = 2.0 * sigma * se;
+  out[5] = 2.0 * sc;
+  if (!isfinite(sd) || !isfinite(se) || !isfinite(sc)) atomicCAS(status, 0, DEV_NONFINITE);
 }
 
 // Ds = c_0/2 I + sum_{j>=1} c_j T_j over the stored T_j.
@@ -240,13 +264,22 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   }
   }
   const int M = (8 * (npl + 1) > 1024) ? 8 * (npl + 1) : 1024;
-  size_t smem = (size_t)5 * M * sizeof(double);
-  cudaFuncSetAttribute(fermi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
+  rc = ensure((void**)&ctx->wsFoe, &ctx->wsFoe_bytes,
+              ((size_t)3 * M + 3 * (npl + 1)) * sizeof(double));
+  if (rc) return rc;
+  double* fvals = ctx->wsFoe;
+  double* terms = fvals + 3 * M;
+  size_t smem = (size_t)2 * M * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(fermi_level_kernel,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   {
-    Prof p(ctx, ST_FERMI);
-    fermi_kernel<<<1, 1024, smem, st>>>(mom, npl, M, sigma, Ne, Ns, bounds,
-                                        coef, outd, ctx->dev_status);
+    Prof p(ctx, ST_FERMI, 3);
+    fermi_level_kernel<<<1, 1024, smem, st>>>(mom, npl, M, sigma, Ne, Ns, bounds,
+                                              fvals, outd, ctx->dev_status);
+    cheb_coeff_kernel<<<(npl + 1 + 7) / 8, 256, 0, st>>>(fvals, mom, npl, M, coef,
+                                                         terms);
+    fermi_finish_kernel<<<1, 32, 0, st>>>(terms, npl, sigma, outd, ctx->dev_status);
   }
   Prof pd(ctx, ST_D_ACCUM, D != nullptr ? 1 : 0);
   if (D != nullptr && mixed)

@@ -228,11 +228,18 @@ symv_kernel(const double* __restrict__ Hs, const double* __restrict__ v,
   if (lane == 0) w[warp] = s;
 }
 
+// One Lanczos step after w = Hs v_j: alpha_j, three-term update, full
+// reorthogonalisation against v_0..v_j (two classical Gram-Schmidt passes,
+// all projections of a pass computed at once, one warp per basis vector),
+// beta_j and v_{j+1}.
 __global__ void __launch_bounds__(1024)
 lanczos_update_kernel(double* V, double* w, double* alpha, double* beta,
                       double* kcount, int n, int j) {
   __shared__ double sh[32];
+  __shared__ double h[64];
   if (kcount[0] < j) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
   const double* vj = V + (long long)j * n;
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a += w[i] * vj[i];
@@ -244,14 +251,20 @@ lanczos_update_kernel(double* V, double* w, double* alpha, double* beta,
   }
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
-    for (int t = 0; t <= j; ++t) {
+    for (int t = warp; t <= j; t += nw) {
       const double* vt = V + (long long)t * n;
-      double h = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) h += vt[i] * w[i];
-      h = block_sum(h, sh);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] -= h * vt[i];
-      __syncthreads();
+      double d = 0.0;
+      for (int i = lane; i < n; i += 32) d += vt[i] * w[i];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) h[t] = d;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double t = w[i];
+      for (int q = 0; q <= j; ++q) t -= h[q] * V[(long long)q * n + i];
+      w[i] = t;
+    }
+    __syncthreads();
   }
   double b = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) b += w[i] * w[i];
@@ -299,9 +312,28 @@ __device__ double last_component(const double* al, const double* be, int k,
   return r > 1.0 ? 1.0 : r;
 }
 
+// Extremal eigenvalue of the tridiagonal by multisection: 32 lanes test 32
+// interior points per round, shrinking the bracket 33-fold.  `target` is the
+// number of eigenvalues that must lie below the returned point's right end:
+// 1 for the smallest, k for the largest.
+__device__ double multisect(const double* al, const double* be, int k, double lo,
+                            double hi, int target) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 40; ++it) {
+    const double x = lo + (hi - lo) * (lane + 1) / 33.0;
+    const bool ge = sturm_count(al, be, k, x) >= target;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    const int first = m ? __ffs(m) - 1 : 32;       // first lane with count >= target
+    const double nlo = first == 0 ? lo : lo + (hi - lo) * first / 33.0;
+    const double nhi = first == 32 ? hi : lo + (hi - lo) * (first + 1) / 33.0;
+    if (!(nhi - nlo < hi - lo)) break;
+    lo = nlo; hi = nhi;
+  }
+  return 0.5 * (lo + hi);
+}
+
 __global__ void lanczos_finish_kernel(const double* alpha, const double* beta,
                                       const double* kcount, double* bounds) {
-  if (threadIdx.x != 0) return;
   const bool terminated = kcount[0] < 0;
   const int k = (int)fabs(kcount[0]);
   double lo = 1e300, hi = -1e300;
@@ -310,23 +342,9 @@ __global__ void lanczos_finish_kernel(const double* alpha, const double* beta,
     lo = fmin(lo, alpha[i] - r);
     hi = fmax(hi, alpha[i] + r);
   }
-  double tmin, tmax;
-  {
-    double a = lo, b = hi;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (a + b);
-      if (mid <= a || mid >= b) break;
-      if (sturm_count(alpha, beta, k, mid) >= 1) b = mid; else a = mid;
-    }
-    tmin = 0.5 * (a + b);
-    a = lo; b = hi;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (a + b);
-      if (mid <= a || mid >= b) break;
-      if (sturm_count(alpha, beta, k, mid) >= k) b = mid; else a = mid;
-    }
-    tmax = 0.5 * (a + b);
-  }
+  const double tmin = multisect(alpha, beta, k, lo, hi, 1);
+  const double tmax = multisect(alpha, beta, k, lo, hi, k);
+  if (threadIdx.x != 0) return;
   double bk = terminated ? 0.0 : fabs(beta[k - 1]);
   double rmin = bk * last_component(alpha, beta, k, tmin);
   double rmax = bk * last_component(alpha, beta, k, tmax);

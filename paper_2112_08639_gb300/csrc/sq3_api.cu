@@ -107,13 +107,15 @@ static int upload(T** dst, const T* src, size_t n) {
 
 static int elem_size(sq3_prec p) { return p == SQ3_FP64 ? 8 : 4; }
 
-// gC workspace for the nonlocal projection of one block.
-static int gc_buffer(sq3_ctx* ctx, int Ns, void** out) {
+// Two gC workspaces (current and next step) for the nonlocal projections.
+static int gc_buffer(sq3_ctx* ctx, int Ns, void** out, void** out2 = nullptr) {
   *out = nullptr;
+  if (out2) *out2 = nullptr;
   if (ctx->proj.n_proj == 0) return SQ3_OK;
-  int rc = ensure((void**)&ctx->wsProj, &ctx->wsProj_bytes,
-                  (size_t)ctx->proj.n_proj * Ns * sizeof(double));
+  const size_t one = (size_t)ctx->proj.n_proj * Ns * sizeof(double);
+  int rc = ensure((void**)&ctx->wsProj, &ctx->wsProj_bytes, 2 * one);
   *out = ctx->wsProj;
+  if (out2) *out2 = (char*)ctx->wsProj + one;
   return rc;
 }
 
@@ -128,8 +130,8 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   }
   {
     Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, Y, (const T*)gC, Ns, 1.0, 0.0, 0.0,
-                        ctx->stream);
+    launch_cheb_step<T>(ctx, X, nullptr, Y, (const T*)gC, nullptr, Ns, 1.0,
+                        0.0, 0.0, ctx->stream);
   }
   return cuda_err(cudaGetLastError());
 }
@@ -148,9 +150,12 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
-  void* gC;
-  rc = gc_buffer(ctx, Ns, &gC);
+  void *gA, *gB;
+  rc = gc_buffer(ctx, Ns, &gA, &gB);
   if (rc) return rc;
+  T* gC = (T*)gA;        // projections of the current iterate
+  T* gN = (T*)gB;        // projections of the step's output
+  const size_t gbytes = (size_t)ctx->proj.n_proj * Ns * sizeof(T);
   T* W = (T*)ctx->wsX;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   const double s1 = e / (a0 - c);
@@ -161,24 +166,27 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   const bool nl = ctx->proj.n_proj > 0;
   if (nl) {
     Prof p(ctx, ST_NL_PROJECT);
-    launch_nl_project<T>(ctx, X, (T*)gC, Ns, ctx->stream);
+    launch_nl_project<T>(ctx, X, gC, Ns, ctx->stream);
+    if (m > 1) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
   }
   {
     Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, W, (const T*)gC, Ns, s1 / e, c, 0.0,
-                        ctx->stream);
+    launch_cheb_step<T>(ctx, X, nullptr, W, gC, (nl && m > 1) ? gN : nullptr,
+                        Ns, s1 / e, c, 0.0, ctx->stream);
   }
   for (int k = 2; k <= m; ++k) {
     const double sn = 1.0 / (tau - s);
+    const bool want_next = nl && k < m;
     if (nl) {
-      Prof p(ctx, ST_NL_PROJECT);
-      launch_nl_project<T>(ctx, cur, (T*)gC, Ns, ctx->stream);
+      std::swap(gC, gN);
+      if (want_next) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
     }
     {
-      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev)
+      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev);
+      // the step also accumulates the projections of Y_k for step k+1
       Prof p(ctx, ST_STENCIL);
-      launch_cheb_step<T>(ctx, cur, prev, prev, (const T*)gC, Ns,
-                          2.0 * sn / e, c, -s * sn, ctx->stream);
+      launch_cheb_step<T>(ctx, cur, prev, prev, gC, want_next ? gN : nullptr,
+                          Ns, 2.0 * sn / e, c, -s * sn, ctx->stream);
     }
     std::swap(cur, prev);
     s = sn;
@@ -359,7 +367,7 @@ void sq3_destroy(sq3_ctx* c) {
   for (auto& r : c->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
-                  c->wsMat, c->wsT, c->wsProj, c->wsSplit};
+                  c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   delete c;

@@ -10,7 +10,7 @@
 #include "../../include/sq3.h"
 
 #define SQ3_MAX_FD_RADIUS 6
-#define SQ3_MAX_NPL 700
+#define SQ3_MAX_NPL 1000
 #define SQ3_DEV_SCAL 2304
 // bf16 pieces per FP32 operand in the mixed path (3 pieces, 6 products)
 #define MIXED_PIECES 3
@@ -96,6 +96,7 @@ struct sq3_ctx {
   double* wsT = nullptr; size_t wsT_bytes = 0;      // stored T_j
   double* wsProj = nullptr; size_t wsProj_bytes = 0;  // projection coeffs
   void* wsSplit = nullptr; size_t wsSplit_bytes = 0;  // bf16 split operands
+  double* wsFoe = nullptr; size_t wsFoe_bytes = 0;    // quadrature node values
 };
 
 namespace sq3 {
@@ -115,12 +116,13 @@ int check_device_status(sq3_ctx* ctx);
 
 // ---- stencil / Hamiltonian (stencil.cu) ----
 // out = s1 * (H y - c y) + s2 * yprev, per vector, for Ns vectors.
-// gC: n_proj x Ns projection coefficients gamma_p c_p^T y (may be null when
-// there are no projectors).  yprev may alias out.
+// gC: projection coefficients gC[v * n_proj + p] = gamma_p c_p^T y_v (null
+// when there are no projectors).  gC_next (may be null): zero-initialised
+// array that receives the same coefficients of `out`.  yprev may alias out.
 template <typename T>
 void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                      const T* gC, int Ns, double s1, double c, double s2,
-                      cudaStream_t st);
+                      const T* gC, T* gC_next, int Ns, double s1, double c,
+                      double s2, cudaStream_t st);
 // gC[vec * n_proj + p] = gamma_p * sum_k c_p[k] y[k + vec*N]
 template <typename T>
 void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,

@@ -19,6 +19,8 @@
 // tile's y-halo; yprev, V and out stream once.  The nonlocal term is added
 // from a per-point table of (projector, c_p[k]) and the precomputed
 // coefficients gC = gamma (c^T y) of the same vector.
+#include <stdlib.h>
+
 #include "sq3_internal.cuh"
 
 namespace sq3 {
@@ -31,15 +33,24 @@ struct StepCoef {
   T az[SQ3_MAX_FD_RADIUS + 1];
 };
 
-template <typename T, int R>
+// VB vectors per CTA share the (x, y) tile: the potential, the per-point
+// projector entries and the index arithmetic are loaded once for all VB.
+// With gC_next non-null the kernel also accumulates the projections of its
+// own output, gC_next[v][p] += gamma_p sum_k c_p[k] out_v[k] (per-CTA partial
+// sums in shared memory, one global atomic per projector and vector), so the
+// next filter step needs no separate gather over the block.
+template <typename T, int R, int VB>
 __global__ void __launch_bounds__(1024)
-cheb_step_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
+cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
                  const T* __restrict__ y, const T* yprev, T* out,
                  const T* __restrict__ V, const T* __restrict__ gC,
                  const int* __restrict__ pt_ptr, const int* __restrict__ pt_proj,
-                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2) {
+                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2,
+                 T* gC_next, const double* __restrict__ gamma) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);          // (TY + 2R) x nx
+  const int rows = TY + 2 * R;
+  T* sm = reinterpret_cast<T*>(smem_raw);           // VB planes, rows x nx each
+  T* pacc = sm + (size_t)VB * rows * nx;             // n_proj x VB partial sums
   const int tid = threadIdx.x;
   const int x = tid % nx;
   const int ty = tid / nx;
@@ -48,96 +59,164 @@ cheb_step_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
   const bool active = (ty < TY) && (yy < ny);
   const long long N = (long long)nx * ny * nz;
   const long long plane = (long long)nx * ny;
-  const long long vbase = (long long)blockIdx.y * N;
-  const T* yv = y + vbase;
-  const int col = yy * nx + x;                      // offset inside a plane
+  const int v0 = blockIdx.y * VB;
+  const int nv = min(VB, Ns - v0);
+  const int col = yy * nx + x;
   const int halo_elems = 2 * R * nx;
-  const int rows = TY + 2 * R;
+  const bool proj_out = gC_next != nullptr;
+  if (proj_out)
+    for (int i = tid; i < n_proj * VB; i += blockDim.x) pacc[i] = T(0);
 
-  T q[2 * R + 1];
+  T q[VB][2 * R + 1];
 #pragma unroll
-  for (int i = 0; i < 2 * R + 1; ++i) q[i] = T(0);
+  for (int v = 0; v < VB; ++v)
+#pragma unroll
+    for (int i = 0; i < 2 * R + 1; ++i) q[v][i] = T(0);
   if (active) {
 #pragma unroll
-    for (int i = 1; i < 2 * R + 1; ++i) {
-      int zz = i - 1 - R;                           // planes -R .. R-1
-      zz += (zz < 0) ? nz : 0;
-      zz -= (zz >= nz) ? nz : 0;
-      q[i] = __ldg(yv + (long long)zz * plane + col);
+    for (int v = 0; v < VB; ++v) {
+      if (v < nv) {
+        const T* yv = y + (long long)(v0 + v) * N;
+#pragma unroll
+        for (int i = 1; i < 2 * R + 1; ++i) {
+          int zz = i - 1 - R;
+          zz += (zz < 0) ? nz : 0;
+          zz -= (zz >= nz) ? nz : 0;
+          q[v][i] = __ldg(yv + (long long)zz * plane + col);
+        }
+      }
     }
   }
 
   for (int z = 0; z < nz; ++z) {
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
     int zl = z + R;
     zl -= (zl >= nz) ? nz : 0;
     zl -= (zl >= nz) ? nz : 0;
-    if (active) q[2 * R] = __ldg(yv + (long long)zl * plane + col);
+    const long long gidx = (long long)z * plane + col;
+    T yp[VB];
+    T vz = T(0);
+    int e0 = 0, e1 = 0;
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) q[v][i] = q[v][i + 1];
+        q[v][2 * R] = (v < nv) ? __ldg(y + (long long)(v0 + v) * N + (long long)zl * plane + col)
+                               : T(0);
+        yp[v] = (s2 != T(0) && v < nv) ? yprev[(long long)(v0 + v) * N + gidx] : T(0);
+      }
+      vz = __ldg(V + gidx);
+      if (gC != nullptr || proj_out) {
+        e0 = __ldg(pt_ptr + gidx);
+        e1 = __ldg(pt_ptr + gidx + 1);
+      }
+    }
 
     __syncthreads();  // previous plane fully consumed
-    if (active) sm[(ty + R) * nx + x] = q[R];
-    const T* pz = yv + (long long)z * plane;
-    for (int e = tid; e < halo_elems; e += blockDim.x) {
-      int r = e / nx, xx = e - r * nx;
-      int srow = (r < R) ? r : (r + TY);            // smem row
-      int gy = y0 - R + srow;
-      gy %= ny;
-      gy += (gy < 0) ? ny : 0;
-      sm[srow * nx + xx] = __ldg(pz + gy * nx + xx);
-    }
-    // rows of a partial last tile that have no owner thread
-    for (int e = tid; e < TY * nx; e += blockDim.x) {
-      int r = e / nx;
-      if (y0 + r >= ny) {
-        int gy = (y0 + r) % ny;
-        sm[(r + R) * nx + (e - r * nx)] = __ldg(pz + gy * nx + (e - r * nx));
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      if (v >= nv) break;
+      T* smv = sm + (size_t)v * rows * nx;
+      if (active) smv[(ty + R) * nx + x] = q[v][R];
+      const T* pz = y + (long long)(v0 + v) * N + (long long)z * plane;
+      for (int e = tid; e < halo_elems; e += blockDim.x) {
+        int r = e / nx, xx = e - r * nx;
+        int srow = (r < R) ? r : (r + TY);
+        int gy = y0 - R + srow;
+        gy %= ny;
+        gy += (gy < 0) ? ny : 0;
+        smv[srow * nx + xx] = __ldg(pz + gy * nx + xx);
+      }
+      for (int e = tid; e < TY * nx; e += blockDim.x) {
+        int r = e / nx;
+        if (y0 + r >= ny) {
+          int gy = (y0 + r) % ny;
+          smv[(r + R) * nx + (e - r * nx)] = __ldg(pz + gy * nx + (e - r * nx));
+        }
       }
     }
     __syncthreads();
 
     if (active) {
-      const long long gidx = (long long)z * plane + col;
-      const T u = q[R];
-      const T* row = sm + (ty + R) * nx;
-      T acc = (k.diag + __ldg(V + gidx) - c) * u;
+      T acc[VB];
 #pragma unroll
-      for (int p = 1; p <= R; ++p) {
-        int xp = x + p; xp -= (xp >= nx) ? nx : 0;
-        int xm = x - p; xm += (xm < 0) ? nx : 0;
-        acc += k.ax[p] * (row[xp] + row[xm]);
-        acc += k.ay[p] * (row[p * nx + x] + row[-p * nx + x]);
-        acc += k.az[p] * (q[R + p] + q[R - p]);
+      for (int v = 0; v < VB; ++v) {
+        const T* row = sm + (size_t)v * rows * nx + (ty + R) * nx;
+        const T u = q[v][R];
+        T a = (k.diag + vz - c) * u;
+#pragma unroll
+        for (int p = 1; p <= R; ++p) {
+          int xp = x + p; xp -= (xp >= nx) ? nx : 0;
+          int xm = x - p; xm += (xm < 0) ? nx : 0;
+          a += k.ax[p] * (row[xp] + row[xm]);
+          a += k.ay[p] * (row[p * nx + x] + row[-p * nx + x]);
+          a += k.az[p] * (q[v][R + p] + q[v][R - p]);
+        }
+        acc[v] = a;
       }
       if (gC != nullptr) {
-        const int e0 = __ldg(pt_ptr + gidx), e1 = __ldg(pt_ptr + gidx + 1);
-        const T* gv = gC + (long long)blockIdx.y * n_proj;
-        for (int e = e0; e < e1; ++e)
-          acc += __ldg(pt_val + e) * __ldg(gv + __ldg(pt_proj + e));
+        for (int e = e0; e < e1; ++e) {
+          const T val = __ldg(pt_val + e);
+          const int pid = __ldg(pt_proj + e);
+#pragma unroll
+          for (int v = 0; v < VB; ++v)
+            if (v < nv) acc[v] += val * __ldg(gC + (long long)(v0 + v) * n_proj + pid);
+        }
       }
-      T r = s1 * acc;
-      if (s2 != T(0)) r += s2 * yprev[vbase + gidx];
-      out[vbase + gidx] = r;
+      T r[VB];
+#pragma unroll
+      for (int v = 0; v < VB; ++v) {
+        r[v] = s1 * acc[v] + s2 * yp[v];
+        if (v < nv) out[(long long)(v0 + v) * N + gidx] = r[v];
+      }
+      if (proj_out) {
+        for (int e = e0; e < e1; ++e) {
+          const T val = __ldg(pt_val + e);
+          const int pid = __ldg(pt_proj + e);
+#pragma unroll
+          for (int v = 0; v < VB; ++v)
+            if (v < nv) atomicAdd(pacc + pid * VB + v, val * r[v]);
+        }
+      }
+    }
+  }
+  if (proj_out) {
+    __syncthreads();
+    for (int i = tid; i < n_proj * VB; i += blockDim.x) {
+      const int v = i % VB, pid = i / VB;
+      const T a = pacc[i];
+      if (v < nv && a != T(0))
+        atomicAdd(gC_next + (long long)(v0 + v) * n_proj + pid, T(gamma[pid]) * a);
     }
   }
 }
 
-static int pick_ty(int nx, int ny) {
+static int pick_ty(int nx, int ny, int target) {
   int best = 1;
   for (int t = 1; t <= ny; ++t)
-    if (ny % t == 0 && nx * t <= 512) best = t;
+    if (ny % t == 0 && nx * t <= target) best = t;
   if (nx * best < 128) {  // tiny rows: allow a ragged last tile
-    best = 512 / nx;
+    best = target / nx;
     if (best > ny) best = ny;
     if (best < 1) best = 1;
   }
   return best;
 }
 
-template <typename T, int R>
-static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                     const T* gC, int Ns, double s1, double c, double s2,
-                     cudaStream_t st) {
+static int stencil_vb(int esize) {
+  static int forced = -1;
+  if (forced < 0) {
+    const char* e = getenv("SQ3_STENCIL_VB");
+    forced = e ? atoi(e) : 0;
+  }
+  if (forced == 1 || forced == 2 || forced == 4) return forced;
+  return esize == 8 ? 2 : 4;
+}
+
+template <typename T, int R, int VB>
+static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                      const T* gC, T* gC_next, int Ns, double s1, double c,
+                      double s2, cudaStream_t st) {
   const Grid& g = ctx->grid;
   StepCoef<T> k{};
   double ix = 1.0 / (g.hx * g.hx), iy = 1.0 / (g.hy * g.hy),
@@ -148,12 +227,14 @@ static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
     k.ay[p] = T(-0.5 * g.w[p] * iy);
     k.az[p] = T(-0.5 * g.w[p] * iz);
   }
-  const int TY = pick_ty(g.nx, g.ny);
-  dim3 grid((g.ny + TY - 1) / TY, Ns);
+  const int TY = pick_ty(g.nx, g.ny, VB == 1 ? 512 : 384);
+  dim3 grid((g.ny + TY - 1) / TY, (Ns + VB - 1) / VB);
   dim3 block(g.nx * TY);
-  size_t smem = (size_t)(TY + 2 * R) * g.nx * sizeof(T);
-  const T* V = nullptr;
-  const T* pv = nullptr;
+  const bool nl = ctx->proj.n_proj > 0;
+  size_t smem = (size_t)VB * (TY + 2 * R) * g.nx * sizeof(T);
+  if (nl && gC_next) smem += (size_t)ctx->proj.n_proj * VB * sizeof(T);
+  const T* V;
+  const T* pv;
   if constexpr (sizeof(T) == 8) {
     V = reinterpret_cast<const T*>(ctx->V);
     pv = reinterpret_cast<const T*>(ctx->proj.pt_val);
@@ -161,24 +242,37 @@ static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
     V = reinterpret_cast<const T*>(ctx->Vf);
     pv = reinterpret_cast<const T*>(ctx->proj.pt_valf);
   }
-  const bool nl = (ctx->proj.n_proj > 0) && gC != nullptr;
-  cheb_step_kernel<T, R><<<grid, block, smem, st>>>(
-      g.nx, g.ny, g.nz, TY, k, y, yprev, out, V, nl ? gC : nullptr,
-      ctx->proj.pt_ptr, ctx->proj.pt_proj, pv, ctx->proj.n_proj, T(s1), T(c),
-      T(s2));
+  auto kern = cheb_step_kernel<T, R, VB>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, block, smem, st>>>(g.nx, g.ny, g.nz, Ns, TY, k, y, yprev, out, V,
+                                  nl ? gC : nullptr, ctx->proj.pt_ptr, ctx->proj.pt_proj,
+                                  pv, ctx->proj.n_proj, T(s1), T(c), T(s2),
+                                  nl ? gC_next : nullptr, ctx->proj.gamma);
+}
+
+template <typename T, int R>
+static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                     const T* gC, T* gC_next, int Ns, double s1, double c,
+                     double s2, cudaStream_t st) {
+  switch (stencil_vb(sizeof(T))) {
+    case 1: launch_rv<T, R, 1>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 2: launch_rv<T, R, 2>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    default: launch_rv<T, R, 4>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+  }
 }
 
 template <typename T>
 void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                      const T* gC, int Ns, double s1, double c, double s2,
-                      cudaStream_t st) {
+                      const T* gC, T* gC_next, int Ns, double s1, double c,
+                      double s2, cudaStream_t st) {
   switch (ctx->grid.radius) {
-    case 1: launch_r<T, 1>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
-    case 2: launch_r<T, 2>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
-    case 3: launch_r<T, 3>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
-    case 4: launch_r<T, 4>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
-    case 5: launch_r<T, 5>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
-    default: launch_r<T, 6>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st); break;
+    case 1: launch_r<T, 1>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 2: launch_r<T, 2>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 3: launch_r<T, 3>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 4: launch_r<T, 4>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 5: launch_r<T, 5>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    default: launch_r<T, 6>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
   }
 }
 
@@ -263,11 +357,12 @@ void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
 
 template void launch_cheb_step<double>(const sq3_ctx*, const double*,
                                        const double*, double*, const double*,
-                                       int, double, double, double,
+                                       double*, int, double, double, double,
                                        cudaStream_t);
 template void launch_cheb_step<float>(const sq3_ctx*, const float*,
-                                      const float*, float*, const float*, int,
-                                      double, double, double, cudaStream_t);
+                                      const float*, float*, const float*,
+                                      float*, int, double, double, double,
+                                      cudaStream_t);
 template void launch_nl_project<double>(const sq3_ctx*, const double*, double*,
                                         int, cudaStream_t);
 template void launch_nl_project<float>(const sq3_ctx*, const float*, float*,

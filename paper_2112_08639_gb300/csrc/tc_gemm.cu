@@ -143,6 +143,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+        "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long long e,
                                             long long piece_stride, int pieces) {
   __nv_bfloat16 h = __float2bfloat16_rn(t);
@@ -155,22 +169,38 @@ __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long lo
   }
 }
 
+// Thread roles (640 threads): warp 0 allocates TMEM and its lane 0 issues
+// the TMA copies and the MMAs; warps 4..19 are the accumulation warps.  Each
+// K-block's piece products go into a fresh TMEM accumulator (two of them,
+// alternating), so the tensor core never adds into a long running sum; the
+// accumulation warps read every finished K-block partial and add it into
+// Kahan-compensated FP32 registers (warp 4 + 4h + q owns TMEM lanes
+// 32q..32q+31 and columns 32h..32h+31).  The K-block partial is the sum of
+// at most 4 nprod tensor-core steps started from zero, which bounds the
+// accumulation error of the result by about that many half-ulps of a
+// K-block partial instead of half an ulp per step of the whole K loop.
+constexpr int ACC_WARPS = 16;
+constexpr int THREADS = 128 + 32 * ACC_WARPS;
+constexpr int ACC_COLS = BN / (ACC_WARPS / 4);   // columns per accumulation thread
+
 template <int PA, int PB, int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapB, TcParams p) {
   constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
+  // full[s], empty[s] for the smem stages; accf[b], acce[b] for the two
+  // TMEM accumulators
+  __shared__ __align__(8) uint64_t bars[2 * STAGES + 4];
   __shared__ uint32_t tmem_slot;
+  __shared__ int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.y, nt = blockIdx.x;
   const int m0 = mt * BM, n0 = nt * BN;
   if (p.tri == 1 && nt < mt) return;   // symmetric output: upper tiles only
 
-  // K range of this CTA
   const int Keff = (p.tri == 2) ? min(p.K, n0 + BN) : p.K;
   int kchunk = (Keff + (int)gridDim.z - 1) / (int)gridDim.z;
   kchunk = (kchunk + BK - 1) / BK * BK;
@@ -181,12 +211,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]);
   const uint32_t empty0 = smem_u32(&bars[STAGES]);
-  const uint32_t done = smem_u32(&bars[2 * STAGES]);
+  const uint32_t accf0 = smem_u32(&bars[2 * STAGES]);
+  const uint32_t acce0 = smem_u32(&bars[2 * STAGES + 2]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(BN));
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
@@ -194,7 +225,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, ACC_WARPS);
+    }
+    failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -202,13 +237,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  __shared__ int failed;
-  if (threadIdx.x == 0) failed = 0;
-  __syncthreads();
-
   if (threadIdx.x == 0) {
+    // ------------------------- producer / MMA issuer -----------------------
     const uint32_t idesc = idesc_bf16();
-    int issued = 0;      // K-blocks whose copies were issued
+    int issued = 0;
     bool ok = true;
     auto issue = [&](int kb) {
       const int s = kb % STAGES;
@@ -222,21 +254,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
     for (; issued < nk && issued < STAGES; ++issued) issue(issued);
     for (int kb = 0; kb < nk && ok; ++kb) {
       const int s = kb % STAGES;
+      const int buf = kb & 1;
+      // the accumulator used two K-blocks ago must have been drained
+      if (kb >= 2 && !mbar_wait(acce0 + 8 * buf, ((kb - 2) >> 1) & 1)) { ok = false; break; }
       if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = base + s * STAGE_BYTES;
       const uint32_t sb = sa + PA * TILE_BYTES;
+      const uint32_t td = tmem + (uint32_t)(buf * BN);
       for (int q = 0; q < p.nprod; ++q) {
         const uint32_t pa = sa + p.prod_a[q] * TILE_BYTES;
         const uint32_t pb = sb + p.prod_b[q] * TILE_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t acc = (kb > 0 || q > 0 || kk > 0) ? 1u : 0u;
-          mma_bf16(tmem, sw128_desc(pa + kk * 32), sw128_desc(pb + kk * 32), idesc, acc);
-        }
+        for (int kk = 0; kk < BK / 16; ++kk)
+          mma_bf16(td, sw128_desc(pa + kk * 32), sw128_desc(pb + kk * 32), idesc,
+                   (q > 0 || kk > 0) ? 1u : 0u);
       }
-      mma_commit(empty0 + 8 * s);
-      // refill the stage consumed one step earlier once its MMAs are done
+      mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
+      mma_commit(accf0 + 8 * buf);     // K-block partial ready
       if (kb >= 1 && issued < nk) {
         const int sp = (kb - 1) % STAGES;
         if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / STAGES) & 1)) { ok = false; break; }
@@ -244,71 +279,90 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         ++issued;
       }
     }
-    if (ok) {
-      mma_commit(done);
-    } else {
-      failed = 1;
+    if (!ok) {
+      atomicExch(&failed, 1);
       atomicCAS(p.status, 0, DEV_TIMEOUT);
-      // drain: the last copy issued into each stage must land before the CTA
-      // exits (each wait bounded)
       for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
         mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
     }
   }
-  __syncwarp();
-  __syncthreads();
-  bool have = (failed == 0) && nk > 0;
-  if (have) {
-    if (!mbar_wait(done, 0)) {
-      atomicCAS(p.status, 0, DEV_TIMEOUT);
-      have = false;
+
+  // ------------------------------ accumulation ------------------------------
+  const bool accw = warp >= 4;
+  const int aw = warp - 4;
+  const int q4 = aw & 3, half = aw >> 2;
+  float sum[ACC_COLS], comp[ACC_COLS];
+#pragma unroll
+  for (int i = 0; i < ACC_COLS; ++i) { sum[i] = 0.f; comp[i] = 0.f; }
+  bool have = nk > 0;
+  if (accw) {
+    for (int kb = 0; kb < nk; ++kb) {
+      const int buf = kb & 1;
+      if (!mbar_wait(accf0 + 8 * buf, (kb >> 1) & 1)) {
+        have = false;
+        atomicExch(&failed, 1);
+        atomicCAS(p.status, 0, DEV_TIMEOUT);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + half * ACC_COLS);
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < ACC_COLS / 16; ++c) {
+        tmem_ld16(ta + c * 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {   // Kahan summation
+          const float yk = v[i] - comp[c * 16 + i];
+          const float t = sum[c * 16 + i] + yk;
+          comp[c * 16 + i] = (t - sum[c * 16 + i]) - yk;
+          sum[c * 16 + i] = t;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * buf)
+                     : "memory");
     }
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  have = have && (failed == 0);
 
-  // ---------------- epilogue: warp w owns rows m0 + 32 w .. + 31 ----------
-  const int m = m0 + warp * 32 + lane;
-  const bool mrow = m < p.M;
-  double rsum = 0.0;
-  if (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      if (have) {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      } else {
+  // ------------------------------- epilogue --------------------------------
+  if (accw) {
+    const int m = m0 + q4 * 32 + lane;
+    const bool mrow = m < p.M;
+    double rsum = 0.0;
+    if (mrow && (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB)) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.f;
-      }
-      if (!mrow) continue;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int n = n0 + c0 + i;
+      for (int i = 0; i < ACC_COLS; ++i) {
+        const int n = n0 + half * ACC_COLS + i;
         if (n >= p.N) continue;
         const long long e = (long long)m + (long long)n * p.ldc;
+        const double acc = have ? (double)sum[i] - (double)comp[i] : 0.0;
         if (EPI == EPI_TC_ATOMIC) {
-          atomicAdd(p.C64 + e, (double)v[i]);
+          atomicAdd(p.C64 + e, acc);
         } else if (EPI == EPI_TC_STORE) {
-          p.C32[e] = p.alpha * v[i];
+          p.C32[e] = (float)((double)p.alpha * acc);
         } else if (EPI == EPI_TC_CHEB) {
-          const float t = 2.f * v[i] - p.Tprev[e];
+          const float t = (float)(2.0 * acc - (double)p.Tprev[e]);
           p.C32[e] = t;
           split_store(t, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
                       p.next_pieces);
           if (m == n) atomicAdd(p.trace, (double)t);
         } else {  // EPI_TC_RHO
-          rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * (double)v[i];
+          rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * acc;
         }
       }
     }
+    if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
   }
-  if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(BN));
+                 "r"(2 * BN));
 }
 
 // ---------------------------------------------------------------------------
@@ -362,7 +416,7 @@ static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& 
       return SQ3_ECUDA;
     attr = true;
   }
-  k<<<grid, 128, smem, st>>>(a, b, p);
+  k<<<grid, THREADS, smem, st>>>(a, b, p);
   return cuda_err(cudaGetLastError());
 }
 
