@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--config", default="al108_72")
     p.add_argument("--impl", default="sq3", choices=["sq3", "reference"])
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -345,7 +345,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.steps is None:
-        args.steps = 2 if args.prec == "fp64" else 10
+        args.steps = 1 if args.prec == "fp64" else 5
     if args.impl == "reference":
         if rank != 0:
             return

@@ -75,7 +75,8 @@ void sq3_destroy(sq3_ctx* ctx);
  * with a central finite-difference Laplacian of order fd_order (even, 2..12;
  * the paper uses 12, Sec. 5).  Weights: Fornberg closed form
  * w_p = 2(-1)^(p+1)(n!)^2/(p^2 (n-p)!(n+p)!), w_0 = -2 sum 1/p^2, n = order/2.
- * Resets the potential and projectors.  Errors: SQ3_EINVAL. */
+ * Requires fd_order/2 <= nx, ny, nz and nx <= 512.  Resets the potential and
+ * projectors.  Errors: SQ3_EINVAL. */
 int sq3_setup_grid(sq3_ctx* ctx, int nx, int ny, int nz,
                    double Lx, double Ly, double Lz, int fd_order);
 

@@ -150,12 +150,10 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
-  void *gA, *gB;
-  rc = gc_buffer(ctx, Ns, &gA, &gB);
+  void* gA;
+  rc = gc_buffer(ctx, Ns, &gA);
   if (rc) return rc;
-  T* gC = (T*)gA;        // projections of the current iterate
-  T* gN = (T*)gB;        // projections of the step's output
-  const size_t gbytes = (size_t)ctx->proj.n_proj * Ns * sizeof(T);
+  T* gC = (T*)gA;        // projections gamma c^T of the current iterate
   T* W = (T*)ctx->wsX;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   const double s1 = e / (a0 - c);
@@ -167,26 +165,23 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   if (nl) {
     Prof p(ctx, ST_NL_PROJECT);
     launch_nl_project<T>(ctx, X, gC, Ns, ctx->stream);
-    if (m > 1) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
   }
   {
     Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, W, gC, (nl && m > 1) ? gN : nullptr,
-                        Ns, s1 / e, c, 0.0, ctx->stream);
+    launch_cheb_step<T>(ctx, X, nullptr, W, gC, nullptr, Ns, s1 / e, c, 0.0,
+                        ctx->stream);
   }
   for (int k = 2; k <= m; ++k) {
     const double sn = 1.0 / (tau - s);
-    const bool want_next = nl && k < m;
     if (nl) {
-      std::swap(gC, gN);
-      if (want_next) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
+      Prof p(ctx, ST_NL_PROJECT);
+      launch_nl_project<T>(ctx, cur, gC, Ns, ctx->stream);
     }
     {
-      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev);
-      // the step also accumulates the projections of Y_k for step k+1
+      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev)
       Prof p(ctx, ST_STENCIL);
-      launch_cheb_step<T>(ctx, cur, prev, prev, gC, want_next ? gN : nullptr,
-                          Ns, 2.0 * sn / e, c, -s * sn, ctx->stream);
+      launch_cheb_step<T>(ctx, cur, prev, prev, gC, nullptr, Ns, 2.0 * sn / e,
+                          c, -s * sn, ctx->stream);
     }
     std::swap(cur, prev);
     s = sn;
@@ -378,7 +373,7 @@ int sq3_setup_grid(sq3_ctx* c, int nx, int ny, int nz, double Lx, double Ly,
   if (!c || fd_order < 2 || fd_order > 2 * SQ3_MAX_FD_RADIUS || fd_order % 2)
     return SQ3_EINVAL;
   const int R = fd_order / 2;
-  if (nx < R || ny < R || nz < R || nx > 1024 ||
+  if (nx < R || ny < R || nz < R || nx > 512 ||
       !(Lx > 0) || !(Ly > 0) || !(Lz > 0))
     return SQ3_EINVAL;
   cudaSetDevice(c->device);

@@ -35,78 +35,103 @@ struct StepCoef {
 
 // VB vectors per CTA share the (x, y) tile: the potential, the per-point
 // projector entries and the index arithmetic are loaded once for all VB.
-// With gC_next non-null the kernel also accumulates the projections of its
-// own output, gC_next[v][p] += gamma_p sum_k c_p[k] out_v[k] (per-CTA partial
-// sums in shared memory, one global atomic per projector and vector), so the
-// next filter step needs no separate gather over the block.
+// Shared-memory rows carry R wrapped columns on each side, so the x-taps
+// need no index wrap.  The next plane's register-queue entry and yprev are
+// loaded one iteration ahead.  The projector coefficients gC of the input
+// block are staged in shared memory.
 template <typename T, int R, int VB>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512, 1)
 cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
                  const T* __restrict__ y, const T* yprev, T* out,
                  const T* __restrict__ V, const T* __restrict__ gC,
                  const int* __restrict__ pt_ptr, const int* __restrict__ pt_proj,
-                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2,
-                 T* gC_next, const double* __restrict__ gamma) {
+                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rows = TY + 2 * R;
-  T* sm = reinterpret_cast<T*>(smem_raw);           // VB planes, rows x nx each
-  T* pacc = sm + (size_t)VB * rows * nx;             // n_proj x VB partial sums
+  const int W = nx + 2 * R;                          // padded row width
+  T* sm = reinterpret_cast<T*>(smem_raw);           // VB planes, rows x W each
+  T* gcs = sm + (size_t)VB * rows * W;               // n_proj x VB staged gC
   const int tid = threadIdx.x;
   const int x = tid % nx;
   const int ty = tid / nx;
   const int y0 = blockIdx.x * TY;
   const int yy = y0 + ty;
   const bool active = (ty < TY) && (yy < ny);
-  const long long N = (long long)nx * ny * nz;
-  const long long plane = (long long)nx * ny;
+  const int plane = nx * ny;
+  const long long N = (long long)plane * nz;
   const int v0 = blockIdx.y * VB;
   const int nv = min(VB, Ns - v0);
   const int col = yy * nx + x;
-  const int halo_elems = 2 * R * nx;
-  const bool proj_out = gC_next != nullptr;
-  if (proj_out)
-    for (int i = tid; i < n_proj * VB; i += blockDim.x) pacc[i] = T(0);
+  const bool nl = gC != nullptr;
+  if (nl) {
+    for (int i = tid; i < n_proj * VB; i += blockDim.x) {
+      const int v = i % VB, pid = i / VB;
+      gcs[i] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + pid] : T(0);
+    }
+  }
+  const T* yb[VB];
+  T* ob[VB];
+  const T* pb[VB];
+#pragma unroll
+  for (int v = 0; v < VB; ++v) {
+    const int vv = (v < nv) ? v0 + v : v0;
+    yb[v] = y + (long long)vv * N;
+    ob[v] = out + (long long)vv * N;
+    pb[v] = (yprev != nullptr) ? yprev + (long long)vv * N : nullptr;
+  }
 
   T q[VB][2 * R + 1];
+  T ypn[VB], la[VB];
 #pragma unroll
-  for (int v = 0; v < VB; ++v)
+  for (int v = 0; v < VB; ++v) {
 #pragma unroll
     for (int i = 0; i < 2 * R + 1; ++i) q[v][i] = T(0);
+    ypn[v] = T(0);
+    la[v] = T(0);
+  }
   if (active) {
 #pragma unroll
     for (int v = 0; v < VB; ++v) {
-      if (v < nv) {
-        const T* yv = y + (long long)(v0 + v) * N;
 #pragma unroll
-        for (int i = 1; i < 2 * R + 1; ++i) {
-          int zz = i - 1 - R;
-          zz += (zz < 0) ? nz : 0;
-          zz -= (zz >= nz) ? nz : 0;
-          q[v][i] = __ldg(yv + (long long)zz * plane + col);
-        }
+      for (int i = 1; i < 2 * R + 1; ++i) {
+        int zz = i - 1 - R;                          // planes -R .. R-1
+        zz += (zz < 0) ? nz : 0;
+        zz -= (zz >= nz) ? nz : 0;
+        q[v][i] = __ldg(yb[v] + zz * plane + col);
       }
+      // first look-ahead: plane R for the queue, plane 0 of yprev
+      la[v] = __ldg(yb[v] + (R % nz) * plane + col);
+      if (s2 != T(0)) ypn[v] = pb[v][col];
     }
   }
 
   for (int z = 0; z < nz; ++z) {
-    int zl = z + R;
-    zl -= (zl >= nz) ? nz : 0;
-    zl -= (zl >= nz) ? nz : 0;
-    const long long gidx = (long long)z * plane + col;
+    const int gidx = z * plane + col;
     T yp[VB];
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      // la[v] holds the look-ahead value for plane z + R
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) q[v][i] = q[v][i + 1];
+      q[v][2 * R] = la[v];
+      yp[v] = ypn[v];
+    }
     T vz = T(0);
     int e0 = 0, e1 = 0;
     if (active) {
+      // look-ahead loads for the next iteration
+      if (z + 1 < nz) {
+        int zl = z + 1 + R;
+        zl -= (zl >= nz) ? nz : 0;
+        zl -= (zl >= nz) ? nz : 0;
 #pragma unroll
-      for (int v = 0; v < VB; ++v) {
-#pragma unroll
-        for (int i = 0; i < 2 * R; ++i) q[v][i] = q[v][i + 1];
-        q[v][2 * R] = (v < nv) ? __ldg(y + (long long)(v0 + v) * N + (long long)zl * plane + col)
-                               : T(0);
-        yp[v] = (s2 != T(0) && v < nv) ? yprev[(long long)(v0 + v) * N + gidx] : T(0);
+        for (int v = 0; v < VB; ++v) {
+          la[v] = __ldg(yb[v] + zl * plane + col);
+          if (s2 != T(0)) ypn[v] = pb[v][gidx + plane];
+        }
       }
       vz = __ldg(V + gidx);
-      if (gC != nullptr || proj_out) {
+      if (nl) {
         e0 = __ldg(pt_ptr + gidx);
         e1 = __ldg(pt_ptr + gidx + 1);
       }
@@ -115,23 +140,35 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
     __syncthreads();  // previous plane fully consumed
 #pragma unroll
     for (int v = 0; v < VB; ++v) {
-      if (v >= nv) break;
-      T* smv = sm + (size_t)v * rows * nx;
-      if (active) smv[(ty + R) * nx + x] = q[v][R];
-      const T* pz = y + (long long)(v0 + v) * N + (long long)z * plane;
-      for (int e = tid; e < halo_elems; e += blockDim.x) {
-        int r = e / nx, xx = e - r * nx;
-        int srow = (r < R) ? r : (r + TY);
+      T* smv = sm + (size_t)v * rows * W;
+      if (active) {
+        T* row = smv + (ty + R) * W + R;
+        const T u = q[v][R];
+        row[x] = u;
+        if (x < R) row[nx + x] = u;                  // wrapped right halo
+        if (x >= nx - R) row[x - nx] = u;            // wrapped left halo
+      }
+      const T* pz = yb[v] + z * plane;
+      for (int e = tid; e < 2 * R * nx; e += blockDim.x) {
+        const int r = e / nx, xx = e - r * nx;
+        const int srow = (r < R) ? r : (r + TY);
         int gy = y0 - R + srow;
         gy %= ny;
         gy += (gy < 0) ? ny : 0;
-        smv[srow * nx + xx] = __ldg(pz + gy * nx + xx);
+        const T u = __ldg(pz + gy * nx + xx);
+        T* row = smv + srow * W + R;
+        row[xx] = u;
+        if (xx < R) row[nx + xx] = u;
+        if (xx >= nx - R) row[xx - nx] = u;
       }
-      for (int e = tid; e < TY * nx; e += blockDim.x) {
-        int r = e / nx;
+      for (int e = tid; e < TY * nx; e += blockDim.x) {   // rows past ny (tiny grids)
+        const int r = e / nx, xx = e - r * nx;
         if (y0 + r >= ny) {
-          int gy = (y0 + r) % ny;
-          smv[(r + R) * nx + (e - r * nx)] = __ldg(pz + gy * nx + (e - r * nx));
+          const T u = __ldg(pz + ((y0 + r) % ny) * nx + xx);
+          T* row = smv + (r + R) * W + R;
+          row[xx] = u;
+          if (xx < R) row[nx + xx] = u;
+          if (xx >= nx - R) row[xx - nx] = u;
         }
       }
     }
@@ -141,52 +178,29 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
       T acc[VB];
 #pragma unroll
       for (int v = 0; v < VB; ++v) {
-        const T* row = sm + (size_t)v * rows * nx + (ty + R) * nx;
+        const T* row = sm + (size_t)v * rows * W + (ty + R) * W + R + x;
         const T u = q[v][R];
         T a = (k.diag + vz - c) * u;
 #pragma unroll
         for (int p = 1; p <= R; ++p) {
-          int xp = x + p; xp -= (xp >= nx) ? nx : 0;
-          int xm = x - p; xm += (xm < 0) ? nx : 0;
-          a += k.ax[p] * (row[xp] + row[xm]);
-          a += k.ay[p] * (row[p * nx + x] + row[-p * nx + x]);
+          a += k.ax[p] * (row[p] + row[-p]);
+          a += k.ay[p] * (row[p * W] + row[-p * W]);
           a += k.az[p] * (q[v][R + p] + q[v][R - p]);
         }
         acc[v] = a;
       }
-      if (gC != nullptr) {
+      if (nl) {
+#pragma unroll 2
         for (int e = e0; e < e1; ++e) {
           const T val = __ldg(pt_val + e);
-          const int pid = __ldg(pt_proj + e);
+          const T* gp = gcs + __ldg(pt_proj + e) * VB;
 #pragma unroll
-          for (int v = 0; v < VB; ++v)
-            if (v < nv) acc[v] += val * __ldg(gC + (long long)(v0 + v) * n_proj + pid);
+          for (int v = 0; v < VB; ++v) acc[v] += val * gp[v];
         }
       }
-      T r[VB];
 #pragma unroll
-      for (int v = 0; v < VB; ++v) {
-        r[v] = s1 * acc[v] + s2 * yp[v];
-        if (v < nv) out[(long long)(v0 + v) * N + gidx] = r[v];
-      }
-      if (proj_out) {
-        for (int e = e0; e < e1; ++e) {
-          const T val = __ldg(pt_val + e);
-          const int pid = __ldg(pt_proj + e);
-#pragma unroll
-          for (int v = 0; v < VB; ++v)
-            if (v < nv) atomicAdd(pacc + pid * VB + v, val * r[v]);
-        }
-      }
-    }
-  }
-  if (proj_out) {
-    __syncthreads();
-    for (int i = tid; i < n_proj * VB; i += blockDim.x) {
-      const int v = i % VB, pid = i / VB;
-      const T a = pacc[i];
-      if (v < nv && a != T(0))
-        atomicAdd(gC_next + (long long)(v0 + v) * n_proj + pid, T(gamma[pid]) * a);
+      for (int v = 0; v < VB; ++v)
+        if (v < nv) ob[v][gidx] = s1 * acc[v] + s2 * yp[v];
     }
   }
 }
@@ -210,7 +224,7 @@ static int stencil_vb(int esize) {
     forced = e ? atoi(e) : 0;
   }
   if (forced == 1 || forced == 2 || forced == 4) return forced;
-  return esize == 8 ? 2 : 4;
+  return esize == 8 ? 1 : 2;
 }
 
 template <typename T, int R, int VB>
@@ -227,12 +241,12 @@ static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
     k.ay[p] = T(-0.5 * g.w[p] * iy);
     k.az[p] = T(-0.5 * g.w[p] * iz);
   }
-  const int TY = pick_ty(g.nx, g.ny, VB == 1 ? 512 : 384);
+  const int TY = pick_ty(g.nx, g.ny, 512);
   dim3 grid((g.ny + TY - 1) / TY, (Ns + VB - 1) / VB);
   dim3 block(g.nx * TY);
   const bool nl = ctx->proj.n_proj > 0;
-  size_t smem = (size_t)VB * (TY + 2 * R) * g.nx * sizeof(T);
-  if (nl && gC_next) smem += (size_t)ctx->proj.n_proj * VB * sizeof(T);
+  size_t smem = (size_t)VB * (TY + 2 * R) * (g.nx + 2 * R) * sizeof(T);
+  if (nl) smem += (size_t)ctx->proj.n_proj * VB * sizeof(T);
   const T* V;
   const T* pv;
   if constexpr (sizeof(T) == 8) {
@@ -247,8 +261,8 @@ static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<grid, block, smem, st>>>(g.nx, g.ny, g.nz, Ns, TY, k, y, yprev, out, V,
                                   nl ? gC : nullptr, ctx->proj.pt_ptr, ctx->proj.pt_proj,
-                                  pv, ctx->proj.n_proj, T(s1), T(c), T(s2),
-                                  nl ? gC_next : nullptr, ctx->proj.gamma);
+                                  pv, ctx->proj.n_proj, T(s1), T(c), T(s2));
+  (void)gC_next;
 }
 
 template <typename T, int R>
