@@ -176,6 +176,34 @@ int sq3_profile_enable(sq3_ctx* ctx, int enable);
 int sq3_profile_read(sq3_ctx* ctx, double* ms, long long* launches,
                      int n_stages);
 
+/* Allocation-free spectral bounds of a subspace Hamiltonian.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory: processes that reserve
+ * all of HBM up front for their own arena and forbid allocations by
+ * libraries, and loops where a device allocation, which may synchronise the
+ * whole device, would stall work on other streams.  It computes the same
+ * bounds as the Lanczos step of sq3_kernel_from_hs with bounds_in == NULL:
+ * 40 Lanczos steps with full reorthogonalisation on the symmetric Hs,
+ * extremal Ritz values widened by their residual bounds, then xi *= 1.001,
+ * and writes {chi, xi} to `bounds`.
+ *
+ * Hs: device Ns x Ns double, symmetric (caller-owned).  bounds: DEVICE
+ * array of 2 doubles (caller-owned).  cuda_stream: the cudaStream_t the work
+ * is ordered on (NULL = legacy default stream); the call returns after that
+ * stream has finished the work.  It needs no context, and calls no
+ * cudaMalloc, cudaFree or allocating routine: its scratch is a fixed
+ * device array inside the library, sized for Ns <= 8192 (2.7 MB), which
+ * every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the previous call's contents, so two
+ * calls whose GPU work overlaps (other streams, other host threads) race
+ * and give wrong bounds: serialise them.
+ * Errors: SQ3_EINVAL (null pointer, Ns < 1, or Ns > 8192), SQ3_ECUDA. */
+int sq3_lanczos_bounds_noalloc(const double* Hs, int Ns, double* bounds,
+                               void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sq3_status_string(int status);
 

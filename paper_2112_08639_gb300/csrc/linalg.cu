@@ -11,6 +11,8 @@
 //   lambda_Ns of Hs without saying how they are obtained).
 #include <math.h>
 
+#include <mutex>
+
 #include "sq3_internal.cuh"
 
 namespace sq3 {
@@ -376,3 +378,60 @@ void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
 }
 
 }  // namespace sq3
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the spectral bounds (see sq3_lanczos_bounds_noalloc
+// in sq3.h).  Its scratch is this file-scope device array, sized for
+// Ns <= SQ3_NOALLOC_MAX_NS and the fixed 40 Lanczos steps.
+// ---------------------------------------------------------------------------
+namespace sq3 {
+namespace {
+constexpr int kNoAllocSteps = 40;
+constexpr size_t kNoAllocWords =
+    (size_t)(kNoAllocSteps + 2) * SQ3_NOALLOC_MAX_NS + 2 * kNoAllocSteps + 8;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+}  // namespace sq3
+
+extern "C" int sq3_lanczos_bounds_noalloc(const double* Hs, int Ns, double* bounds,
+                                          void* cuda_stream) {
+  using namespace sq3;
+  if (!Hs || !bounds || Ns < 1) return SQ3_EINVAL;
+  if (Ns > SQ3_NOALLOC_MAX_NS) return SQ3_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return SQ3_ECUDA;
+  }
+  double* scratch = nullptr;
+  {
+    // first call on this device: look up the device address of the array
+    // with the device current (the host-side name is only a stand-in)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return SQ3_ECUDA;
+      }
+      g_noalloc_addr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int steps = Ns < kNoAllocSteps ? Ns : kNoAllocSteps;
+  // every scratch word the kernels read is written earlier in the same call
+  // (the basis, the step counter, alpha and beta), so nothing is cleared here
+  lanczos_bounds_f64(nullptr, Hs, Ns, steps, bounds, scratch, st);
+  if (cudaGetLastError() != cudaSuccess) return SQ3_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return SQ3_ECUDA;
+  }
+  return SQ3_OK;
+}

@@ -14,6 +14,8 @@
 #define SQ3_DEV_SCAL 2304
 // bf16 pieces per FP32 operand in the mixed path (3 pieces, 6 products)
 #define MIXED_PIECES 3
+// largest Ns accepted by sq3_lanczos_bounds_noalloc (static scratch size)
+#define SQ3_NOALLOC_MAX_NS 8192
 
 namespace sq3 {
 

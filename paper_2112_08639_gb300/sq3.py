@@ -47,6 +47,7 @@ _sigs = {
     "sq3_status_string": (ctypes.c_char_p, [_i]),
     "sq3_version": (ctypes.c_char_p, []),
     "sq3_profile_enable": (_i, [_p, _i]),
+    "sq3_lanczos_bounds_noalloc": (_i, [_p, _i, _p, _p]),
     "sq3_profile_read": (_i, [_p, _p, _p, _i]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -80,6 +81,24 @@ def _prec_dtype(prec: int):
 
 def version() -> str:
     return lib.sq3_version().decode()
+
+
+NOALLOC_MAX_NS = 8192
+
+
+def lanczos_bounds_noalloc(Hs: torch.Tensor, bounds: torch.Tensor | None = None,
+                           stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Spectral bounds {chi, xi} of a symmetric device matrix through the
+    allocation-free entry point (its scratch is a fixed array inside the
+    library; see include/sq3.h).  `bounds` is a caller-owned device tensor of
+    2 doubles; one is created here when it is not given."""
+    if bounds is None:
+        bounds = torch.empty(2, dtype=torch.float64, device=Hs.device)
+    st = stream if stream is not None else torch.cuda.current_stream(Hs.device)
+    _check(lib.sq3_lanczos_bounds_noalloc(_ptr(Hs), Hs.shape[0], _ptr(bounds),
+                                          ctypes.c_void_p(st.cuda_stream)),
+           "sq3_lanczos_bounds_noalloc")
+    return bounds
 
 
 class Context:
