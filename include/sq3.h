@@ -169,9 +169,9 @@ int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
  *   3 Cholesky, 4 triangular inverse, 5 X R^{-1}, 6 X^T (H X),
  *   7 Lanczos, 8 Chebyshev recurrence GEMM, 9 Fermi level/coefficients,
  *   10 Ds accumulation, 11 density X Ds row-dot, 12 BF16 split,
- *   13 device copies.
+ *   13 device copies, 14 nonlocal pass (apply and next-step projection).
  * Host pointers; either may be NULL. */
-#define SQ3_N_STAGES 14
+#define SQ3_N_STAGES 15
 int sq3_profile_enable(sq3_ctx* ctx, int enable);
 int sq3_profile_read(sq3_ctx* ctx, double* ms, long long* launches,
                      int n_stages);

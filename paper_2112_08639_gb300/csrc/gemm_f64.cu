@@ -24,6 +24,7 @@ gemm_f64_kernel(GemmArgs g) {
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (g.tri == 1 && n0 + BN <= m0) return;       // tile strictly below diagonal
+  if (g.tri == 3 && n0 >= m0 + BM) return;       // tile strictly above diagonal
   const int Keff = (g.tri == 2) ? min(g.K, n0 + BN) : g.K;
   int kchunk = (Keff + g.splits - 1) / g.splits;
   kchunk = (kchunk + BK - 1) / BK * BK;

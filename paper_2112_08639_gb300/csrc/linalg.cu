@@ -114,6 +114,7 @@ int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, double* diag_ws,
     g.B = S + (k0 + kb) + (long long)k0 * n; g.ldb = n; g.b_kcontig = false;
     g.C = S + (k0 + kb) + (long long)(k0 + kb) * n; g.ldc = n;
     g.alpha = -1.0; g.beta = 1.0; g.splits = 1;
+    g.tri = 3;                 // later panels read only the lower triangle
     gemm_f64(g, EPI_STORE, st);
   }
   return cuda_err(cudaGetLastError());
@@ -139,8 +140,56 @@ tri_inv_kernel(const double* __restrict__ L, double* Rinv, int n) {
     Rinv[j + (long long)i * n] = (i >= j) ? r[i] : 0.0;
 }
 
+// Same result with TRI_WPB columns per CTA, one warp each, walking the rows
+// i together: column i of L (below the diagonal) is copied into shared
+// memory once per step for all the CTA's columns, and 1/L_ii comes from a
+// precomputed array, so a step costs one coalesced column read and two
+// block barriers.
+constexpr int TRI_WPB = 8;
+__global__ void __launch_bounds__(32 * TRI_WPB)
+tri_inv_block_kernel(const double* __restrict__ L, const double* __restrict__ inv_diag,
+                     double* Rinv, int n) {
+  extern __shared__ double sm[];
+  double* lc = sm;                          // n : current column of L
+  double* rw = sm + n;                      // TRI_WPB x n
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.x * TRI_WPB;
+  const int j = j0 + warp;
+  double* r = rw + (size_t)warp * n;
+  for (int i = lane; i < n; i += 32) r[i] = (i == j) ? 1.0 : 0.0;
+  for (int i = j0; i < n; ++i) {
+    __syncthreads();                        // previous column consumed
+    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) lc[k] = L[k + (long long)i * n];
+    __syncthreads();
+    if (j < n && i >= j) {
+      const double wi = r[i] * inv_diag[i];
+      __syncwarp();
+      if (lane == 0) r[i] = wi;
+      for (int k = i + 1 + lane; k < n; k += 32) r[k] -= lc[k] * wi;
+    }
+  }
+  __syncthreads();
+  if (j < n)
+    for (int i = lane; i < n; i += 32) Rinv[j + (long long)i * n] = (i >= j) ? r[i] : 0.0;
+}
+
+__global__ void inv_diag_kernel(const double* L, int n, double* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = 1.0 / L[i + (long long)i * n];
+}
+
 void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
-                               cudaStream_t st) {
+                               double* diag_ws, cudaStream_t st) {
+  const size_t wsm = (size_t)(TRI_WPB + 1) * n * sizeof(double);
+  if (wsm <= 200 * 1024) {
+    if (wsm > 48 * 1024)
+      cudaFuncSetAttribute(tri_inv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)wsm);
+    inv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(L, n, diag_ws);
+    tri_inv_block_kernel<<<(n + TRI_WPB - 1) / TRI_WPB, 32 * TRI_WPB, wsm, st>>>(
+        L, diag_ws, Rinv, n);
+    return;
+  }
   size_t smem = (size_t)n * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(tri_inv_kernel,

@@ -51,6 +51,41 @@ __global__ void split_cols_kernel(const T* __restrict__ src, long long lds, int 
   }
 }
 
+// Same layout for an FP32 source, four consecutive rows per thread (16-byte
+// load, 8-byte stores per piece) on a 2-D grid (rows x columns), so no
+// 64-bit division per element.
+__global__ void split_cols_f32x4_kernel(const float* __restrict__ src, long long lds,
+                                        int rows, __nv_bfloat16* out, long long ld,
+                                        long long ps, int pieces) {
+  const long long c = blockIdx.y;
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (r >= rows) return;
+  const float* sp = src + c * lds + r;
+  const long long e = c * ld + r;
+  if (r + 4 <= rows) {
+    const float4 x = *reinterpret_cast<const float4*>(sp);
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+    __nv_bfloat16 h[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[0][i] = __float2bfloat16_rn(xs[i]);
+      const float r1 = xs[i] - __bfloat162float(h[0][i]);
+      h[1][i] = __float2bfloat16_rn(r1);
+      h[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][i]));
+    }
+    for (int q = 0; q < pieces; ++q) {
+      __nv_bfloat162 lo = __halves2bfloat162(h[q][0], h[q][1]);
+      __nv_bfloat162 hi = __halves2bfloat162(h[q][2], h[q][3]);
+      uint2 pk;
+      pk.x = *reinterpret_cast<unsigned*>(&lo);
+      pk.y = *reinterpret_cast<unsigned*>(&hi);
+      *reinterpret_cast<uint2*>(out + e + q * ps) = pk;
+    }
+  } else {
+    for (long long t = r; t < rows; ++t) split3(src[c * lds + t], out, c * ld + t, ps, pieces);
+  }
+}
+
 // Column-major rows x cols source -> pieces with the source ROW as operand
 // row: out[q][r * ld + c] (a transpose through shared memory).
 __global__ void split_rows_kernel(const float* __restrict__ src, long long lds, int rows,
@@ -182,8 +217,14 @@ static void split_block_cols(sq3_ctx* ctx, const float* X, int Ns, __nv_bfloat16
                              const MixedBuffers& b) {
   Prof p(ctx, ST_SPLIT);
   const long long N = ctx->grid.N;
-  split_cols_kernel<float><<<grid_for(N * Ns), 256, 0, ctx->stream>>>(
-      X, N, (int)N, Ns, out, b.ldN, b.psN, MIXED_PIECES);
+  if (N % 4 == 0) {      // 16-byte aligned columns
+    dim3 grid((unsigned)((N / 4 + 255) / 256), Ns);
+    split_cols_f32x4_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, out, b.ldN, b.psN,
+                                                            MIXED_PIECES);
+  } else {
+    split_cols_kernel<float><<<grid_for(N * Ns), 256, 0, ctx->stream>>>(
+        X, N, (int)N, Ns, out, b.ldN, b.psN, MIXED_PIECES);
+  }
 }
 
 static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBuffers& b) {
@@ -212,12 +253,23 @@ static Operand op_mat(const __nv_bfloat16* base, int Ns, const MixedBuffers& b) 
   return Operand{base, Ns, Ns, b.ldS, b.psS, MIXED_PIECES};
 }
 
+// Split-K factor for `tiles` output tiles: each CTA keeps >= 4096 of K, and
+// the CTA count is chosen close to a whole number of waves over the 152 SMs
+// (one 197 KB CTA per SM).
 static int splits_for(int tiles, long long K) {
-  int want = (2 * 152 + tiles - 1) / tiles;
-  long long maxs = K / 4096;           // keep >= 4096 of K per CTA
+  long long maxs = K / 4096;
   if (maxs < 1) maxs = 1;
-  if (want > maxs) want = (int)maxs;
-  return want < 1 ? 1 : want;
+  if (maxs > 64) maxs = 64;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= maxs; ++s) {
+    const long long ctas = (long long)tiles * s;
+    const long long waves = (ctas + 151) / 152;
+    const double eff = (double)ctas / (double)(waves * 152);
+    if (ctas >= 152 && eff >= 0.95) return s;
+    if (eff > best_eff) { best_eff = eff; best = s; }
+  }
+  return best;
 }
 
 // S = A^T B over the grid for two split blocks (upper tiles, mirrored).
@@ -297,7 +349,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     if (rc) return rc;
     {
       Prof p(ctx, ST_TRINV);
-      tri_inverse_transpose_f64(S, Rinv, Ns, ctx->stream);
+      tri_inverse_transpose_f64(S, Rinv, Ns, diag, ctx->stream);
     }
     split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
     split_block_rows(ctx, X, Ns, b);

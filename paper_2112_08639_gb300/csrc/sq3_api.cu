@@ -89,7 +89,9 @@ __global__ void to_float_kernel(const double* a, float* b, long long n) {
 static void free_projectors(Projectors& P) {
   void* ptrs[] = {P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
                   P.ball_valoff, P.ball_val, P.ball_valf, P.gamma,
-                  P.pt_ptr, P.pt_proj, P.pt_val, P.pt_valf};
+                  P.pt_ptr, P.pt_proj, P.pt_val, P.pt_valf,
+                  P.bp_ptr, P.bp_lidx, P.bp_val, P.bp_valf, P.bl_ptr,
+                  P.bl_proj, P.be_ptr, P.be_pt, P.be_val, P.be_valf};
   for (void* p : ptrs) if (p) cudaFree(p);
   P = Projectors{};
 }
@@ -130,8 +132,12 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   }
   {
     Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, Y, (const T*)gC, nullptr, Ns, 1.0,
-                        0.0, 0.0, ctx->stream);
+    launch_cheb_step<T>(ctx, X, nullptr, Y, nullptr, nullptr, Ns, 1.0, 0.0, 0.0,
+                        ctx->stream);
+  }
+  if (ctx->proj.n_proj) {
+    Prof p(ctx, ST_NL_PASS);
+    launch_nl_pass<T>(ctx, Y, (const T*)gC, nullptr, Ns, 1.0, ctx->stream);
   }
   return cuda_err(cudaGetLastError());
 }
@@ -150,10 +156,12 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
-  void* gA;
-  rc = gc_buffer(ctx, Ns, &gA);
+  void *gA, *gB;
+  rc = gc_buffer(ctx, Ns, &gA, &gB);
   if (rc) return rc;
   T* gC = (T*)gA;        // projections gamma c^T of the current iterate
+  T* gN = (T*)gB;        // projections of the step's output
+  const size_t gbytes = (size_t)ctx->proj.n_proj * Ns * sizeof(T);
   T* W = (T*)ctx->wsX;
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   const double s1 = e / (a0 - c);
@@ -162,27 +170,31 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   T* cur = W;      // holds Y_1 after the first step
   T* prev = X;     // holds Y_0
   const bool nl = ctx->proj.n_proj > 0;
+  // one step: local stencil into `out`, then the nonlocal pass in place,
+  // which also accumulates the projections of the result for the next step
+  auto step = [&](const T* yk, const T* ykm1, T* out, double sc1, double sc2,
+                  bool want_next) {
+    {
+      Prof p(ctx, ST_STENCIL);
+      launch_cheb_step<T>(ctx, yk, ykm1, out, nullptr, nullptr, Ns, sc1, c, sc2,
+                          ctx->stream);
+    }
+    if (nl) {
+      Prof p(ctx, ST_NL_PASS);
+      if (want_next) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
+      launch_nl_pass<T>(ctx, out, gC, want_next ? gN : nullptr, Ns, sc1, ctx->stream);
+    }
+  };
   if (nl) {
     Prof p(ctx, ST_NL_PROJECT);
     launch_nl_project<T>(ctx, X, gC, Ns, ctx->stream);
   }
-  {
-    Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, W, gC, nullptr, Ns, s1 / e, c, 0.0,
-                        ctx->stream);
-  }
+  step(X, nullptr, W, s1 / e, 0.0, m > 1);
   for (int k = 2; k <= m; ++k) {
     const double sn = 1.0 / (tau - s);
-    if (nl) {
-      Prof p(ctx, ST_NL_PROJECT);
-      launch_nl_project<T>(ctx, cur, gC, Ns, ctx->stream);
-    }
-    {
-      // Y_k overwrites Y_{k-2} in place (each element reads only its yprev)
-      Prof p(ctx, ST_STENCIL);
-      launch_cheb_step<T>(ctx, cur, prev, prev, gC, nullptr, Ns, 2.0 * sn / e,
-                          c, -s * sn, ctx->stream);
-    }
+    if (nl) std::swap(gC, gN);
+    // Y_k overwrites Y_{k-2} in place (each element reads only its yprev)
+    step(cur, prev, prev, 2.0 * sn / e, -s * sn, k < m);
     std::swap(cur, prev);
     s = sn;
   }
@@ -241,7 +253,7 @@ static int orthonormalise_f64(sq3_ctx* ctx, double* X, int Ns) {
   if (rc) return rc;
   {
     Prof p(ctx, ST_TRINV);
-    tri_inverse_transpose_f64(S, Rinv, Ns, ctx->stream);
+    tri_inverse_transpose_f64(S, Rinv, Ns, diag, ctx->stream);
   }
   GemmArgs g{};
   g.M = (int)N; g.N = Ns; g.K = Ns;
@@ -480,6 +492,70 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   rc = rc ? rc : upload(&P.pt_proj, tproj.data(), tproj.size());
   rc = rc ? rc : upload(&P.pt_val, tval.data(), tval.size());
   rc = rc ? rc : upload(&P.pt_valf, tvalf.data(), tvalf.size());
+  // brick tables for the nonlocal pass (8 x 8 x 8 bricks, x fastest)
+  {
+    const int nx = c->grid.nx, ny = c->grid.ny, nz = c->grid.nz;
+    const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8, nbz = (nz + 7) / 8;
+    const long long nb = (long long)nbx * nby * nbz;
+    std::vector<int> bptr{0}, lptr{0}, lproj, eptr{0};
+    std::vector<short> blidx, ept;
+    std::vector<double> bval, eval;
+    std::vector<int> ids;
+    std::vector<std::vector<std::pair<short, double>>> lists;
+    int maxc = 0;
+    for (long long b = 0; b < nb; ++b) {
+      const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+      auto gidx = [&](int t) -> long long {
+        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7), iz = bz * 8 + (t >> 6);
+        if (ix >= nx || iy >= ny || iz >= nz) return -1;
+        return (long long)ix + (long long)nx * (iy + (long long)ny * iz);
+      };
+      ids.clear();
+      for (int t = 0; t < NL_BRICK_PTS; ++t) {
+        const long long kk = gidx(t);
+        if (kk < 0) continue;
+        for (int e = cnt[kk]; e < cnt[kk + 1]; ++e) ids.push_back(tproj[e]);
+      }
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      lists.assign(ids.size(), {});
+      for (int t = 0; t < NL_BRICK_PTS; ++t) {
+        const long long kk = gidx(t);
+        if (kk >= 0) {
+          for (int e = cnt[kk]; e < cnt[kk + 1]; ++e) {
+            const int l =
+                (int)(std::lower_bound(ids.begin(), ids.end(), tproj[e]) - ids.begin());
+            blidx.push_back((short)l);
+            bval.push_back(tval[e]);
+            lists[l].push_back({(short)t, tval[e]});
+          }
+        }
+        bptr.push_back((int)blidx.size());
+      }
+      for (auto& lst : lists) {
+        for (auto& pr : lst) {
+          ept.push_back(pr.first);
+          eval.push_back(pr.second);
+        }
+        eptr.push_back((int)ept.size());
+      }
+      lproj.insert(lproj.end(), ids.begin(), ids.end());
+      lptr.push_back((int)lproj.size());
+      maxc = std::max(maxc, (int)ids.size());
+    }
+    P.max_chunk_proj = maxc;
+    std::vector<float> bvalf(bval.begin(), bval.end()), evalf(eval.begin(), eval.end());
+    rc = rc ? rc : upload(&P.bp_ptr, bptr.data(), bptr.size());
+    rc = rc ? rc : upload(&P.bp_lidx, blidx.data(), blidx.size());
+    rc = rc ? rc : upload(&P.bp_val, bval.data(), bval.size());
+    rc = rc ? rc : upload(&P.bp_valf, bvalf.data(), bvalf.size());
+    rc = rc ? rc : upload(&P.bl_ptr, lptr.data(), lptr.size());
+    rc = rc ? rc : upload(&P.bl_proj, lproj.data(), lproj.size());
+    rc = rc ? rc : upload(&P.be_ptr, eptr.data(), eptr.size());
+    rc = rc ? rc : upload(&P.be_pt, ept.data(), ept.size());
+    rc = rc ? rc : upload(&P.be_val, eval.data(), eval.size());
+    rc = rc ? rc : upload(&P.be_valf, evalf.data(), evalf.size());
+  }
   c->proj = P;
   if (rc) { free_projectors(c->proj); return rc; }
   return SQ3_OK;

@@ -16,6 +16,9 @@
 #define MIXED_PIECES 3
 // largest Ns accepted by sq3_lanczos_bounds_noalloc (static scratch size)
 #define SQ3_NOALLOC_MAX_NS 8192
+// nonlocal pass: points per CTA (an 8 x 8 x 8 brick) and vectors per CTA
+#define NL_BRICK_PTS 512
+#define NL_VB 32
 
 namespace sq3 {
 
@@ -60,6 +63,23 @@ struct Projectors {
   int* pt_proj = nullptr;
   double* pt_val = nullptr;
   float* pt_valf = nullptr;
+  // per 8 x 8 x 8 brick b of the grid (bricks x-fastest), local point
+  // t = tx + 8 ty + 64 tz: entries bp_ptr[512 b + t] .. bp_ptr[512 b + t + 1]-1
+  // hold the projector as an index into the brick's list
+  // bl_proj[bl_ptr[b] .. bl_ptr[b+1]-1] (bp_lidx) and c_p at the point
+  // (bp_val); the transposed lists per (brick, local projector) slot give
+  // the point (be_pt) and c_p (be_val).  max_chunk_proj = longest list.
+  int* bp_ptr = nullptr;
+  short* bp_lidx = nullptr;
+  double* bp_val = nullptr;
+  float* bp_valf = nullptr;
+  int* bl_ptr = nullptr;
+  int* bl_proj = nullptr;
+  int* be_ptr = nullptr;
+  short* be_pt = nullptr;
+  double* be_val = nullptr;
+  float* be_valf = nullptr;
+  int max_chunk_proj = 0;
 };
 
 }  // namespace sq3
@@ -69,7 +89,7 @@ namespace sq3 {
 enum Stage {
   ST_STENCIL = 0, ST_NL_PROJECT, ST_GRAM, ST_CHOL, ST_TRINV, ST_XRINV,
   ST_HS_GEMM, ST_LANCZOS, ST_CHEB_GEMM, ST_FERMI, ST_D_ACCUM, ST_RHO,
-  ST_SPLIT, ST_COPY, ST_COUNT
+  ST_SPLIT, ST_COPY, ST_NL_PASS, ST_COUNT
 };
 struct ProfRec { int stage; int launches; cudaEvent_t a, b; };
 }  // namespace sq3
@@ -125,6 +145,11 @@ template <typename T>
 void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
                       const T* gC, T* gC_next, int Ns, double s1, double c,
                       double s2, cudaStream_t st);
+// In-place nonlocal pass on a local step's output (see stencil.cu):
+// out += s1 * sum_p c_p gC[p]; gC_next (zeroed, may be null) += gamma c^T out.
+template <typename T>
+void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
+                    double s1, cudaStream_t st);
 // gC[vec * n_proj + p] = gamma_p * sum_k c_p[k] y[k + vec*N]
 template <typename T>
 void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
@@ -141,7 +166,8 @@ struct GemmArgs {
   int splits;                 // split-K factor (EPI_ATOMIC)
   // 1: only tiles on or above the diagonal are computed (C symmetric);
   // 2: B is upper triangular (B(k,n) = 0 for k > n), so K stops at the
-  //    tile's last column.
+  //    tile's last column;
+  // 3: only tiles on or below the diagonal are computed.
   int tri;
   // EPI_CHEB: C = 2*acc - P, P(m,n) = P[m + n*ldp]; trace of C -> *trace.
   const double* P; long long ldp; double* trace;
@@ -154,7 +180,7 @@ void gemm_f64(const GemmArgs& g, Epi epi, cudaStream_t st);
 int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, double* diag_ws,
                        cudaStream_t st);
 void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
-                               cudaStream_t st);
+                               double* diag_ws, cudaStream_t st);
 void symmetrize_f64(double* A, int n, cudaStream_t st);
 void mirror_upper_f64(double* A, int n, cudaStream_t st);
 void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,

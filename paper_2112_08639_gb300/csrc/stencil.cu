@@ -205,6 +205,157 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Vectorised variant for rows whose length is a multiple of the 16-byte
+// vector width VW (4 floats or 2 doubles).  Each thread owns VW consecutive
+// points of one row: global loads and stores are 16-byte vectors, the
+// x-taps come from one contiguous run of VW + 2 PAD shared-memory values,
+// each y-tap is one 16-byte shared load serving VW points, and the
+// register queue holds 16-byte vectors.  Blocks are ordered row-tile-fastest
+// so that the tiles of one vector run together and read each other's halo
+// rows from L2.  The nonlocal term is added by the nonlocal pass afterwards.
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 2)
+cheb_step_vec_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
+                     const T* __restrict__ y, const T* yprev, T* out,
+                     const T* __restrict__ V, T s1, T c, T s2) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::W;
+  constexpr int PAD = ((R + VW - 1) / VW) * VW;
+  constexpr int HS = 2;                                // halo slots per thread
+  constexpr int XW = VW + 2 * PAD;                     // x-window length
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TX = nx / VW;
+  const int Wd = nx + 2 * PAD;
+  const int rows = TY + 2 * R;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = tx * VW;
+  const long long vec = blockIdx.y;
+  const int y0 = blockIdx.x * TY;
+  const int yy = y0 + ty;
+  const int plane = nx * ny;
+  const long long N = (long long)plane * nz;
+  const T* yv = y + vec * N;
+  T* ov = out + vec * N;
+  const T* pv = (yprev != nullptr) ? yprev + vec * N : nullptr;
+  const int col = yy * nx + x0;
+
+  // halo rows of a plane (2R rows x TX vectors) spread over the threads
+  int hsrc[HS], hdst[HS];
+  const int nhalo = 2 * R * TX;
+#pragma unroll
+  for (int sl = 0; sl < HS; ++sl) {
+    const int e = tid + sl * blockDim.x;
+    hsrc[sl] = -1;
+    hdst[sl] = 0;
+    if (e < nhalo) {
+      const int r = e / TX, hx = e - r * TX;
+      const int srow = (r < R) ? r : r + TY;
+      int gy = (y0 - R + srow) % ny;
+      gy += (gy < 0) ? ny : 0;
+      hsrc[sl] = gy * nx + hx * VW;
+      hdst[sl] = srow * Wd + PAD + hx * VW;
+    }
+  }
+  const bool padr = x0 < PAD;             // also feeds the right pad
+  const bool padl = x0 >= nx - PAD;       // also feeds the left pad
+
+  VT q[2 * R + 1];
+  VT la, ypn;
+#pragma unroll
+  for (int i = 1; i < 2 * R + 1; ++i) {
+    int zz = i - 1 - R;
+    zz += (zz < 0) ? nz : 0;
+    zz -= (zz >= nz) ? nz : 0;
+    q[i] = *reinterpret_cast<const VT*>(yv + zz * plane + col);
+  }
+  la = *reinterpret_cast<const VT*>(yv + (R % nz) * plane + col);
+  if (s2 != T(0)) ypn = *reinterpret_cast<const VT*>(pv + col);
+  else ypn = VT{};
+
+  for (int z = 0; z < nz; ++z) {
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+    q[2 * R] = la;
+    const VT yp = ypn;
+    const int gz = z * plane;
+    if (z + 1 < nz) {
+      int zl = z + 1 + R;
+      zl -= (zl >= nz) ? nz : 0;
+      zl -= (zl >= nz) ? nz : 0;
+      la = __ldg(reinterpret_cast<const VT*>(yv + zl * plane + col));
+      if (s2 != T(0)) ypn = *reinterpret_cast<const VT*>(pv + gz + plane + col);
+    }
+    const VT vz = __ldg(reinterpret_cast<const VT*>(V + gz + col));
+    VT hv[HS];
+#pragma unroll
+    for (int sl = 0; sl < HS; ++sl)
+      if (hsrc[sl] >= 0) hv[sl] = __ldg(reinterpret_cast<const VT*>(yv + gz + hsrc[sl]));
+
+    __syncthreads();   // previous plane consumed
+    {
+      T* d = sm + (ty + R) * Wd + PAD + x0;
+      *reinterpret_cast<VT*>(d) = q[R];
+      if (padr) *reinterpret_cast<VT*>(d + nx) = q[R];
+      if (padl) *reinterpret_cast<VT*>(d - nx) = q[R];
+    }
+#pragma unroll
+    for (int sl = 0; sl < HS; ++sl) {
+      if (hsrc[sl] >= 0) {
+        T* d = sm + hdst[sl];
+        const int hx0 = hsrc[sl] % nx;
+        *reinterpret_cast<VT*>(d) = hv[sl];
+        if (hx0 < PAD) *reinterpret_cast<VT*>(d + nx) = hv[sl];
+        if (hx0 >= nx - PAD) *reinterpret_cast<VT*>(d - nx) = hv[sl];
+      }
+    }
+    __syncthreads();
+
+    const T* row = sm + (ty + R) * Wd + PAD + x0;
+    T xw[XW];
+#pragma unroll
+    for (int j = 0; j < XW / VW; ++j) {
+      const VT t = *reinterpret_cast<const VT*>(row - PAD + j * VW);
+      const T* tp = reinterpret_cast<const T*>(&t);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) xw[j * VW + i] = tp[i];
+    }
+    T acc[VW];
+    const T* vzp = reinterpret_cast<const T*>(&vz);
+    const T* qc = reinterpret_cast<const T*>(&q[R]);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) acc[i] = (k.diag + vzp[i] - c) * qc[i];
+#pragma unroll
+    for (int p = 1; p <= R; ++p) {
+      const VT up = *reinterpret_cast<const VT*>(row + p * Wd);
+      const VT dn = *reinterpret_cast<const VT*>(row - p * Wd);
+      const T* upp = reinterpret_cast<const T*>(&up);
+      const T* dnp = reinterpret_cast<const T*>(&dn);
+      const T* zp = reinterpret_cast<const T*>(&q[R + p]);
+      const T* zm = reinterpret_cast<const T*>(&q[R - p]);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        acc[i] += k.ax[p] * (xw[PAD + i + p] + xw[PAD + i - p]);
+        acc[i] += k.ay[p] * (upp[i] + dnp[i]);
+        acc[i] += k.az[p] * (zp[i] + zm[i]);
+      }
+    }
+    VT o;
+    T* op = reinterpret_cast<T*>(&o);
+    const T* ypp = reinterpret_cast<const T*>(&yp);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) op[i] = s1 * acc[i] + s2 * ypp[i];
+    *reinterpret_cast<VT*>(ov + gz + col) = o;
+  }
+}
+
 static int pick_ty(int nx, int ny, int target) {
   int best = 1;
   for (int t = 1; t <= ny; ++t)
@@ -244,9 +395,7 @@ static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   const int TY = pick_ty(g.nx, g.ny, 512);
   dim3 grid((g.ny + TY - 1) / TY, (Ns + VB - 1) / VB);
   dim3 block(g.nx * TY);
-  const bool nl = ctx->proj.n_proj > 0;
   size_t smem = (size_t)VB * (TY + 2 * R) * (g.nx + 2 * R) * sizeof(T);
-  if (nl) smem += (size_t)ctx->proj.n_proj * VB * sizeof(T);
   const T* V;
   const T* pv;
   if constexpr (sizeof(T) == 8) {
@@ -260,15 +409,58 @@ static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<grid, block, smem, st>>>(g.nx, g.ny, g.nz, Ns, TY, k, y, yprev, out, V,
-                                  nl ? gC : nullptr, ctx->proj.pt_ptr, ctx->proj.pt_proj,
+                                  nullptr, ctx->proj.pt_ptr, ctx->proj.pt_proj,
                                   pv, ctx->proj.n_proj, T(s1), T(c), T(s2));
   (void)gC_next;
+}
+
+// Vectorised launch when the grid allows it; returns false otherwise.
+template <typename T, int R>
+static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
+                       const T* gC, int Ns, double s1, double c, double s2,
+                       cudaStream_t st) {
+  constexpr int VW = Vec16<T>::W;
+  constexpr int PAD = ((R + VW - 1) / VW) * VW;
+  const Grid& g = ctx->grid;
+  static int disabled = -1;
+  if (disabled < 0) {
+    const char* e = getenv("SQ3_STENCIL_GENERIC");
+    disabled = (e && atoi(e) == 1) ? 1 : 0;
+  }
+  if (disabled) return false;
+  if (g.nx % VW || g.nx < PAD) return false;
+  const int TX = g.nx / VW;
+  int TY = 0;
+  for (int t = 1; t <= g.ny; ++t)
+    if (g.ny % t == 0 && TX * t <= 256 && 2 * TX * t >= 2 * R * TX) TY = t;
+  if (TY == 0) return false;
+  StepCoef<T> k{};
+  const double ix = 1.0 / (g.hx * g.hx), iy = 1.0 / (g.hy * g.hy),
+               iz = 1.0 / (g.hz * g.hz);
+  k.diag = T(-0.5 * g.w[0] * (ix + iy + iz));
+  for (int p = 1; p <= R; ++p) {
+    k.ax[p] = T(-0.5 * g.w[p] * ix);
+    k.ay[p] = T(-0.5 * g.w[p] * iy);
+    k.az[p] = T(-0.5 * g.w[p] * iz);
+  }
+  const T* V;
+  if constexpr (sizeof(T) == 8) V = reinterpret_cast<const T*>(ctx->V);
+  else V = reinterpret_cast<const T*>(ctx->Vf);
+  size_t smem = (size_t)(TY + 2 * R) * (g.nx + 2 * PAD) * sizeof(T);
+  auto kern = cheb_step_vec_kernel<T, R>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(g.ny / TY, Ns);    // the row tiles of one vector run together
+  kern<<<grid, TX * TY, smem, st>>>(g.nx, g.ny, g.nz, TY, k, y, yprev, out, V,
+                                    T(s1), T(c), T(s2));
+  return true;
 }
 
 template <typename T, int R>
 static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
                      const T* gC, T* gC_next, int Ns, double s1, double c,
                      double s2, cudaStream_t st) {
+  if (launch_vec<T, R>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st)) return;
   switch (stencil_vb(sizeof(T))) {
     case 1: launch_rv<T, R, 1>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
     case 2: launch_rv<T, R, 2>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
@@ -368,6 +560,123 @@ void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
       ctx->grid.N, Ns, y, P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
       P.ball_valoff, val, P.gamma, P.n_proj, gC);
 }
+
+// ---------------------------------------------------------------------------
+// Nonlocal pass, in place on the output of a local stencil step:
+//   out_v[k] += s1 sum_p c_p[k] gC[v][p]                      (apply)
+//   gC_next[v][p] += gamma_p sum_k c_p[k] out_v[k]            (projection)
+// A CTA owns one 8 x 8 x 8 brick of grid points (a compact brick touches
+// few projectors) and NL_VB vectors.  Phase 1, one thread per point: the
+// coefficients of the projectors touching the brick are staged in shared
+// memory ([vector][local projector]); the point's entries are read once and
+// applied to all NL_VB vectors from registers; the results are written back
+// and kept in shared memory.  Phase 2, one thread per (projector, vector)
+// pair: the projection over the brick is summed from the brick's transposed
+// entry list and the staged results, then added with one global atomic.
+// Points outside every projector are untouched.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NL_BRICK_PTS)
+nl_pass_kernel(int nx, int ny, int nz, int Ns, T* out, const T* __restrict__ gC,
+               T* gC_next, T s1, const int* __restrict__ bp_ptr,
+               const short* __restrict__ bp_lidx, const T* __restrict__ bp_val,
+               const int* __restrict__ bl_ptr, const int* __restrict__ bl_proj,
+               const int* __restrict__ be_ptr, const short* __restrict__ be_pt,
+               const T* __restrict__ be_val, const double* __restrict__ gamma,
+               int n_proj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int YS = NL_BRICK_PTS + 1;               // padded row of ybuf
+  const int b = blockIdx.x;
+  const int v0 = blockIdx.y * NL_VB;
+  const int nv = min(NL_VB, Ns - v0);
+  const int c0 = bl_ptr[b], nloc = bl_ptr[b + 1] - c0;
+  if (nloc == 0) return;
+  T* ybuf = reinterpret_cast<T*>(smem_raw);          // NL_VB x YS
+  T* gloc = ybuf + (size_t)NL_VB * YS;               // NL_VB x nloc
+  const int tid = threadIdx.x;
+  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
+    const int v = i / nloc, l = i - v * nloc;
+    gloc[i] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + bl_proj[c0 + l]] : T(0);
+  }
+  __syncthreads();
+  // phase 1: apply
+  const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
+  const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+  const int ix = bx * 8 + (tid & 7), iy = by * 8 + ((tid >> 3) & 7), iz = bz * 8 + (tid >> 6);
+  const long long N = (long long)nx * ny * nz;
+  const long long k = (long long)ix + (long long)nx * (iy + (long long)ny * iz);
+  const int pe = b * NL_BRICK_PTS + tid;
+  const int e0 = bp_ptr[pe], e1 = bp_ptr[pe + 1];
+  if (e1 > e0) {
+    T acc[NL_VB];
+#pragma unroll
+    for (int v = 0; v < NL_VB; ++v) acc[v] = T(0);
+    for (int e = e0; e < e1; ++e) {
+      const T val = bp_val[e];
+      const T* gl = gloc + bp_lidx[e];
+#pragma unroll
+      for (int v = 0; v < NL_VB; ++v) acc[v] += val * gl[v * nloc];
+    }
+#pragma unroll
+    for (int v = 0; v < NL_VB; ++v) {
+      if (v < nv) {
+        T* o = out + (long long)(v0 + v) * N + k;
+        const T yv = *o + s1 * acc[v];
+        *o = yv;
+        ybuf[v * YS + tid] = yv;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = T(0);
+  }
+  if (gC_next == nullptr) return;
+  __syncthreads();
+  // phase 2: projection sums per (local projector, vector)
+  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
+    const int l = i / NL_VB, v = i - l * NL_VB;
+    if (v >= nv) continue;
+    const T* yb = ybuf + v * YS;
+    T a = T(0);
+    for (int e = be_ptr[c0 + l]; e < be_ptr[c0 + l + 1]; ++e) a += be_val[e] * yb[be_pt[e]];
+    if (a != T(0)) {
+      const int pid = bl_proj[c0 + l];
+      atomicAdd(gC_next + (long long)(v0 + v) * n_proj + pid, T(gamma[pid]) * a);
+    }
+  }
+}
+
+template <typename T>
+void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
+                    double s1, cudaStream_t st) {
+  const Projectors& P = ctx->proj;
+  if (P.n_proj == 0) return;
+  const Grid& g = ctx->grid;
+  const int nb = ((g.nx + 7) / 8) * ((g.ny + 7) / 8) * ((g.nz + 7) / 8);
+  const size_t smem =
+      ((size_t)NL_VB * (NL_BRICK_PTS + 1) + (size_t)P.max_chunk_proj * NL_VB) * sizeof(T);
+  auto kern = nl_pass_kernel<T>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(nb, (Ns + NL_VB - 1) / NL_VB);
+  const T* pv;
+  const T* cev;
+  if constexpr (sizeof(T) == 8) {
+    pv = reinterpret_cast<const T*>(P.bp_val);
+    cev = reinterpret_cast<const T*>(P.be_val);
+  } else {
+    pv = reinterpret_cast<const T*>(P.bp_valf);
+    cev = reinterpret_cast<const T*>(P.be_valf);
+  }
+  kern<<<grid, NL_BRICK_PTS, smem, st>>>(g.nx, g.ny, g.nz, Ns, out, gC, gC_next, T(s1),
+                                         P.bp_ptr, P.bp_lidx, pv, P.bl_ptr, P.bl_proj,
+                                         P.be_ptr, P.be_pt, cev, P.gamma, P.n_proj);
+}
+
+template void launch_nl_pass<double>(const sq3_ctx*, double*, const double*, double*, int,
+                                     double, cudaStream_t);
+template void launch_nl_pass<float>(const sq3_ctx*, float*, const float*, float*, int,
+                                    double, cudaStream_t);
 
 template void launch_cheb_step<double>(const sq3_ctx*, const double*,
                                        const double*, double*, const double*,

@@ -7,10 +7,11 @@
 // sum_(p,q) A_p B_q, each issued as tcgen05.mma kind::f16 with BF16 inputs
 // and FP32 accumulation in tensor memory (TMEM).
 //
-// Tile: 128 x 128 output, K stepped by 64 (one 128-byte swizzle row of
-// bf16).  Operands are K-major; each stage holds all pieces of a 128 x 64 A
-// tile and a 128 x 64 B tile, loaded by one 3-D TMA copy per operand with
-// 128-byte swizzle.  One thread issues the TMA copies and the MMAs; a
+// Tile: 128 x 128 output, K stepped by 32 per shared-memory stage (one
+// 64-byte swizzle row of bf16).  Operands are K-major; each stage holds all
+// pieces of a 128 x 32 A tile and a 128 x 32 B tile, loaded by one 3-D TMA
+// copy per operand with 64-byte swizzle; four stages (three pieces) keep
+// three copies in flight while the tensor core works on the fourth.  One thread issues the TMA copies and the MMAs; a
 // multi-stage mbarrier ring overlaps the copies of later K-blocks with the
 // MMAs of the current one.  The accumulator (128 lanes x 128 FP32 columns)
 // is read back by four warps with tcgen05.ld, each warp owning 32 rows, and
@@ -33,8 +34,10 @@ namespace sq3 {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int TILE_BYTES = 128 * BK * 2;          // one piece of a 128 x 64 tile
+constexpr int BM = 128, BN = 128;
+constexpr int BK = 32;                            // K per smem stage (64-byte rows)
+constexpr int KPP = 2;                            // stages per TMEM partial (64 of K)
+constexpr int TILE_BYTES = 128 * BK * 2;          // one piece of a 128 x 32 tile
 constexpr int SMEM_BUDGET = 196608;               // bytes of tile stages
 constexpr unsigned long long WAIT_NS = 1000000000ull;  // 1 s
 
@@ -90,15 +93,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), version 1, base offset 0.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle (one
+// 32-element bf16 row per 64 bytes), 8-row groups 512 bytes apart (SBO),
+// version 1, base offset 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused, SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset
   d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                 // 64-byte swizzle
   return d;
 }
 
@@ -254,9 +258,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
     for (; issued < nk && issued < STAGES; ++issued) issue(issued);
     for (int kb = 0; kb < nk && ok; ++kb) {
       const int s = kb % STAGES;
-      const int buf = kb & 1;
-      // the accumulator used two K-blocks ago must have been drained
-      if (kb >= 2 && !mbar_wait(acce0 + 8 * buf, ((kb - 2) >> 1) & 1)) { ok = false; break; }
+      const int grp = kb / KPP;                 // TMEM partial this stage feeds
+      const int buf = grp & 1;
+      const bool first = (kb % KPP) == 0;
+      const bool last = (kb % KPP) == KPP - 1 || kb == nk - 1;
+      // the accumulator used two partials ago must have been drained
+      if (first && grp >= 2 && !mbar_wait(acce0 + 8 * buf, ((grp - 2) >> 1) & 1)) {
+        ok = false;
+        break;
+      }
       if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = base + s * STAGE_BYTES;
@@ -267,11 +277,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         const uint32_t pb = sb + p.prod_b[q] * TILE_BYTES;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
-          mma_bf16(td, sw128_desc(pa + kk * 32), sw128_desc(pb + kk * 32), idesc,
-                   (q > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(td, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
+                   (!first || q > 0 || kk > 0) ? 1u : 0u);
       }
       mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
-      mma_commit(accf0 + 8 * buf);     // K-block partial ready
+      if (last) mma_commit(accf0 + 8 * buf);   // partial of up to KPP stages ready
       if (kb >= 1 && issued < nk) {
         const int sp = (kb - 1) % STAGES;
         if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / STAGES) & 1)) { ok = false; break; }
@@ -295,8 +305,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
 #pragma unroll
   for (int i = 0; i < ACC_COLS; ++i) { sum[i] = 0.f; comp[i] = 0.f; }
   bool have = nk > 0;
+  const int ngrp = (nk + KPP - 1) / KPP;
   if (accw) {
-    for (int kb = 0; kb < nk; ++kb) {
+    for (int kb = 0; kb < ngrp; ++kb) {
       const int buf = kb & 1;
       if (!mbar_wait(accf0 + 8 * buf, (kb >> 1) & 1)) {
         have = false;
@@ -397,7 +408,7 @@ static int make_map(CUtensorMap* map, const Operand& o, int box_rows) {
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)o.pieces};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)o.base, dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SQ3_OK : SQ3_ECUDA;
 }

@@ -202,7 +202,7 @@ class Context:
         return rho
 
     STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
-              "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy")
+              "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy", "nl_pass")
 
     def profile(self, enable: bool = True):
         _check(lib.sq3_profile_enable(self._h, int(enable)), "sq3_profile_enable")
