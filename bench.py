@@ -211,7 +211,8 @@ def run_sq3(args, rank, world):
     stage_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1] or v[0]}
     pk, pk_src = peaks()
     dominant = max(prof, key=lambda k: prof[k][0])
-    roof = roofline(dominant, prof, cfg, esize, prec == sq3.FP64, pk, pk_src, args.steps)
+    n_cov = int(np.unique(cell.proj.idx).size) if cell.proj is not None else 0
+    roof = roofline(dominant, prof, cfg, esize, prec == sq3.FP64, pk, pk_src, args.steps, n_cov)
     clocks = clk.summary()
     res = {
         "metric": METRIC,
@@ -247,44 +248,49 @@ def run_sq3(args, rank, world):
     return res
 
 
-def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps):
+def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
     """Roofline entry for the kernel class that takes the most device time.
 
-    Algorithmic work per launch: the stencil moves 3 words per grid point per
-    vector (read Y_k and Y_{k-1}, write Y_{k+1}) and does 2*(6*3*2+2) = 76
-    flop plus the recurrence update; GEMM classes count 2*M*N*K useful flops.
+    Algorithmic work per launch:
+      stencil   3 words per grid point per vector (read Y_k and Y_{k-1},
+                write Y_{k+1}); FP64 path: ~80 flop per point per vector
+      nl_pass   read and write of the step's output at the n_covered grid
+                points inside at least one projector
+      GEMMs     useful flops: Gram and X^T(HX) N Ns^2 (upper triangle),
+                X R^{-1} N Ns^2 (triangular), X Ds 2 N Ns^2, recurrence 2 Ns^3
     """
-    N, Ns, npl = cfg.N, cfg.Ns, cfg.npl
+    N, Ns = cfg.N, cfg.Ns
     ms, n = prof[dominant]
-    per_launch_ms = ms / max(n, 1)
-    gemm_flops = {"gram": N * Ns * Ns, "hs_gemm": N * Ns * Ns, "x_rinv": N * Ns * Ns,
-                  "rho": 2 * N * Ns * Ns, "cheb_gemm": 2 * Ns ** 3}
+    per_launch_s = ms / max(n, 1) / 1e3
+    fp64_peak = {"peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                 "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    hbm_peak = {"peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src + " (MEASURED_PEAKS hbm_gbs)"}
     if dominant == "stencil":
         if fp64:
-            flops = 80.0 * N * Ns
-            ach = flops / (per_launch_ms / 1e3) / 1e12
-            return {"bound": "alu", "kernel": "cheb_step (FP64 stencil)", "achieved": round(ach, 4),
-                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                    "traffic": None, "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz"}
-        byts = 3.0 * N * Ns * esize
-        ach = byts / (per_launch_ms / 1e3) / 1e9
-        return {"bound": "hbm", "kernel": "cheb_step (FP32 stencil)", "achieved": round(ach, 1),
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
-                "traffic": None, "peak_source": pk_src}
+            ach = 80.0 * N * Ns / per_launch_s / 1e12
+            return dict(bound="alu", kernel="cheb_step (FP64 stencil)", achieved=round(ach, 4),
+                        frac=round(ach / FP64_PEAK_TFLOPS, 4), traffic=None, **fp64_peak)
+        ach = 3.0 * N * Ns * esize / per_launch_s / 1e9
+        return dict(bound="hbm", kernel="cheb_step_vec (FP32 stencil)", achieved=round(ach, 1),
+                    frac=round(ach / pk["hbm_gbs"], 4), traffic=None, **hbm_peak)
+    if dominant == "nl_pass":
+        ach = 2.0 * n_covered * Ns * esize / per_launch_s / 1e9
+        return dict(bound="hbm", kernel="nl_pass (nonlocal apply + projection)",
+                    achieved=round(ach, 1), frac=round(ach / pk["hbm_gbs"], 4), traffic=None,
+                    **hbm_peak)
+    gemm_flops = {"gram": N * Ns * Ns, "hs_gemm": N * Ns * Ns, "x_rinv": N * Ns * Ns,
+                  "rho": 2 * N * Ns * Ns, "cheb_gemm": 2 * Ns ** 3}
     if dominant in gemm_flops:
-        f = gemm_flops[dominant]
-        if dominant == "cheb_gemm":
-            f = 2 * Ns ** 3
-        ach = f / (per_launch_ms / 1e3) / 1e12
+        ach = gemm_flops[dominant] / per_launch_s / 1e12
         if fp64:
-            return {"bound": "alu", "kernel": f"{dominant} (FP64 GEMM)", "achieved": round(ach, 4),
-                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                    "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                    "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz"}
+            return dict(bound="alu", kernel=f"{dominant} (FP64 GEMM)", achieved=round(ach, 4),
+                        frac=round(ach / FP64_PEAK_TFLOPS, 4), traffic=None, **fp64_peak)
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        return {"bound": "tensor", "kernel": f"{dominant} (tcgen05 bf16 split)", "achieved": round(ach, 2),
-                "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_source": pk_src + " sustained bf16"}
+        # six BF16 piece products are issued per useful FP32-level product
+        return dict(bound="tensor", kernel=f"{dominant} (tcgen05, 6 BF16 piece products)",
+                    achieved=round(6 * ach, 2), useful=round(ach, 2), peak=peak, unit="TFLOP/s",
+                    frac=round(6 * ach / peak, 4), traffic=None,
+                    peak_source=pk_src + " (bf16_tflops_sustained)")
     return {"bound": "unknown", "kernel": dominant, "achieved": None, "peak": None, "unit": None,
             "frac": None, "traffic": None}
 

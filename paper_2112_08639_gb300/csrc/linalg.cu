@@ -30,7 +30,10 @@ __global__ void copy_diag_kernel(const double* S, int n, double* d) {
 
 // Factor the kb x kb diagonal block at (k0, k0) of the column-major n x n S.
 // A pivot that is not above 1e-13 times the original diagonal entry diag0
-// (numerically rank-deficient X) or is not finite sets DEV_NOTPD.
+// (numerically rank-deficient X) or is not finite sets DEV_NOTPD.  The
+// shared block A keeps the running Schur complement; step j reads column j
+// of A, writes column j of the factor straight to S and updates the trailing
+// part of A, so one barrier per column suffices.
 __global__ void __launch_bounds__(256)
 potrf_diag_kernel(double* S, int n, int k0, int kb, const double* diag0,
                   int* status) {
@@ -41,28 +44,20 @@ potrf_diag_kernel(double* S, int n, int k0, int kb, const double* diag0,
   }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    if (threadIdx.x == 0) {
-      double d = A[j][j];
-      if (!(d > 1e-13 * diag0[k0 + j]) || !isfinite(d)) {
-        set_status(status, DEV_NOTPD);
-        d = 1.0;
-      }
-      A[j][j] = sqrt(d);
+    double d = A[j][j];
+    if (!(d > 1e-13 * diag0[k0 + j]) || !isfinite(d)) {
+      if (threadIdx.x == 0) set_status(status, DEV_NOTPD);
+      d = 1.0;
     }
-    __syncthreads();
-    const double djj = A[j][j];
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][j] /= djj;
-    __syncthreads();
+    const double sd = sqrt(d), inv = 1.0 / d;
+    for (int i = j + threadIdx.x; i < kb; i += blockDim.x)
+      S[(k0 + i) + (long long)(k0 + j) * n] = (i == j) ? sd : A[i][j] / sd;
     const int m = kb - j - 1;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e % m, l = j + 1 + e / m;
-      if (l <= i) A[i][l] -= A[i][j] * A[l][j];
+      const int i = j + 1 + e % m, l = j + 1 + e / m;
+      if (l <= i) A[i][l] -= A[i][j] * A[l][j] * inv;
     }
     __syncthreads();
-  }
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    int i = e % kb, j = e / kb;
-    if (i >= j) S[(k0 + i) + (long long)(k0 + j) * n] = A[i][j];
   }
 }
 

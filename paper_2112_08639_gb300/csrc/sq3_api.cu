@@ -492,21 +492,22 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   rc = rc ? rc : upload(&P.pt_proj, tproj.data(), tproj.size());
   rc = rc ? rc : upload(&P.pt_val, tval.data(), tval.size());
   rc = rc ? rc : upload(&P.pt_valf, tvalf.data(), tvalf.size());
-  // brick tables for the nonlocal pass (8 x 8 x 8 bricks, x fastest)
+  // brick tables for the nonlocal pass (8 x 8 x NL_BZ bricks, x fastest)
   {
     const int nx = c->grid.nx, ny = c->grid.ny, nz = c->grid.nz;
-    const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8, nbz = (nz + 7) / 8;
+    const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8, nbz = (nz + NL_BZ - 1) / NL_BZ;
     const long long nb = (long long)nbx * nby * nbz;
     std::vector<int> bptr{0}, lptr{0}, lproj, eptr{0};
     std::vector<short> blidx, ept;
     std::vector<double> bval, eval;
     std::vector<int> ids;
     std::vector<std::vector<std::pair<short, double>>> lists;
-    int maxc = 0;
+    int maxc = 0, maxe = 0;
     for (long long b = 0; b < nb; ++b) {
+      const int ebeg = (int)blidx.size();
       const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
       auto gidx = [&](int t) -> long long {
-        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7), iz = bz * 8 + (t >> 6);
+        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7), iz = bz * NL_BZ + (t >> 6);
         if (ix >= nx || iy >= ny || iz >= nz) return -1;
         return (long long)ix + (long long)nx * (iy + (long long)ny * iz);
       };
@@ -542,8 +543,15 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
       lproj.insert(lproj.end(), ids.begin(), ids.end());
       lptr.push_back((int)lproj.size());
       maxc = std::max(maxc, (int)ids.size());
+      maxe = std::max(maxe, (int)blidx.size() - ebeg);
     }
     P.max_chunk_proj = maxc;
+    P.max_brick_entries = maxe;
+    // shared memory of the nonlocal pass (FP64 variant, 16 vectors per CTA)
+    const size_t need = ((size_t)16 * (NL_BRICK_PTS + 1) + (size_t)36 * maxc + 2 * maxe) * 8 +
+                        (size_t)2 * maxe * 2 + 16;
+    (void)nbz;
+    if (need > 227 * 1024) rc = SQ3_EINVAL;
     std::vector<float> bvalf(bval.begin(), bval.end()), evalf(eval.begin(), eval.end());
     rc = rc ? rc : upload(&P.bp_ptr, bptr.data(), bptr.size());
     rc = rc ? rc : upload(&P.bp_lidx, blidx.data(), blidx.size());

@@ -16,9 +16,9 @@
 #define MIXED_PIECES 3
 // largest Ns accepted by sq3_lanczos_bounds_noalloc (static scratch size)
 #define SQ3_NOALLOC_MAX_NS 8192
-// nonlocal pass: points per CTA (an 8 x 8 x 8 brick) and vectors per CTA
-#define NL_BRICK_PTS 512
-#define NL_VB 32
+// nonlocal pass: points per CTA (an 8 x 8 x NL_BZ brick)
+#define NL_BZ 4
+#define NL_BRICK_PTS (64 * NL_BZ)
 
 namespace sq3 {
 
@@ -63,8 +63,9 @@ struct Projectors {
   int* pt_proj = nullptr;
   double* pt_val = nullptr;
   float* pt_valf = nullptr;
-  // per 8 x 8 x 8 brick b of the grid (bricks x-fastest), local point
-  // t = tx + 8 ty + 64 tz: entries bp_ptr[512 b + t] .. bp_ptr[512 b + t + 1]-1
+  // per 8 x 8 x NL_BZ brick b of the grid (bricks x-fastest), local point
+  // t = tx + 8 ty + 64 tz: entries bp_ptr[NL_BRICK_PTS b + t] ..
+  // bp_ptr[NL_BRICK_PTS b + t + 1] - 1
   // hold the projector as an index into the brick's list
   // bl_proj[bl_ptr[b] .. bl_ptr[b+1]-1] (bp_lidx) and c_p at the point
   // (bp_val); the transposed lists per (brick, local projector) slot give
@@ -80,6 +81,7 @@ struct Projectors {
   double* be_val = nullptr;
   float* be_valf = nullptr;
   int max_chunk_proj = 0;
+  int max_brick_entries = 0;   // largest number of entries in one brick
 };
 
 }  // namespace sq3

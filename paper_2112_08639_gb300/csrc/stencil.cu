@@ -19,11 +19,15 @@
 // tile's y-halo; yprev, V and out stream once.  The nonlocal term is added
 // from a per-point table of (projector, c_p[k]) and the precomputed
 // coefficients gC = gamma (c^T y) of the same vector.
+#include <stdint.h>
 #include <stdlib.h>
 
+#include "async_copy.cuh"
 #include "sq3_internal.cuh"
 
 namespace sq3 {
+
+using namespace ac;
 
 template <typename T>
 struct StepCoef {
@@ -356,6 +360,149 @@ cheb_step_vec_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
   }
 }
 
+// Pipelined form of the vectorised step.  The same tile and register queue,
+// but every plane's inputs arrive by asynchronous copies issued A planes
+// ahead into a ring of A + 1 shared-memory entries, so each thread keeps
+// several planes of loads in flight without holding them in registers:
+//   window ring : y plane z, TY + 2R rows with PAD wrapped columns per side
+//                 (the x- and y-taps);
+//   centre ring : y plane z + R on the CTA's own rows (the queue's new
+//                 entry), V and yprev of plane z.
+// The centre copy is the first touch of each element; the window copy of
+// the same rows R planes later hits L2.  One barrier per plane.
+template <typename T, int R, int A>
+__global__ void __launch_bounds__(256, 2)
+cheb_step_ring_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
+                      const T* __restrict__ y, const T* yprev, T* out,
+                      const T* __restrict__ V, T s1, T c, T s2) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::W;
+  constexpr int PAD = ((R + VW - 1) / VW) * VW;
+  constexpr int PV = PAD / VW;
+  constexpr int XW = VW + 2 * PAD;
+  constexpr int KC = 4;                  // window copies per thread per plane
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TX = nx / VW;
+  const int Wd = nx + 2 * PAD;
+  const int rows = TY + 2 * R;
+  const int wsz = rows * Wd;             // one window entry
+  const int csz = TY * nx;               // one centre array
+  T* win = reinterpret_cast<T*>(smem_raw);
+  T* cen = win + (A + 1) * wsz;          // (A + 1) entries of 3 centre arrays
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = tx * VW;
+  const long long vec = blockIdx.y;
+  const int y0 = blockIdx.x * TY;
+  const int plane = nx * ny;
+  const long long N = (long long)plane * nz;
+  const T* yv = y + vec * N;
+  T* ov = out + vec * N;
+  const T* pv = (s2 != T(0)) ? yprev + vec * N : nullptr;
+  const int col = (y0 + ty) * nx + x0;
+  const int cofs = ty * nx + x0;
+
+  // this thread's share of a window: (row, 16-byte vector) pairs
+  const int rv = TX + 2 * PV;
+  int wsrc[KC], wdst[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) {
+    const int e = tid + j * nthr;
+    wsrc[j] = -1;
+    wdst[j] = 0;
+    if (e < rows * rv) {
+      const int r = e / rv, v = e - r * rv;
+      int gy = (y0 - R + r) % ny;
+      gy += (gy < 0) ? ny : 0;
+      int sx = v * VW - PAD;
+      sx += (sx < 0) ? nx : 0;
+      sx -= (sx >= nx) ? nx : 0;
+      wsrc[j] = gy * nx + sx;
+      wdst[j] = r * Wd + v * VW;
+    }
+  }
+  // entry `it`: window of plane it, centre of plane it + R, V and yprev of it
+  auto issue = [&](int it) {
+    if (it < nz) {
+      const int sl = it % (A + 1);
+      T* w = win + sl * wsz;
+      const T* src = yv + (long long)it * plane;
+#pragma unroll
+      for (int j = 0; j < KC; ++j)
+        if (wsrc[j] >= 0) cp_async16(w + wdst[j], src + wsrc[j]);
+      T* ce = cen + sl * 3 * csz;
+      int zq = it + R;
+      zq -= (zq >= nz) ? nz : 0;
+      zq -= (zq >= nz) ? nz : 0;
+      cp_async16(ce + cofs, yv + (long long)zq * plane + col);
+      cp_async16(ce + csz + cofs, V + (long long)it * plane + col);
+      if (pv) cp_async16(ce + 2 * csz + cofs, pv + (long long)it * plane + col);
+    }
+    cp_async_commit();
+  };
+
+  VT q[2 * R + 1];
+#pragma unroll
+  for (int i = 1; i < 2 * R + 1; ++i) {
+    int zz = i - 1 - R;
+    zz += (zz < 0) ? nz : 0;
+    zz -= (zz >= nz) ? nz : 0;
+    q[i] = __ldg(reinterpret_cast<const VT*>(yv + (long long)zz * plane + col));
+  }
+#pragma unroll
+  for (int it = 0; it < A; ++it) issue(it);
+
+  for (int z = 0; z < nz; ++z) {
+    cp_async_wait<A - 1>();
+    __syncthreads();     // entry z landed for all; entry z - 1 fully consumed
+    issue(z + A);        // reuses the slot of entry z - 1
+    const int sl = z % (A + 1);
+    const T* ce = cen + sl * 3 * csz;
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
+    q[2 * R] = *reinterpret_cast<const VT*>(ce + cofs);
+    const VT vz = *reinterpret_cast<const VT*>(ce + csz + cofs);
+    const VT yp = pv ? *reinterpret_cast<const VT*>(ce + 2 * csz + cofs) : VT{};
+    const T* row = win + sl * wsz + (ty + R) * Wd + PAD + x0;
+    T xw[XW];
+#pragma unroll
+    for (int j = 0; j < XW / VW; ++j) {
+      const VT t = *reinterpret_cast<const VT*>(row - PAD + j * VW);
+      const T* tp = reinterpret_cast<const T*>(&t);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) xw[j * VW + i] = tp[i];
+    }
+    T acc[VW];
+    const T* vzp = reinterpret_cast<const T*>(&vz);
+    const T* qc = reinterpret_cast<const T*>(&q[R]);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) acc[i] = (k.diag + vzp[i] - c) * qc[i];
+#pragma unroll
+    for (int p = 1; p <= R; ++p) {
+      const VT up = *reinterpret_cast<const VT*>(row + p * Wd);
+      const VT dn = *reinterpret_cast<const VT*>(row - p * Wd);
+      const T* upp = reinterpret_cast<const T*>(&up);
+      const T* dnp = reinterpret_cast<const T*>(&dn);
+      const T* zp = reinterpret_cast<const T*>(&q[R + p]);
+      const T* zm = reinterpret_cast<const T*>(&q[R - p]);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        acc[i] += k.ax[p] * (xw[PAD + i + p] + xw[PAD + i - p]);
+        acc[i] += k.ay[p] * (upp[i] + dnp[i]);
+        acc[i] += k.az[p] * (zp[i] + zm[i]);
+      }
+    }
+    VT o;
+    T* op = reinterpret_cast<T*>(&o);
+    const T* ypp = reinterpret_cast<const T*>(&yp);
+#pragma unroll
+    for (int i = 0; i < VW; ++i) op[i] = s1 * acc[i] + s2 * ypp[i];
+    *reinterpret_cast<VT*>(ov + (long long)z * plane + col) = o;
+  }
+  cp_async_wait<0>();
+}
+
 static int pick_ty(int nx, int ny, int target) {
   int best = 1;
   for (int t = 1; t <= ny; ++t)
@@ -429,6 +576,8 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   }
   if (disabled) return false;
   if (g.nx % VW || g.nx < PAD) return false;
+  // 16-byte vector accesses need 16-byte aligned blocks
+  if (((uintptr_t)y | (uintptr_t)out | (uintptr_t)(yprev ? yprev : y)) & 15) return false;
   const int TX = g.nx / VW;
   int TY = 0;
   for (int t = 1; t <= g.ny; ++t)
@@ -446,6 +595,27 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   const T* V;
   if constexpr (sizeof(T) == 8) V = reinterpret_cast<const T*>(ctx->V);
   else V = reinterpret_cast<const T*>(ctx->Vf);
+  static int ring = -1;
+  if (ring < 0) {
+    const char* e = getenv("SQ3_STENCIL_RING");
+    ring = (e && atoi(e) == 0) ? 0 : 1;
+  }
+  const int rv = TX + 2 * (PAD / VW);
+  if (ring && (TY + 2 * R) * rv <= 4 * TX * TY) {
+    constexpr int A = 4;
+    const size_t rs = (size_t)(A + 1) *
+                      ((size_t)(TY + 2 * R) * (g.nx + 2 * PAD) + 3 * (size_t)TY * g.nx) *
+                      sizeof(T);
+    if (rs <= 227 * 1024) {
+      auto kr = cheb_step_ring_kernel<T, R, A>;
+      if (rs > 48 * 1024)
+        cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+      dim3 grid(g.ny / TY, Ns);
+      kr<<<grid, TX * TY, rs, st>>>(g.nx, g.ny, g.nz, TY, k, y, yprev, out, V,
+                                    T(s1), T(c), T(s2));
+      return true;
+    }
+  }
   size_t smem = (size_t)(TY + 2 * R) * (g.nx + 2 * PAD) * sizeof(T);
   auto kern = cheb_step_vec_kernel<T, R>;
   if (smem > 48 * 1024)
@@ -566,80 +736,125 @@ void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
 //   out_v[k] += s1 sum_p c_p[k] gC[v][p]                      (apply)
 //   gC_next[v][p] += gamma_p sum_k c_p[k] out_v[k]            (projection)
 // A CTA owns one 8 x 8 x 8 brick of grid points (a compact brick touches
-// few projectors) and NL_VB vectors.  Phase 1, one thread per point: the
-// coefficients of the projectors touching the brick are staged in shared
-// memory ([vector][local projector]); the point's entries are read once and
-// applied to all NL_VB vectors from registers; the results are written back
-// and kept in shared memory.  Phase 2, one thread per (projector, vector)
-// pair: the projection over the brick is summed from the brick's transposed
-// entry list and the staged results, then added with one global atomic.
-// Points outside every projector are untouched.
+// few projectors) and NL_VB vectors.  It first stages, with independent
+// coalesced loads, the brick's values of its vectors, the brick's
+// projector entries and the coefficients of the projectors touching the
+// brick; phase 1 (one thread per point) applies the term from shared memory
+// and writes the point back; phase 2 (one warp per projector, one lane per
+// vector) sums the projection over the brick from the transposed entry list
+// and adds it with one global atomic.  Points outside every projector are
+// untouched.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NL_BRICK_PTS)
+template <typename T, int NL_VB>
+__global__ void __launch_bounds__(NL_BRICK_PTS, 1)
 nl_pass_kernel(int nx, int ny, int nz, int Ns, T* out, const T* __restrict__ gC,
                T* gC_next, T s1, const int* __restrict__ bp_ptr,
                const short* __restrict__ bp_lidx, const T* __restrict__ bp_val,
                const int* __restrict__ bl_ptr, const int* __restrict__ bl_proj,
                const int* __restrict__ be_ptr, const short* __restrict__ be_pt,
                const T* __restrict__ be_val, const double* __restrict__ gamma,
-               int n_proj) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+               int n_proj, int max_entries) {
   constexpr int YS = NL_BRICK_PTS + 1;               // padded row of ybuf
+  constexpr int GS = NL_VB + 4;                      // padded row of gloc
+  constexpr int VG = 8;                              // vectors per register group
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int v0 = blockIdx.y * NL_VB;
   const int nv = min(NL_VB, Ns - v0);
   const int c0 = bl_ptr[b], nloc = bl_ptr[b + 1] - c0;
   if (nloc == 0) return;
+  const int eb = bp_ptr[b * NL_BRICK_PTS];
+  const int ne = bp_ptr[(b + 1) * NL_BRICK_PTS] - eb;
+  const int fb = be_ptr[c0];
   T* ybuf = reinterpret_cast<T*>(smem_raw);          // NL_VB x YS
-  T* gloc = ybuf + (size_t)NL_VB * YS;               // NL_VB x nloc
+  T* gloc = ybuf + (size_t)NL_VB * YS;               // nloc x GS
+  T* sval = gloc + (size_t)nloc * GS;                // point-ordered entry values
+  T* tval = sval + max_entries;                      // projector-ordered entry values
+  T* pacc = tval + max_entries;                      // nloc x NL_VB projection sums
+  short* slid = reinterpret_cast<short*>(pacc + (size_t)nloc * NL_VB);   // local ids
+  short* tpt = slid + max_entries;                              // brick point ids
   const int tid = threadIdx.x;
-  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
-    const int v = i / nloc, l = i - v * nloc;
-    gloc[i] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + bl_proj[c0 + l]] : T(0);
-  }
-  __syncthreads();
-  // phase 1: apply
   const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
   const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-  const int ix = bx * 8 + (tid & 7), iy = by * 8 + ((tid >> 3) & 7), iz = bz * 8 + (tid >> 6);
+  const int ix = bx * 8 + (tid & 7), iy = by * 8 + ((tid >> 3) & 7);
+  const int iz = bz * NL_BZ + (tid >> 6);
   const long long N = (long long)nx * ny * nz;
   const long long k = (long long)ix + (long long)nx * (iy + (long long)ny * iz);
   const int pe = b * NL_BRICK_PTS + tid;
-  const int e0 = bp_ptr[pe], e1 = bp_ptr[pe + 1];
+  const int e0 = bp_ptr[pe] - eb, e1 = bp_ptr[pe + 1] - eb;
+  // bulk staging with independent coalesced loads
+  T* ob = out + (long long)v0 * N + k;
   if (e1 > e0) {
-    T acc[NL_VB];
+#pragma unroll 8
+    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = (v < nv) ? ob[(long long)v * N] : T(0);
+  } else {
+#pragma unroll 8
+    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = T(0);
+  }
+  for (int e = tid; e < ne; e += blockDim.x) {
+    sval[e] = bp_val[eb + e];
+    slid[e] = bp_lidx[eb + e];
+    tval[e] = be_val[fb + e];
+    tpt[e] = be_pt[fb + e];
+  }
+  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
+    const int l = i / NL_VB, v = i - l * NL_VB;
+    gloc[l * GS + v] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + bl_proj[c0 + l]] : T(0);
+    pacc[i] = T(0);
+  }
+  __syncthreads();
+  // phase 1: apply, VG vectors at a time in registers
+  if (e1 > e0) {
+#pragma unroll 1
+    for (int g = 0; g < NL_VB; g += VG) {
+      T acc[VG];
 #pragma unroll
-    for (int v = 0; v < NL_VB; ++v) acc[v] = T(0);
-    for (int e = e0; e < e1; ++e) {
-      const T val = bp_val[e];
-      const T* gl = gloc + bp_lidx[e];
+      for (int i = 0; i < VG; ++i) acc[i] = T(0);
+      for (int e = e0; e < e1; ++e) {
+        const T val = sval[e];
+        const T* gl = gloc + slid[e] * GS + g;
 #pragma unroll
-      for (int v = 0; v < NL_VB; ++v) acc[v] += val * gl[v * nloc];
-    }
+        for (int i = 0; i < VG; ++i) acc[i] += val * gl[i];
+      }
 #pragma unroll
-    for (int v = 0; v < NL_VB; ++v) {
-      if (v < nv) {
-        T* o = out + (long long)(v0 + v) * N + k;
-        const T yv = *o + s1 * acc[v];
-        *o = yv;
+      for (int i = 0; i < VG; ++i) {
+        const int v = g + i;
+        const T yv = ybuf[v * YS + tid] + s1 * acc[i];
         ybuf[v * YS + tid] = yv;
+        if (v < nv) ob[(long long)v * N] = yv;
       }
     }
-  } else {
-#pragma unroll
-    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = T(0);
   }
   if (gC_next == nullptr) return;
   __syncthreads();
-  // phase 2: projection sums per (local projector, vector)
+  // phase 2: per local projector, each vector's sum is split over NSL
+  // slices of the projector's entry list (lanes v + NL_VB * slice), then
+  // combined with shuffles
+  constexpr int NSL = 32 * 4 / NL_VB;                // slices: 4 (FP32), 8 (FP64)
+  constexpr int WPL = NL_VB * NSL / 32;              // warps per projector (4)
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nw = blockDim.x >> 5;
+  for (int task = warp; task < nloc * WPL; task += nw) {
+    const int l = task / WPL;
+    const int slot = (task - l * WPL) * 32 + lane;   // 0 .. NL_VB * NSL - 1
+    const int v = slot % NL_VB, sl = slot / NL_VB;
+    const int f0 = be_ptr[c0 + l] - fb, f1 = be_ptr[c0 + l + 1] - fb;
+    const int len = f1 - f0;
+    const int a0 = f0 + (len * sl) / NSL, a1 = f0 + (len * (sl + 1)) / NSL;
+    const T* yl = ybuf + v * YS;
+    T a = T(0);
+    for (int f = a0; f < a1; ++f) a += tval[f] * yl[tpt[f]];
+    // lanes of one vector within this warp differ by multiples of NL_VB
+#pragma unroll
+    for (int o = 16; o >= NL_VB; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    // the WPL warps of a projector meet in shared memory (at most WPL-way)
+    if (lane < NL_VB && a != T(0)) atomicAdd(pacc + l * NL_VB + v, a);
+  }
+  __syncthreads();
   for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
     const int l = i / NL_VB, v = i - l * NL_VB;
-    if (v >= nv) continue;
-    const T* yb = ybuf + v * YS;
-    T a = T(0);
-    for (int e = be_ptr[c0 + l]; e < be_ptr[c0 + l + 1]; ++e) a += be_val[e] * yb[be_pt[e]];
-    if (a != T(0)) {
+    const T a = pacc[i];
+    if (v < nv && a != T(0)) {
       const int pid = bl_proj[c0 + l];
       atomicAdd(gC_next + (long long)(v0 + v) * n_proj + pid, T(gamma[pid]) * a);
     }
@@ -652,10 +867,15 @@ void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
   const Projectors& P = ctx->proj;
   if (P.n_proj == 0) return;
   const Grid& g = ctx->grid;
-  const int nb = ((g.nx + 7) / 8) * ((g.ny + 7) / 8) * ((g.nz + 7) / 8);
-  const size_t smem =
-      ((size_t)NL_VB * (NL_BRICK_PTS + 1) + (size_t)P.max_chunk_proj * NL_VB) * sizeof(T);
-  auto kern = nl_pass_kernel<T>;
+  const int nb = ((g.nx + 7) / 8) * ((g.ny + 7) / 8) * ((g.nz + NL_BZ - 1) / NL_BZ);
+  // 32 vectors per CTA in FP32, 16 in FP64 (shared-memory budget)
+  constexpr int NL_VB = sizeof(T) == 4 ? 32 : 16;
+  const size_t smem = ((size_t)NL_VB * (NL_BRICK_PTS + 1) +
+                       (size_t)(2 * NL_VB + 4) * P.max_chunk_proj +
+                       (size_t)2 * P.max_brick_entries) * sizeof(T) +
+                      (size_t)2 * P.max_brick_entries * sizeof(short) + 16;
+  if (smem > 227 * 1024) return;     // reported by the caller's status check
+  auto kern = nl_pass_kernel<T, NL_VB>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(nb, (Ns + NL_VB - 1) / NL_VB);
@@ -670,7 +890,8 @@ void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
   }
   kern<<<grid, NL_BRICK_PTS, smem, st>>>(g.nx, g.ny, g.nz, Ns, out, gC, gC_next, T(s1),
                                          P.bp_ptr, P.bp_lidx, pv, P.bl_ptr, P.bl_proj,
-                                         P.be_ptr, P.be_pt, cev, P.gamma, P.n_proj);
+                                         P.be_ptr, P.be_pt, cev, P.gamma, P.n_proj,
+                                         P.max_brick_entries);
 }
 
 template void launch_nl_pass<double>(const sq3_ctx*, double*, const double*, double*, int,
