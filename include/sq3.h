@@ -93,9 +93,9 @@ int sq3_set_potential(sq3_ctx* ctx, const double* V);
  * Projectors that share an index list (the lm components of one atom) are
  * grouped internally.  n_proj = 0 removes the projectors.  Copied into the
  * context.  Errors: SQ3_ENOTSETUP, SQ3_EINVAL (index out of range, ptr not
- * monotone, or projectors so dense that one 8 x 8 x 8 brick of the grid holds
- * more entries than the nonlocal pass can stage in shared memory, about
- * 7,000). */
+ * monotone, or projectors so dense that one 8 x 8 x 4 brick of the grid holds
+ * more (point, projector) entries than the nonlocal pass can stage in shared
+ * memory, about 7,700). */
 int sq3_set_projectors(sq3_ctx* ctx, int n_proj, const int* ptr,
                        const int* idx, const double* val, const double* gamma);
 

@@ -137,7 +137,8 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   }
   if (ctx->proj.n_proj) {
     Prof p(ctx, ST_NL_PASS);
-    launch_nl_pass<T>(ctx, Y, (const T*)gC, nullptr, Ns, 1.0, ctx->stream);
+    rc = launch_nl_pass<T>(ctx, Y, (const T*)gC, nullptr, Ns, 1.0, ctx->stream);
+    if (rc) return rc;
   }
   return cuda_err(cudaGetLastError());
 }
@@ -172,6 +173,7 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
   const bool nl = ctx->proj.n_proj > 0;
   // one step: local stencil into `out`, then the nonlocal pass in place,
   // which also accumulates the projections of the result for the next step
+  int nrc = SQ3_OK;
   auto step = [&](const T* yk, const T* ykm1, T* out, double sc1, double sc2,
                   bool want_next) {
     {
@@ -179,10 +181,10 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
       launch_cheb_step<T>(ctx, yk, ykm1, out, nullptr, nullptr, Ns, sc1, c, sc2,
                           ctx->stream);
     }
-    if (nl) {
+    if (nl && nrc == SQ3_OK) {
       Prof p(ctx, ST_NL_PASS);
       if (want_next) cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
-      launch_nl_pass<T>(ctx, out, gC, want_next ? gN : nullptr, Ns, sc1, ctx->stream);
+      nrc = launch_nl_pass<T>(ctx, out, gC, want_next ? gN : nullptr, Ns, sc1, ctx->stream);
     }
   };
   if (nl) {
@@ -198,6 +200,7 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
     std::swap(cur, prev);
     s = sn;
   }
+  if (nrc) return nrc;
   if (cur != X) {
     Prof p(ctx, ST_COPY, 0);
     rc = cuda_err(cudaMemcpyAsync(X, cur, blk, cudaMemcpyDeviceToDevice,
@@ -547,9 +550,10 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
     }
     P.max_chunk_proj = maxc;
     P.max_brick_entries = maxe;
-    // shared memory of the nonlocal pass (FP64 variant, 16 vectors per CTA)
-    const size_t need = ((size_t)16 * (NL_BRICK_PTS + 1) + (size_t)36 * maxc + 2 * maxe) * 8 +
-                        (size_t)2 * maxe * 2 + 16;
+    // shared memory of the nonlocal pass (FP64 variant: two boxes of 16
+    // vectors, two coefficient buffers, both entry orders, barriers, alignment)
+    const size_t need = ((size_t)2 * 16 * NL_BRICK_PTS + (size_t)2 * 20 * maxc + 2 * maxe) * 8 +
+                        (size_t)2 * maxe * 2 + 8 + 2 * 8 + 128;
     (void)nbz;
     if (need > 227 * 1024) rc = SQ3_EINVAL;
     std::vector<float> bvalf(bval.begin(), bval.end()), evalf(eval.begin(), eval.end());

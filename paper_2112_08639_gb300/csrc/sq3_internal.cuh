@@ -1,5 +1,6 @@
 // Internal declarations shared by the translation units of libsq3.
 #pragma once
+#include <cuda.h>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -137,6 +138,12 @@ struct Prof {
 };
 int cuda_err(cudaError_t e);
 int check_device_status(sq3_ctx* ctx);
+// Tiled TMA tensor map over a dense array (FP32 or FP64 elements), no
+// swizzle, zero fill; dims and box innermost first, strides in bytes for
+// dims 1..rank-1.  Returns SQ3_OK, SQ3_EINVAL (alignment) or SQ3_ECUDA.
+int encode_tensor_map(CUtensorMap* map, bool fp64, int rank, void* base,
+                      const unsigned long long* dims, const unsigned long long* strides,
+                      const unsigned* box);
 
 // ---- stencil / Hamiltonian (stencil.cu) ----
 // out = s1 * (H y - c y) + s2 * yprev, per vector, for Ns vectors.
@@ -149,10 +156,12 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
                       double s2, cudaStream_t st);
 // In-place nonlocal pass on a local step's output (see stencil.cu):
 // out += s1 * sum_p c_p gC[p]; gC_next (zeroed, may be null) += gamma c^T out.
+// Returns an SQ3_* status (EINVAL when a brick's tables exceed shared memory
+// or out is not 16-byte aligned).
 template <typename T>
-void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
-                    double s1, cudaStream_t st);
-// gC[vec * n_proj + p] = gamma_p * sum_k c_p[k] y[k + vec*N]
+int launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
+                   double s1, cudaStream_t st);
+// gC[p * Ns + vec] = gamma_p * sum_k c_p[k] y[k + vec*N]  (projector-major)
 template <typename T>
 void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
                        cudaStream_t st);

@@ -70,7 +70,7 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
   if (nl) {
     for (int i = tid; i < n_proj * VB; i += blockDim.x) {
       const int v = i % VB, pid = i / VB;
-      gcs[i] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + pid] : T(0);
+      gcs[i] = (v < nv) ? gC[(long long)pid * Ns + v0 + v] : T(0);
     }
   }
   const T* yb[VB];
@@ -653,7 +653,7 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
 }
 
 // ---------------------------------------------------------------------------
-// Nonlocal projection gC[v * n_proj + p] = gamma_p * sum_k c_p[k] y[k + v N].
+// Nonlocal projection gC[p * Ns + v] = gamma_p * sum_k c_p[k] y[k + v N].
 // One CTA per (ball, group of VB vectors); a ball's points are read once per
 // group and its (<= 4) projectors are accumulated together.
 // ---------------------------------------------------------------------------
@@ -711,7 +711,7 @@ nl_project_kernel(long long N, int Ns, const T* __restrict__ y,
     const int v = t / 4, p = t % 4;
     if (p < np && v0 + v < Ns) {
       const int pid = ball_proj0[b] + p;
-      gC[(long long)(v0 + v) * n_proj + pid] = T(gamma[pid]) * s;
+      gC[(long long)pid * Ns + v0 + v] = T(gamma[pid]) * s;
     }
   }
 }
@@ -733,152 +733,223 @@ void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
 
 // ---------------------------------------------------------------------------
 // Nonlocal pass, in place on the output of a local stencil step:
-//   out_v[k] += s1 sum_p c_p[k] gC[v][p]                      (apply)
-//   gC_next[v][p] += gamma_p sum_k c_p[k] out_v[k]            (projection)
-// A CTA owns one 8 x 8 x 8 brick of grid points (a compact brick touches
-// few projectors) and NL_VB vectors.  It first stages, with independent
-// coalesced loads, the brick's values of its vectors, the brick's
-// projector entries and the coefficients of the projectors touching the
-// brick; phase 1 (one thread per point) applies the term from shared memory
-// and writes the point back; phase 2 (one warp per projector, one lane per
-// vector) sums the projection over the brick from the transposed entry list
-// and adds it with one global atomic.  Points outside every projector are
-// untouched.
+//   out_v[k] += s1 sum_p c_p[k] gC[p][v]                      (apply)
+//   gC_next[p][v] += gamma_p sum_k c_p[k] out_v[k]            (projection)
+// (gC is projector-major: gC[p * Ns + v].)  A CTA owns one 8 x 8 x NL_BZ
+// brick of grid points (a compact brick touches few projectors) and a run
+// of vector groups of VB vectors.  The brick's projector entries are staged
+// in shared memory once, in two orders (by point for the apply, by
+// projector for the projection).  Each group's values, a VB x NL_BZ x 8 x 8
+// box of the block, arrive by one 4-D TMA load into a ring of NBUF buffers
+// (issued NBUF groups ahead); the group's coefficients gC arrive by cp.async.
+//   phase 1: one thread per point applies the term in shared memory; the
+//            box goes back to global memory with one TMA store;
+//   phase 2: one warp per local projector, lanes over its entries, VB
+//            partial sums per lane folded across the warp by a transposed
+//            butterfly; one coalesced atomic per (projector, vector).
+// The box store writes unchanged points back unchanged; elements outside
+// the grid or beyond Ns are zero-filled on load and skipped on store.
 // ---------------------------------------------------------------------------
-template <typename T, int NL_VB>
-__global__ void __launch_bounds__(NL_BRICK_PTS, 1)
-nl_pass_kernel(int nx, int ny, int nz, int Ns, T* out, const T* __restrict__ gC,
-               T* gC_next, T s1, const int* __restrict__ bp_ptr,
-               const short* __restrict__ bp_lidx, const T* __restrict__ bp_val,
-               const int* __restrict__ bl_ptr, const int* __restrict__ bl_proj,
-               const int* __restrict__ be_ptr, const short* __restrict__ be_pt,
-               const T* __restrict__ be_val, const double* __restrict__ gamma,
-               int n_proj, int max_entries) {
-  constexpr int YS = NL_BRICK_PTS + 1;               // padded row of ybuf
-  constexpr int GS = NL_VB + 4;                      // padded row of gloc
+template <typename T, int VB>
+__device__ __forceinline__ T warp_transpose_sum(T (&a)[VB], int lane) {
+  // on return a[0] in lane L holds the sum over all lanes of a[L % VB]
+  if constexpr (VB < 32) {
+#pragma unroll
+    for (int i = 0; i < VB; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], VB);
+  }
+#pragma unroll
+  for (int s = VB / 2; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const T send = up ? a[i] : a[i + s];
+      const T keep = up ? a[i + s] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return a[0];
+}
+
+template <typename T, int VB, int NBUF, int MINB>
+__global__ void __launch_bounds__(NL_BRICK_PTS, MINB)
+nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns,
+                int groups_per_cta, const T* __restrict__ gC, T* gC_next, T s1,
+                const int* __restrict__ bp_ptr, const short* __restrict__ bp_lidx,
+                const T* __restrict__ bp_val, const int* __restrict__ bl_ptr,
+                const int* __restrict__ bl_proj, const int* __restrict__ be_ptr,
+                const short* __restrict__ be_pt, const T* __restrict__ be_val,
+                const double* __restrict__ gamma, int max_entries, int max_proj,
+                int* status) {
+  constexpr int PTS = NL_BRICK_PTS;
+  constexpr int GS = VB + 4;                         // padded row of gloc
   constexpr int VG = 8;                              // vectors per register group
+  constexpr int BOX = VB * PTS;                      // elements of one box
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
-  const int v0 = blockIdx.y * NL_VB;
-  const int nv = min(NL_VB, Ns - v0);
   const int c0 = bl_ptr[b], nloc = bl_ptr[b + 1] - c0;
-  if (nloc == 0) return;
-  const int eb = bp_ptr[b * NL_BRICK_PTS];
-  const int ne = bp_ptr[(b + 1) * NL_BRICK_PTS] - eb;
-  const int fb = be_ptr[c0];
-  T* ybuf = reinterpret_cast<T*>(smem_raw);          // NL_VB x YS
-  T* gloc = ybuf + (size_t)NL_VB * YS;               // nloc x GS
-  T* sval = gloc + (size_t)nloc * GS;                // point-ordered entry values
-  T* tval = sval + max_entries;                      // projector-ordered entry values
-  T* pacc = tval + max_entries;                      // nloc x NL_VB projection sums
-  short* slid = reinterpret_cast<short*>(pacc + (size_t)nloc * NL_VB);   // local ids
+  if (nloc == 0) return;                             // brick outside every projector
+  // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes)
+  unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int ngroups = (Ns + VB - 1) / VB;
+  const int g0 = blockIdx.y * groups_per_cta;
+  const int g1 = min(ngroups, g0 + groups_per_cta);
+  if (g0 >= g1) return;
+  T* ybuf = reinterpret_cast<T*>(sbase);             // NBUF boxes
+  T* gloc = ybuf + NBUF * BOX;                       // NBUF x max_proj x GS
+  T* sval = gloc + (size_t)NBUF * max_proj * GS;     // point-ordered values
+  T* tval = sval + max_entries;                      // projector-ordered values
+  short* slid = reinterpret_cast<short*>(tval + max_entries);   // local projector ids
   short* tpt = slid + max_entries;                              // brick point ids
-  const int tid = threadIdx.x;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(tpt + max_entries) + 7) & ~uintptr_t(7));
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
   const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-  const int ix = bx * 8 + (tid & 7), iy = by * 8 + ((tid >> 3) & 7);
-  const int iz = bz * NL_BZ + (tid >> 6);
-  const long long N = (long long)nx * ny * nz;
-  const long long k = (long long)ix + (long long)nx * (iy + (long long)ny * iz);
-  const int pe = b * NL_BRICK_PTS + tid;
-  const int e0 = bp_ptr[pe] - eb, e1 = bp_ptr[pe + 1] - eb;
-  // bulk staging with independent coalesced loads
-  T* ob = out + (long long)v0 * N + k;
-  if (e1 > e0) {
-#pragma unroll 8
-    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = (v < nv) ? ob[(long long)v * N] : T(0);
-  } else {
-#pragma unroll 8
-    for (int v = 0; v < NL_VB; ++v) ybuf[v * YS + tid] = T(0);
+  const int eb = bp_ptr[b * PTS];
+  const int ne = bp_ptr[(b + 1) * PTS] - eb;
+  const int e0 = bp_ptr[b * PTS + tid] - eb, e1 = bp_ptr[b * PTS + tid + 1] - eb;
+  const int fb = be_ptr[c0];
+  const uint32_t bar0 = smem_u32(bars);
+  if (tid == 0) {
+    abort_flag = 0;
+#pragma unroll
+    for (int i = 0; i < NBUF; ++i) mbar_init(bar0 + 8 * i, 1);
+    mbar_init_fence();
   }
-  for (int e = tid; e < ne; e += blockDim.x) {
+  __syncthreads();
+  auto issue_box = [&](int g) {                      // thread 0
+    const int bi = (g - g0) % NBUF;
+    mbar_expect_tx(bar0 + 8 * bi, BOX * (uint32_t)sizeof(T));
+    tma_load_4d(smem_u32(ybuf + bi * BOX), &omap, bar0 + 8 * bi, bx * 8, by * 8,
+                bz * NL_BZ, g * VB);
+  };
+  auto issue_gloc = [&](int g) {                     // all threads, one commit group
+    if (g < g1) {
+      T* gl = gloc + (size_t)((g - g0) % NBUF) * max_proj * GS;
+      for (int i = tid; i < nloc * VB; i += PTS) {
+        const int l = i / VB, v = i - l * VB;
+        const int vg = g * VB + v;
+        const T* src = gC + (long long)bl_proj[c0 + l] * Ns + (vg < Ns ? vg : 0);
+        cp_async_zfill<(int)sizeof(T)>(gl + l * GS + v, src, vg < Ns ? (int)sizeof(T) : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  if (tid == 0)
+    for (int g = g0; g < g1 && g < g0 + NBUF; ++g) issue_box(g);
+#pragma unroll
+  for (int i = 0; i < NBUF; ++i) issue_gloc(g0 + i);
+  for (int e = tid; e < ne; e += PTS) {
     sval[e] = bp_val[eb + e];
     slid[e] = bp_lidx[eb + e];
     tval[e] = be_val[fb + e];
     tpt[e] = be_pt[fb + e];
   }
-  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
-    const int l = i / NL_VB, v = i - l * NL_VB;
-    gloc[l * GS + v] = (v < nv) ? gC[(long long)(v0 + v) * n_proj + bl_proj[c0 + l]] : T(0);
-    pacc[i] = T(0);
-  }
-  __syncthreads();
-  // phase 1: apply, VG vectors at a time in registers
-  if (e1 > e0) {
+  int g = g0;
+  for (; g < g1; ++g) {
+    const int j = g - g0, bi = j % NBUF;
+    cp_async_wait<NBUF - 1>();                       // this thread's gloc copies of g
+    if (!mbar_wait(bar0 + 8 * bi, (uint32_t)((j / NBUF) & 1))) {
+      atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+      abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    T* yb = ybuf + bi * BOX;
+    const T* gl = gloc + (size_t)bi * max_proj * GS;
+    // phase 1: apply
+    if (e1 > e0) {
 #pragma unroll 1
-    for (int g = 0; g < NL_VB; g += VG) {
-      T acc[VG];
+      for (int gg = 0; gg < VB; gg += VG) {
+        T acc[VG];
 #pragma unroll
-      for (int i = 0; i < VG; ++i) acc[i] = T(0);
-      for (int e = e0; e < e1; ++e) {
-        const T val = sval[e];
-        const T* gl = gloc + slid[e] * GS + g;
+        for (int i = 0; i < VG; ++i) acc[i] = T(0);
+        for (int e = e0; e < e1; ++e) {
+          const T val = sval[e];
+          const T* row = gl + slid[e] * GS + gg;
 #pragma unroll
-        for (int i = 0; i < VG; ++i) acc[i] += val * gl[i];
-      }
+          for (int i = 0; i < VG; ++i) acc[i] += val * row[i];
+        }
 #pragma unroll
-      for (int i = 0; i < VG; ++i) {
-        const int v = g + i;
-        const T yv = ybuf[v * YS + tid] + s1 * acc[i];
-        ybuf[v * YS + tid] = yv;
-        if (v < nv) ob[(long long)v * N] = yv;
+        for (int i = 0; i < VG; ++i) yb[(gg + i) * PTS + tid] += s1 * acc[i];
       }
     }
-  }
-  if (gC_next == nullptr) return;
-  __syncthreads();
-  // phase 2: per local projector, each vector's sum is split over NSL
-  // slices of the projector's entry list (lanes v + NL_VB * slice), then
-  // combined with shuffles
-  constexpr int NSL = 32 * 4 / NL_VB;                // slices: 4 (FP32), 8 (FP64)
-  constexpr int WPL = NL_VB * NSL / 32;              // warps per projector (4)
-  const int warp = tid >> 5, lane = tid & 31;
-  const int nw = blockDim.x >> 5;
-  for (int task = warp; task < nloc * WPL; task += nw) {
-    const int l = task / WPL;
-    const int slot = (task - l * WPL) * 32 + lane;   // 0 .. NL_VB * NSL - 1
-    const int v = slot % NL_VB, sl = slot / NL_VB;
-    const int f0 = be_ptr[c0 + l] - fb, f1 = be_ptr[c0 + l + 1] - fb;
-    const int len = f1 - f0;
-    const int a0 = f0 + (len * sl) / NSL, a1 = f0 + (len * (sl + 1)) / NSL;
-    const T* yl = ybuf + v * YS;
-    T a = T(0);
-    for (int f = a0; f < a1; ++f) a += tval[f] * yl[tpt[f]];
-    // lanes of one vector within this warp differ by multiples of NL_VB
-#pragma unroll
-    for (int o = 16; o >= NL_VB; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    // the WPL warps of a projector meet in shared memory (at most WPL-way)
-    if (lane < NL_VB && a != T(0)) atomicAdd(pacc + l * NL_VB + v, a);
-  }
-  __syncthreads();
-  for (int i = tid; i < nloc * NL_VB; i += blockDim.x) {
-    const int l = i / NL_VB, v = i - l * NL_VB;
-    const T a = pacc[i];
-    if (v < nv && a != T(0)) {
-      const int pid = bl_proj[c0 + l];
-      atomicAdd(gC_next + (long long)(v0 + v) * n_proj + pid, T(gamma[pid]) * a);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_4d(&omap, smem_u32(yb), bx * 8, by * 8, bz * NL_BZ, g * VB);
+      bulk_commit();
     }
+    // phase 2: projection of the updated values
+    if (gC_next != nullptr) {
+      for (int l = warp; l < nloc; l += PTS / 32) {
+        const int f0 = be_ptr[c0 + l] - fb, f1 = be_ptr[c0 + l + 1] - fb;
+        T a[VB];
+#pragma unroll
+        for (int v = 0; v < VB; ++v) a[v] = T(0);
+        for (int f = f0 + lane; f < f1; f += 32) {
+          const T tv = tval[f];
+          const T* yl = yb + tpt[f];
+#pragma unroll
+          for (int v = 0; v < VB; ++v) a[v] += tv * yl[v * PTS];
+        }
+        const T sum = warp_transpose_sum<T, VB>(a, lane);
+        const int vg = g * VB + lane;
+        if (lane < VB && vg < Ns && sum != T(0)) {
+          const int pid = bl_proj[c0 + l];
+          atomicAdd(gC_next + (long long)pid * Ns + vg, T(gamma[pid]) * sum);
+        }
+      }
+    }
+    __syncthreads();                                 // box and coefficients consumed
+    if (tid == 0 && g + NBUF < g1) {
+      bulk_wait_read0();                             // the store has read the box
+      issue_box(g + NBUF);
+    }
+    issue_gloc(g + NBUF);
   }
+  // drain: loads still in flight after an abort, then every store
+  if (tid == 0) {
+    for (int h = g; h < g1 && h < g + NBUF; ++h) {
+      const int j = h - g0;
+      if (h > g || abort_flag) mbar_wait(bar0 + 8 * (j % NBUF), (uint32_t)((j / NBUF) & 1));
+    }
+    bulk_wait0();
+  }
+  cp_async_wait<0>();
 }
 
-template <typename T>
-void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
-                    double s1, cudaStream_t st) {
+template <typename T, int VB, int NBUF, int MINB>
+static int launch_brick(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
+                        double s1, cudaStream_t st) {
   const Projectors& P = ctx->proj;
-  if (P.n_proj == 0) return;
   const Grid& g = ctx->grid;
+  const size_t es = sizeof(T);
+  const size_t smem = (size_t)NBUF * VB * NL_BRICK_PTS * es +
+                      (size_t)NBUF * P.max_chunk_proj * (VB + 4) * es +
+                      (size_t)2 * P.max_brick_entries * es +
+                      (size_t)2 * P.max_brick_entries * sizeof(short) + 8 + NBUF * 8 + 128;
+  if (smem > 227 * 1024) return SQ3_EINVAL;
+  CUtensorMap map;
+  const unsigned long long dims[4] = {(unsigned long long)g.nx, (unsigned long long)g.ny,
+                                      (unsigned long long)g.nz, (unsigned long long)Ns};
+  const unsigned long long strides[3] = {(unsigned long long)g.nx * es,
+                                         (unsigned long long)g.nx * g.ny * es,
+                                         (unsigned long long)g.N * es};
+  const unsigned box[4] = {8, 8, NL_BZ, VB};
+  int rc = encode_tensor_map(&map, sizeof(T) == 8, 4, out, dims, strides, box);
+  if (rc) return rc;
   const int nb = ((g.nx + 7) / 8) * ((g.ny + 7) / 8) * ((g.nz + NL_BZ - 1) / NL_BZ);
-  // 32 vectors per CTA in FP32, 16 in FP64 (shared-memory budget)
-  constexpr int NL_VB = sizeof(T) == 4 ? 32 : 16;
-  const size_t smem = ((size_t)NL_VB * (NL_BRICK_PTS + 1) +
-                       (size_t)(2 * NL_VB + 4) * P.max_chunk_proj +
-                       (size_t)2 * P.max_brick_entries) * sizeof(T) +
-                      (size_t)2 * P.max_brick_entries * sizeof(short) + 16;
-  if (smem > 227 * 1024) return;     // reported by the caller's status check
-  auto kern = nl_pass_kernel<T, NL_VB>;
+  const int ngroups = (Ns + VB - 1) / VB;
+  // runs of groups: several CTAs per SM-slot in total, each run long enough
+  // to amortise staging the brick's tables
+  int per = (ngroups + 7) / 8;
+  if (per < 4) per = ngroups < 4 ? ngroups : 4;
+  const int nruns = (ngroups + per - 1) / per;
+  auto kern = nl_brick_kernel<T, VB, NBUF, MINB>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(nb, (Ns + NL_VB - 1) / NL_VB);
   const T* pv;
   const T* cev;
   if constexpr (sizeof(T) == 8) {
@@ -888,16 +959,35 @@ void launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
     pv = reinterpret_cast<const T*>(P.bp_valf);
     cev = reinterpret_cast<const T*>(P.be_valf);
   }
-  kern<<<grid, NL_BRICK_PTS, smem, st>>>(g.nx, g.ny, g.nz, Ns, out, gC, gC_next, T(s1),
-                                         P.bp_ptr, P.bp_lidx, pv, P.bl_ptr, P.bl_proj,
-                                         P.be_ptr, P.be_pt, cev, P.gamma, P.n_proj,
-                                         P.max_brick_entries);
+  kern<<<dim3(nb, nruns), NL_BRICK_PTS, smem, st>>>(
+      map, g.nx, g.ny, Ns, per, gC, gC_next, T(s1), P.bp_ptr, P.bp_lidx, pv, P.bl_ptr,
+      P.bl_proj, P.be_ptr, P.be_pt, cev, P.gamma, P.max_brick_entries, P.max_chunk_proj,
+      ctx->dev_status);
+  return SQ3_OK;
 }
 
-template void launch_nl_pass<double>(const sq3_ctx*, double*, const double*, double*, int,
-                                     double, cudaStream_t);
-template void launch_nl_pass<float>(const sq3_ctx*, float*, const float*, float*, int,
+template <typename T>
+int launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
+                   double s1, cudaStream_t st) {
+  if (ctx->proj.n_proj == 0) return SQ3_OK;
+  if ((uintptr_t)out & 15) return SQ3_EINVAL;        // TMA base alignment
+  if constexpr (sizeof(T) == 8) {
+    return launch_brick<T, 16, 2, 1>(ctx, out, gC, gC_next, Ns, s1, st);
+  } else {
+    static int vb = -1;
+    if (vb < 0) {
+      const char* e = getenv("SQ3_NL_VB");
+      vb = (e && atoi(e) == 32) ? 32 : 16;
+    }
+    if (vb == 32) return launch_brick<T, 32, 2, 1>(ctx, out, gC, gC_next, Ns, s1, st);
+    return launch_brick<T, 16, 3, 2>(ctx, out, gC, gC_next, Ns, s1, st);
+  }
+}
+
+template int launch_nl_pass<double>(const sq3_ctx*, double*, const double*, double*, int,
                                     double, cudaStream_t);
+template int launch_nl_pass<float>(const sq3_ctx*, float*, const float*, float*, int,
+                                   double, cudaStream_t);
 
 template void launch_cheb_step<double>(const sq3_ctx*, const double*,
                                        const double*, double*, const double*,

@@ -362,6 +362,34 @@ static int make_map(CUtensorMap* map, const Operand& o, int box_rows) {
   return r == CUDA_SUCCESS ? SQ3_OK : SQ3_ECUDA;
 }
 
+}  // namespace tc
+
+int encode_tensor_map(CUtensorMap* map, bool fp64, int rank, void* base,
+                      const unsigned long long* dims, const unsigned long long* strides,
+                      const unsigned* box) {
+  tc::EncodeTiledFn fn = tc::encode_fn();
+  if (!fn) return SQ3_ECUDA;
+  if (rank < 1 || rank > 5 || ((uintptr_t)base & 15)) return SQ3_EINVAL;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) {
+    if (strides[i] % 16) return SQ3_EINVAL;
+    st[i] = strides[i];
+  }
+  CUresult r = fn(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  (cuuint32_t)rank, base, d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SQ3_OK : SQ3_ECUDA;
+}
+
+namespace tc {
+
 template <int PA, int PB, int EPI>
 static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p,
                     dim3 grid, cudaStream_t st) {
