@@ -87,11 +87,11 @@ __global__ void to_float_kernel(const double* a, float* b, long long n) {
 }
 
 static void free_projectors(Projectors& P) {
-  void* ptrs[] = {P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
-                  P.ball_valoff, P.ball_val, P.ball_valf, P.gamma,
-                  P.pt_ptr, P.pt_proj, P.pt_val, P.pt_valf,
-                  P.bp_ptr, P.bp_lidx, P.bp_val, P.bp_valf, P.bl_ptr,
-                  P.bl_proj, P.be_ptr, P.be_pt, P.be_val, P.be_valf};
+  void* ptrs[] = {P.ball_ptr,   P.ball_idx,    P.ball_proj0, P.ball_nproj,
+                  P.ball_valoff, P.ball_val,   P.ball_valf,  P.gamma,
+                  P.nb_ball_ptr, P.nb_slot_pid, P.nb_pt_ptr, P.nb_pt_lb,
+                  P.nb_pt_val,   P.nb_pt_valf, P.nb_bl_ptr,  P.nb_bl_pt,
+                  P.nb_bl_val,   P.nb_bl_valf};
   for (void* p : ptrs) if (p) cudaFree(p);
   P = Projectors{};
 }
@@ -132,8 +132,7 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   }
   {
     Prof p(ctx, ST_STENCIL);
-    launch_cheb_step<T>(ctx, X, nullptr, Y, nullptr, nullptr, Ns, 1.0, 0.0, 0.0,
-                        ctx->stream);
+    launch_cheb_step<T>(ctx, X, nullptr, Y, Ns, 1.0, 0.0, 0.0, ctx->stream);
   }
   if (ctx->proj.n_proj) {
     Prof p(ctx, ST_NL_PASS);
@@ -178,8 +177,7 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
                   bool want_next) {
     {
       Prof p(ctx, ST_STENCIL);
-      launch_cheb_step<T>(ctx, yk, ykm1, out, nullptr, nullptr, Ns, sc1, c, sc2,
-                          ctx->stream);
+      launch_cheb_step<T>(ctx, yk, ykm1, out, Ns, sc1, c, sc2, ctx->stream);
     }
     if (nl && nrc == SQ3_OK) {
       Prof p(ctx, ST_NL_PASS);
@@ -465,20 +463,7 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
     bptr.push_back((int)bidx.size());
     p = q;
   }
-  // per-point transposed table (projector, c_p[k])
-  std::vector<int> cnt(N + 1, 0);
-  for (long long e = 0; e < nnz; ++e) cnt[idx[e] + 1]++;
-  for (long long k = 0; k < N; ++k) cnt[k + 1] += cnt[k];
-  std::vector<int> fill(cnt.begin(), cnt.end() - 1), tproj(nnz);
-  std::vector<double> tval(nnz);
-  for (int q = 0; q < n_proj; ++q)
-    for (int e = ptr[q]; e < ptr[q + 1]; ++e) {
-      const int k = idx[e];
-      tproj[fill[k]] = q;
-      tval[fill[k]] = val[e] * sq;
-      fill[k]++;
-    }
-  std::vector<float> bvalf(bval.begin(), bval.end()), tvalf(tval.begin(), tval.end());
+  std::vector<float> bvalf(bval.begin(), bval.end());
   Projectors P;
   P.n_proj = n_proj;
   P.n_ball = (int)bp0.size();
@@ -491,82 +476,102 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   rc = rc ? rc : upload(&P.ball_val, bval.data(), bval.size());
   rc = rc ? rc : upload(&P.ball_valf, bvalf.data(), bvalf.size());
   rc = rc ? rc : upload(&P.gamma, gamma, (size_t)n_proj);
-  rc = rc ? rc : upload(&P.pt_ptr, cnt.data(), cnt.size());
-  rc = rc ? rc : upload(&P.pt_proj, tproj.data(), tproj.size());
-  rc = rc ? rc : upload(&P.pt_val, tval.data(), tval.size());
-  rc = rc ? rc : upload(&P.pt_valf, tvalf.data(), tvalf.size());
-  // brick tables for the nonlocal pass (8 x 8 x NL_BZ bricks, x fastest)
+  // brick tables for the nonlocal pass (8 x 8 x NL_BZ bricks, x fastest),
+  // grouped by ball: the <= 4 projectors of one ball share its points
   {
     const int nx = c->grid.nx, ny = c->grid.ny, nz = c->grid.nz;
     const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8, nbz = (nz + NL_BZ - 1) / NL_BZ;
     const long long nb = (long long)nbx * nby * nbz;
-    std::vector<int> bptr{0}, lptr{0}, lproj, eptr{0};
-    std::vector<short> blidx, ept;
-    std::vector<double> bval, eval;
+    const int nballs = (int)bp0.size();
+    // point -> (ball, position in the ball's point list), balls ascending
+    std::vector<int> kptr(N + 1, 0);
+    for (int B = 0; B < nballs; ++B)
+      for (int e = bptr[B]; e < bptr[B + 1]; ++e) kptr[bidx[e] + 1]++;
+    for (long long k = 0; k < N; ++k) kptr[k + 1] += kptr[k];
+    std::vector<int> kfill(kptr.begin(), kptr.end() - 1), kball(bptr[nballs]), kpos(bptr[nballs]);
+    for (int B = 0; B < nballs; ++B)
+      for (int e = bptr[B]; e < bptr[B + 1]; ++e) {
+        const int k = bidx[e];
+        kball[kfill[k]] = B;
+        kpos[kfill[k]] = e - bptr[B];
+        kfill[k]++;
+      }
+    auto ball_val4 = [&](int B, int pos, double* v4) {
+      const int len = bptr[B + 1] - bptr[B];
+      for (int q = 0; q < 4; ++q)
+        v4[q] = (q < bnp[B]) ? bval[(size_t)boff[B] + (size_t)q * len + pos] : 0.0;
+    };
+    std::vector<int> qptr{0}, sptr{0}, spid, zptr{0};
+    std::vector<short> qlb, zpt;
+    std::vector<double> qval, zval;
     std::vector<int> ids;
-    std::vector<std::vector<std::pair<short, double>>> lists;
-    int maxc = 0, maxe = 0;
+    std::vector<std::vector<std::pair<short, int>>> lists;   // (t, kfill index)
+    int maxb = 0, maxe = 0;
     for (long long b = 0; b < nb; ++b) {
-      const int ebeg = (int)blidx.size();
-      const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+      const int ebeg = (int)qlb.size();
+      const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby),
+                bz = (int)(b / ((long long)nbx * nby));
       auto gidx = [&](int t) -> long long {
-        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7), iz = bz * NL_BZ + (t >> 6);
+        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7),
+                  iz = bz * NL_BZ + (t >> 6);
         if (ix >= nx || iy >= ny || iz >= nz) return -1;
         return (long long)ix + (long long)nx * (iy + (long long)ny * iz);
       };
       ids.clear();
       for (int t = 0; t < NL_BRICK_PTS; ++t) {
-        const long long kk = gidx(t);
-        if (kk < 0) continue;
-        for (int e = cnt[kk]; e < cnt[kk + 1]; ++e) ids.push_back(tproj[e]);
+        const long long k = gidx(t);
+        if (k < 0) continue;
+        for (int j = kptr[k]; j < kptr[k + 1]; ++j) ids.push_back(kball[j]);
       }
       std::sort(ids.begin(), ids.end());
       ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
       lists.assign(ids.size(), {});
+      double v4[4];
       for (int t = 0; t < NL_BRICK_PTS; ++t) {
-        const long long kk = gidx(t);
-        if (kk >= 0) {
-          for (int e = cnt[kk]; e < cnt[kk + 1]; ++e) {
-            const int l =
-                (int)(std::lower_bound(ids.begin(), ids.end(), tproj[e]) - ids.begin());
-            blidx.push_back((short)l);
-            bval.push_back(tval[e]);
-            lists[l].push_back({(short)t, tval[e]});
+        const long long k = gidx(t);
+        if (k >= 0) {
+          for (int j = kptr[k]; j < kptr[k + 1]; ++j) {
+            const int lb = (int)(std::lower_bound(ids.begin(), ids.end(), kball[j]) - ids.begin());
+            qlb.push_back((short)lb);
+            ball_val4(kball[j], kpos[j], v4);
+            qval.insert(qval.end(), v4, v4 + 4);
+            lists[lb].push_back({(short)t, j});
           }
         }
-        bptr.push_back((int)blidx.size());
+        qptr.push_back((int)qlb.size());
       }
-      for (auto& lst : lists) {
-        for (auto& pr : lst) {
-          ept.push_back(pr.first);
-          eval.push_back(pr.second);
+      for (size_t lb = 0; lb < ids.size(); ++lb) {
+        const int B = ids[lb];
+        for (int q = 0; q < 4; ++q) spid.push_back(q < bnp[B] ? bp0[B] + q : -1);
+        for (auto& pr : lists[lb]) {
+          zpt.push_back(pr.first);
+          ball_val4(B, kpos[pr.second], v4);
+          zval.insert(zval.end(), v4, v4 + 4);
         }
-        eptr.push_back((int)ept.size());
+        zptr.push_back((int)zpt.size());
       }
-      lproj.insert(lproj.end(), ids.begin(), ids.end());
-      lptr.push_back((int)lproj.size());
-      maxc = std::max(maxc, (int)ids.size());
-      maxe = std::max(maxe, (int)blidx.size() - ebeg);
+      sptr.push_back((int)(spid.size() / 4));
+      maxb = std::max(maxb, (int)ids.size());
+      maxe = std::max(maxe, (int)qlb.size() - ebeg);
     }
-    P.max_chunk_proj = maxc;
+    P.max_brick_balls = maxb;
     P.max_brick_entries = maxe;
-    // shared memory of the nonlocal pass (FP64 variant: two boxes of 16
+    // shared memory of the nonlocal pass, FP64 variant (two boxes of 8
     // vectors, two coefficient buffers, both entry orders, barriers, alignment)
-    const size_t need = ((size_t)2 * 16 * NL_BRICK_PTS + (size_t)2 * 20 * maxc + 2 * maxe) * 8 +
-                        (size_t)2 * maxe * 2 + 8 + 2 * 8 + 128;
+    const size_t need = nl_pass_smem_bytes(8, 8, 2, maxb, maxe);
     (void)nbz;
     if (need > 227 * 1024) rc = SQ3_EINVAL;
-    std::vector<float> bvalf(bval.begin(), bval.end()), evalf(eval.begin(), eval.end());
-    rc = rc ? rc : upload(&P.bp_ptr, bptr.data(), bptr.size());
-    rc = rc ? rc : upload(&P.bp_lidx, blidx.data(), blidx.size());
-    rc = rc ? rc : upload(&P.bp_val, bval.data(), bval.size());
-    rc = rc ? rc : upload(&P.bp_valf, bvalf.data(), bvalf.size());
-    rc = rc ? rc : upload(&P.bl_ptr, lptr.data(), lptr.size());
-    rc = rc ? rc : upload(&P.bl_proj, lproj.data(), lproj.size());
-    rc = rc ? rc : upload(&P.be_ptr, eptr.data(), eptr.size());
-    rc = rc ? rc : upload(&P.be_pt, ept.data(), ept.size());
-    rc = rc ? rc : upload(&P.be_val, eval.data(), eval.size());
-    rc = rc ? rc : upload(&P.be_valf, evalf.data(), evalf.size());
+    std::vector<float> qvalf(qval.begin(), qval.end()), zvalf(zval.begin(), zval.end());
+    rc = rc ? rc : upload(&P.nb_ball_ptr, sptr.data(), sptr.size());
+    rc = rc ? rc : upload(&P.nb_slot_pid, spid.data(), spid.size());
+    rc = rc ? rc : upload(&P.nb_pt_ptr, qptr.data(), qptr.size());
+    rc = rc ? rc : upload(&P.nb_pt_lb, qlb.data(), qlb.size());
+    rc = rc ? rc : upload(&P.nb_pt_val, qval.data(), qval.size());
+    rc = rc ? rc : upload(&P.nb_pt_valf, qvalf.data(), qvalf.size());
+    rc = rc ? rc : upload(&P.nb_bl_ptr, zptr.data(), zptr.size());
+    rc = rc ? rc : upload(&P.nb_bl_pt, zpt.data(), zpt.size());
+    rc = rc ? rc : upload(&P.nb_bl_val, zval.data(), zval.size());
+    rc = rc ? rc : upload(&P.nb_bl_valf, zvalf.data(), zvalf.size());
   }
   c->proj = P;
   if (rc) { free_projectors(c->proj); return rc; }

@@ -59,30 +59,28 @@ struct Projectors {
   double* ball_val = nullptr;   // c = chi sqrt(dV), FP64
   float* ball_valf = nullptr;   // same, FP32
   double* gamma = nullptr;      // n_proj
-  // per point: pt_ptr[k]..pt_ptr[k+1]-1 entries (projector id, value c)
-  int* pt_ptr = nullptr;
-  int* pt_proj = nullptr;
-  double* pt_val = nullptr;
-  float* pt_valf = nullptr;
-  // per 8 x 8 x NL_BZ brick b of the grid (bricks x-fastest), local point
-  // t = tx + 8 ty + 64 tz: entries bp_ptr[NL_BRICK_PTS b + t] ..
-  // bp_ptr[NL_BRICK_PTS b + t + 1] - 1
-  // hold the projector as an index into the brick's list
-  // bl_proj[bl_ptr[b] .. bl_ptr[b+1]-1] (bp_lidx) and c_p at the point
-  // (bp_val); the transposed lists per (brick, local projector) slot give
-  // the point (be_pt) and c_p (be_val).  max_chunk_proj = longest list.
-  int* bp_ptr = nullptr;
-  short* bp_lidx = nullptr;
-  double* bp_val = nullptr;
-  float* bp_valf = nullptr;
-  int* bl_ptr = nullptr;
-  int* bl_proj = nullptr;
-  int* be_ptr = nullptr;
-  short* be_pt = nullptr;
-  double* be_val = nullptr;
-  float* be_valf = nullptr;
-  int max_chunk_proj = 0;
-  int max_brick_entries = 0;   // largest number of entries in one brick
+  // Nonlocal-pass tables per 8 x 8 x NL_BZ brick b of the grid (bricks x
+  // fastest; local point t = tx + 8 ty + 64 tz), grouped by ball:
+  //   local balls of brick b: slots nb_ball_ptr[b] .. nb_ball_ptr[b+1]-1;
+  //     slot s carries projector ids nb_slot_pid[4s .. 4s+3] (-1 = none)
+  //   point-major entries of point t: nb_pt_ptr[NL_BRICK_PTS b + t] ..
+  //     nb_pt_ptr[NL_BRICK_PTS b + t + 1] - 1, each the local ball
+  //     (nb_pt_lb, relative to the brick's first slot) and the ball's four
+  //     c_p values at the point (nb_pt_val, zero padded)
+  //   ball-major entries of slot s: nb_bl_ptr[s] .. nb_bl_ptr[s+1]-1, each
+  //     the point (nb_bl_pt) and the four values (nb_bl_val)
+  int* nb_ball_ptr = nullptr;
+  int* nb_slot_pid = nullptr;
+  int* nb_pt_ptr = nullptr;
+  short* nb_pt_lb = nullptr;
+  double* nb_pt_val = nullptr;
+  float* nb_pt_valf = nullptr;
+  int* nb_bl_ptr = nullptr;
+  short* nb_bl_pt = nullptr;
+  double* nb_bl_val = nullptr;
+  float* nb_bl_valf = nullptr;
+  int max_brick_balls = 0;     // most balls touching one brick
+  int max_brick_entries = 0;   // most (point, ball) entries in one brick
 };
 
 }  // namespace sq3
@@ -146,16 +144,19 @@ int encode_tensor_map(CUtensorMap* map, bool fp64, int rank, void* base,
                       const unsigned* box);
 
 // ---- stencil / Hamiltonian (stencil.cu) ----
-// out = s1 * (H y - c y) + s2 * yprev, per vector, for Ns vectors.
-// gC: projection coefficients gC[v * n_proj + p] = gamma_p c_p^T y_v (null
-// when there are no projectors).  gC_next (may be null): zero-initialised
-// array that receives the same coefficients of `out`.  yprev may alias out.
+// out = s1 * (H_loc y - c y) + s2 * yprev, per vector, for Ns vectors, with
+// H_loc = -1/2 Lap + V.
+// The nonlocal term is added by
+// launch_nl_pass.  yprev may alias out (each element reads only its own
+// yprev before writing it); y must not alias out.
 template <typename T>
-void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                      const T* gC, T* gC_next, int Ns, double s1, double c,
-                      double s2, cudaStream_t st);
+void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out, int Ns,
+                      double s1, double c, double s2, cudaStream_t st);
 // In-place nonlocal pass on a local step's output (see stencil.cu):
 // out += s1 * sum_p c_p gC[p]; gC_next (zeroed, may be null) += gamma c^T out.
+// Dynamic shared memory of the nonlocal pass for element size es, VB vectors
+// per box, NBUF boxes, and the largest brick (balls, entries).
+size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries);
 // Returns an SQ3_* status (EINVAL when a brick's tables exceed shared memory
 // or out is not 16-byte aligned).
 template <typename T>

@@ -20,6 +20,7 @@
 // from a per-point table of (projector, c_p[k]) and the precomputed
 // coefficients gC = gamma (c^T y) of the same vector.
 #include <stdint.h>
+#include <type_traits>
 #include <stdlib.h>
 
 #include "async_copy.cuh"
@@ -37,24 +38,21 @@ struct StepCoef {
   T az[SQ3_MAX_FD_RADIUS + 1];
 };
 
-// VB vectors per CTA share the (x, y) tile: the potential, the per-point
-// projector entries and the index arithmetic are loaded once for all VB.
-// Shared-memory rows carry R wrapped columns on each side, so the x-taps
-// need no index wrap.  The next plane's register-queue entry and yprev are
-// loaded one iteration ahead.  The projector coefficients gC of the input
-// block are staged in shared memory.
+// VB vectors per CTA share the (x, y) tile: the potential and the index
+// arithmetic are loaded once for all VB.  Shared-memory rows carry R wrapped
+// columns on each side, so the x-taps need no index wrap.  The next plane's
+// register-queue entry and yprev are loaded one iteration ahead.  This is
+// the general form (any row length); the vectorised forms below take rows
+// whose length is a multiple of the 16-byte vector width.
 template <typename T, int R, int VB>
 __global__ void __launch_bounds__(512, 1)
 cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
                  const T* __restrict__ y, const T* yprev, T* out,
-                 const T* __restrict__ V, const T* __restrict__ gC,
-                 const int* __restrict__ pt_ptr, const int* __restrict__ pt_proj,
-                 const T* __restrict__ pt_val, int n_proj, T s1, T c, T s2) {
+                 const T* __restrict__ V, T s1, T c, T s2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rows = TY + 2 * R;
   const int W = nx + 2 * R;                          // padded row width
   T* sm = reinterpret_cast<T*>(smem_raw);           // VB planes, rows x W each
-  T* gcs = sm + (size_t)VB * rows * W;               // n_proj x VB staged gC
   const int tid = threadIdx.x;
   const int x = tid % nx;
   const int ty = tid / nx;
@@ -66,13 +64,6 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
   const int v0 = blockIdx.y * VB;
   const int nv = min(VB, Ns - v0);
   const int col = yy * nx + x;
-  const bool nl = gC != nullptr;
-  if (nl) {
-    for (int i = tid; i < n_proj * VB; i += blockDim.x) {
-      const int v = i % VB, pid = i / VB;
-      gcs[i] = (v < nv) ? gC[(long long)pid * Ns + v0 + v] : T(0);
-    }
-  }
   const T* yb[VB];
   T* ob[VB];
   const T* pb[VB];
@@ -121,7 +112,6 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
       yp[v] = ypn[v];
     }
     T vz = T(0);
-    int e0 = 0, e1 = 0;
     if (active) {
       // look-ahead loads for the next iteration
       if (z + 1 < nz) {
@@ -135,10 +125,6 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
         }
       }
       vz = __ldg(V + gidx);
-      if (nl) {
-        e0 = __ldg(pt_ptr + gidx);
-        e1 = __ldg(pt_ptr + gidx + 1);
-      }
     }
 
     __syncthreads();  // previous plane fully consumed
@@ -192,15 +178,6 @@ cheb_step_kernel(int nx, int ny, int nz, int Ns, int TY, StepCoef<T> k,
           a += k.az[p] * (q[v][R + p] + q[v][R - p]);
         }
         acc[v] = a;
-      }
-      if (nl) {
-#pragma unroll 2
-        for (int e = e0; e < e1; ++e) {
-          const T val = __ldg(pt_val + e);
-          const T* gp = gcs + __ldg(pt_proj + e) * VB;
-#pragma unroll
-          for (int v = 0; v < VB; ++v) acc[v] += val * gp[v];
-        }
       }
 #pragma unroll
       for (int v = 0; v < VB; ++v)
@@ -527,8 +504,7 @@ static int stencil_vb(int esize) {
 
 template <typename T, int R, int VB>
 static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                      const T* gC, T* gC_next, int Ns, double s1, double c,
-                      double s2, cudaStream_t st) {
+                      int Ns, double s1, double c, double s2, cudaStream_t st) {
   const Grid& g = ctx->grid;
   StepCoef<T> k{};
   double ix = 1.0 / (g.hx * g.hx), iy = 1.0 / (g.hy * g.hy),
@@ -544,28 +520,19 @@ static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   dim3 block(g.nx * TY);
   size_t smem = (size_t)VB * (TY + 2 * R) * (g.nx + 2 * R) * sizeof(T);
   const T* V;
-  const T* pv;
-  if constexpr (sizeof(T) == 8) {
-    V = reinterpret_cast<const T*>(ctx->V);
-    pv = reinterpret_cast<const T*>(ctx->proj.pt_val);
-  } else {
-    V = reinterpret_cast<const T*>(ctx->Vf);
-    pv = reinterpret_cast<const T*>(ctx->proj.pt_valf);
-  }
+  if constexpr (sizeof(T) == 8) V = reinterpret_cast<const T*>(ctx->V);
+  else V = reinterpret_cast<const T*>(ctx->Vf);
   auto kern = cheb_step_kernel<T, R, VB>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<grid, block, smem, st>>>(g.nx, g.ny, g.nz, Ns, TY, k, y, yprev, out, V,
-                                  nullptr, ctx->proj.pt_ptr, ctx->proj.pt_proj,
-                                  pv, ctx->proj.n_proj, T(s1), T(c), T(s2));
-  (void)gC_next;
+  kern<<<grid, block, smem, st>>>(g.nx, g.ny, g.nz, Ns, TY, k, y, yprev, out, V, T(s1),
+                                  T(c), T(s2));
 }
 
 // Vectorised launch when the grid allows it; returns false otherwise.
 template <typename T, int R>
 static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                       const T* gC, int Ns, double s1, double c, double s2,
-                       cudaStream_t st) {
+                       int Ns, double s1, double c, double s2, cudaStream_t st) {
   constexpr int VW = Vec16<T>::W;
   constexpr int PAD = ((R + VW - 1) / VW) * VW;
   const Grid& g = ctx->grid;
@@ -628,27 +595,25 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
 
 template <typename T, int R>
 static void launch_r(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                     const T* gC, T* gC_next, int Ns, double s1, double c,
-                     double s2, cudaStream_t st) {
-  if (launch_vec<T, R>(ctx, y, yprev, out, gC, Ns, s1, c, s2, st)) return;
+                     int Ns, double s1, double c, double s2, cudaStream_t st) {
+  if (launch_vec<T, R>(ctx, y, yprev, out, Ns, s1, c, s2, st)) return;
   switch (stencil_vb(sizeof(T))) {
-    case 1: launch_rv<T, R, 1>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    case 2: launch_rv<T, R, 2>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    default: launch_rv<T, R, 4>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 1: launch_rv<T, R, 1>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    case 2: launch_rv<T, R, 2>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    default: launch_rv<T, R, 4>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
   }
 }
 
 template <typename T>
 void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
-                      const T* gC, T* gC_next, int Ns, double s1, double c,
-                      double s2, cudaStream_t st) {
+                      int Ns, double s1, double c, double s2, cudaStream_t st) {
   switch (ctx->grid.radius) {
-    case 1: launch_r<T, 1>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    case 2: launch_r<T, 2>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    case 3: launch_r<T, 3>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    case 4: launch_r<T, 4>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    case 5: launch_r<T, 5>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
-    default: launch_r<T, 6>(ctx, y, yprev, out, gC, gC_next, Ns, s1, c, s2, st); break;
+    case 1: launch_r<T, 1>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    case 2: launch_r<T, 2>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    case 3: launch_r<T, 3>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    case 4: launch_r<T, 4>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    case 5: launch_r<T, 5>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
+    default: launch_r<T, 6>(ctx, y, yprev, out, Ns, s1, c, s2, st); break;
   }
 }
 
@@ -736,80 +701,94 @@ void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
 //   out_v[k] += s1 sum_p c_p[k] gC[p][v]                      (apply)
 //   gC_next[p][v] += gamma_p sum_k c_p[k] out_v[k]            (projection)
 // (gC is projector-major: gC[p * Ns + v].)  A CTA owns one 8 x 8 x NL_BZ
-// brick of grid points (a compact brick touches few projectors) and a run
-// of vector groups of VB vectors.  The brick's projector entries are staged
-// in shared memory once, in two orders (by point for the apply, by
-// projector for the projection).  Each group's values, a VB x NL_BZ x 8 x 8
-// box of the block, arrive by one 4-D TMA load into a ring of NBUF buffers
-// (issued NBUF groups ahead); the group's coefficients gC arrive by cp.async.
+// brick of grid points and a run of vector groups of VB vectors.  The
+// projectors are handled per ball: the <= 4 projectors of an atom share its
+// points, so one (point, ball) entry carries four values and one load of a
+// point's value feeds four projectors.  The brick's entries are staged in
+// shared memory once, in two orders (by point for the apply, by ball for
+// the projection).  Each group's values, a VB x NL_BZ x 8 x 8 box of the
+// block, arrive by one 4-D TMA load into a ring of NBUF buffers (issued
+// NBUF groups ahead); the group's coefficients gC arrive by cp.async.
 //   phase 1: one thread per point applies the term in shared memory; the
 //            box goes back to global memory with one TMA store;
-//   phase 2: one warp per local projector, lanes over its entries, VB
-//            partial sums per lane folded across the warp by a transposed
-//            butterfly; one coalesced atomic per (projector, vector).
+//   phase 2: warps take (ball, half of its points) tasks, lanes over points,
+//            4 VB partial sums per lane folded across the warp by a halving
+//            butterfly; one atomic per (projector, vector) and task.
 // The box store writes unchanged points back unchanged; elements outside
 // the grid or beyond Ns are zero-filled on load and skipped on store.
 // ---------------------------------------------------------------------------
-template <typename T, int VB>
-__device__ __forceinline__ T warp_transpose_sum(T (&a)[VB], int lane) {
-  // on return a[0] in lane L holds the sum over all lanes of a[L % VB]
-  if constexpr (VB < 32) {
+struct alignas(16) Dbl4 { double x, y, z, w; };
+
+template <typename T, int NV>
+__device__ __forceinline__ void warp_fold(T (&a)[NV], int lane) {
+  // on return lane L holds in a[0 .. NV/32) the sums over all lanes of
+  // a[(NV/32) L + i]
+  static_assert(NV % 32 == 0, "fold of a multiple of 32 values");
 #pragma unroll
-    for (int i = 0; i < VB; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], VB);
-  }
-#pragma unroll
-  for (int s = VB / 2; s >= 1; s >>= 1) {
+  for (int k = 0; k < 5; ++k) {
+    const int s = 16 >> k;
+    constexpr int n0 = NV;
+    const int half = n0 >> (k + 1);
     const bool up = (lane & s) != 0;
 #pragma unroll
-    for (int i = 0; i < s; ++i) {
-      const T send = up ? a[i] : a[i + s];
-      const T keep = up ? a[i + s] : a[i];
-      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    for (int i = 0; i < NV / 2; ++i) {
+      if (i < half) {
+        const T send = up ? a[i] : a[i + half];
+        const T keep = up ? a[i + half] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+      }
     }
   }
-  return a[0];
+}
+
+size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries) {
+  return 128 + (size_t)NBUF * VB * NL_BRICK_PTS * es +
+         (size_t)NBUF * 4 * max_balls * (VB + 4) * es + (size_t)2 * max_entries * 4 * es +
+         (size_t)2 * max_entries * sizeof(short) + 8 + (size_t)NBUF * 8;
 }
 
 template <typename T, int VB, int NBUF, int MINB>
 __global__ void __launch_bounds__(NL_BRICK_PTS, MINB)
 nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns,
                 int groups_per_cta, const T* __restrict__ gC, T* gC_next, T s1,
-                const int* __restrict__ bp_ptr, const short* __restrict__ bp_lidx,
-                const T* __restrict__ bp_val, const int* __restrict__ bl_ptr,
-                const int* __restrict__ bl_proj, const int* __restrict__ be_ptr,
-                const short* __restrict__ be_pt, const T* __restrict__ be_val,
-                const double* __restrict__ gamma, int max_entries, int max_proj,
+                const int* __restrict__ ball_ptr, const int* __restrict__ slot_pid,
+                const int* __restrict__ pt_ptr, const short* __restrict__ pt_lb,
+                const T* __restrict__ pt_val, const int* __restrict__ bl_ptr,
+                const short* __restrict__ bl_pt, const T* __restrict__ bl_val,
+                const double* __restrict__ gamma, int max_entries, int max_balls,
                 int* status) {
+  using T4 = typename std::conditional<sizeof(T) == 4, float4, Dbl4>::type;
   constexpr int PTS = NL_BRICK_PTS;
   constexpr int GS = VB + 4;                         // padded row of gloc
-  constexpr int VG = 8;                              // vectors per register group
   constexpr int BOX = VB * PTS;                      // elements of one box
+  constexpr int NV = 4 * VB;                         // phase-2 sums per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
-  const int c0 = bl_ptr[b], nloc = bl_ptr[b + 1] - c0;
-  if (nloc == 0) return;                             // brick outside every projector
-  // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes)
-  unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int s0 = ball_ptr[b], nlb = ball_ptr[b + 1] - s0;
+  if (nlb == 0) return;                              // brick outside every ball
   const int ngroups = (Ns + VB - 1) / VB;
   const int g0 = blockIdx.y * groups_per_cta;
   const int g1 = min(ngroups, g0 + groups_per_cta);
   if (g0 >= g1) return;
+  // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes)
+  unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   T* ybuf = reinterpret_cast<T*>(sbase);             // NBUF boxes
-  T* gloc = ybuf + NBUF * BOX;                       // NBUF x max_proj x GS
-  T* sval = gloc + (size_t)NBUF * max_proj * GS;     // point-ordered values
-  T* tval = sval + max_entries;                      // projector-ordered values
-  short* slid = reinterpret_cast<short*>(tval + max_entries);   // local projector ids
-  short* tpt = slid + max_entries;                              // brick point ids
+  T* gloc = ybuf + NBUF * BOX;                       // NBUF x (4 max_balls) x GS
+  T* qval = gloc + (size_t)NBUF * 4 * max_balls * GS;   // point-major values (x4)
+  T* zval = qval + (size_t)4 * max_entries;             // ball-major values (x4)
+  short* qlb = reinterpret_cast<short*>(zval + (size_t)4 * max_entries);
+  short* zpt = qlb + max_entries;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(tpt + max_entries) + 7) & ~uintptr_t(7));
+      (reinterpret_cast<uintptr_t>(zpt + max_entries) + 7) & ~uintptr_t(7));
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
   const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-  const int eb = bp_ptr[b * PTS];
-  const int ne = bp_ptr[(b + 1) * PTS] - eb;
-  const int e0 = bp_ptr[b * PTS + tid] - eb, e1 = bp_ptr[b * PTS + tid + 1] - eb;
-  const int fb = be_ptr[c0];
+  const int eb = pt_ptr[b * PTS];
+  const int ne = pt_ptr[(b + 1) * PTS] - eb;
+  const int e0 = pt_ptr[b * PTS + tid] - eb, e1 = pt_ptr[b * PTS + tid + 1] - eb;
+  const int fb = bl_ptr[s0];
+  const int nrows = 4 * nlb;
   const uint32_t bar0 = smem_u32(bars);
   if (tid == 0) {
     abort_flag = 0;
@@ -826,12 +805,14 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   };
   auto issue_gloc = [&](int g) {                     // all threads, one commit group
     if (g < g1) {
-      T* gl = gloc + (size_t)((g - g0) % NBUF) * max_proj * GS;
-      for (int i = tid; i < nloc * VB; i += PTS) {
-        const int l = i / VB, v = i - l * VB;
+      T* gl = gloc + (size_t)((g - g0) % NBUF) * 4 * max_balls * GS;
+      for (int i = tid; i < nrows * VB; i += PTS) {
+        const int r = i / VB, v = i - r * VB;
         const int vg = g * VB + v;
-        const T* src = gC + (long long)bl_proj[c0 + l] * Ns + (vg < Ns ? vg : 0);
-        cp_async_zfill<(int)sizeof(T)>(gl + l * GS + v, src, vg < Ns ? (int)sizeof(T) : 0);
+        const int pid = slot_pid[4 * s0 + r];
+        const bool ok = pid >= 0 && vg < Ns;
+        const T* src = gC + (ok ? (long long)pid * Ns + vg : 0);
+        cp_async_zfill<(int)sizeof(T)>(gl + r * GS + v, src, ok ? (int)sizeof(T) : 0);
       }
     }
     cp_async_commit();
@@ -840,11 +821,15 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     for (int g = g0; g < g1 && g < g0 + NBUF; ++g) issue_box(g);
 #pragma unroll
   for (int i = 0; i < NBUF; ++i) issue_gloc(g0 + i);
-  for (int e = tid; e < ne; e += PTS) {
-    sval[e] = bp_val[eb + e];
-    slid[e] = bp_lidx[eb + e];
-    tval[e] = be_val[fb + e];
-    tpt[e] = be_pt[fb + e];
+  {
+    const T4* qv = reinterpret_cast<const T4*>(pt_val) + eb;
+    const T4* zv = reinterpret_cast<const T4*>(bl_val) + fb;
+    for (int e = tid; e < ne; e += PTS) {
+      reinterpret_cast<T4*>(qval)[e] = qv[e];
+      reinterpret_cast<T4*>(zval)[e] = zv[e];
+      qlb[e] = pt_lb[eb + e];
+      zpt[e] = bl_pt[fb + e];
+    }
   }
   int g = g0;
   for (; g < g1; ++g) {
@@ -857,23 +842,23 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     __syncthreads();
     if (abort_flag) break;
     T* yb = ybuf + bi * BOX;
-    const T* gl = gloc + (size_t)bi * max_proj * GS;
-    // phase 1: apply
+    const T* gl = gloc + (size_t)bi * 4 * max_balls * GS;
+    // phase 1: apply, one thread per point, four projectors per entry
     if (e1 > e0) {
-#pragma unroll 1
-      for (int gg = 0; gg < VB; gg += VG) {
-        T acc[VG];
+      T acc[VB];
 #pragma unroll
-        for (int i = 0; i < VG; ++i) acc[i] = T(0);
-        for (int e = e0; e < e1; ++e) {
-          const T val = sval[e];
-          const T* row = gl + slid[e] * GS + gg;
+      for (int v = 0; v < VB; ++v) acc[v] = T(0);
+      for (int e = e0; e < e1; ++e) {
+        const T4 c = reinterpret_cast<const T4*>(qval)[e];
+        const T* row = gl + 4 * qlb[e] * GS;
+        const T cq[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-          for (int i = 0; i < VG; ++i) acc[i] += val * row[i];
-        }
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int i = 0; i < VG; ++i) yb[(gg + i) * PTS + tid] += s1 * acc[i];
+          for (int v = 0; v < VB; ++v) acc[v] += cq[q] * row[q * GS + v];
       }
+#pragma unroll
+      for (int v = 0; v < VB; ++v) yb[v * PTS + tid] += s1 * acc[v];
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -881,24 +866,37 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       tma_store_4d(&omap, smem_u32(yb), bx * 8, by * 8, bz * NL_BZ, g * VB);
       bulk_commit();
     }
-    // phase 2: projection of the updated values
+    // phase 2: projection of the updated values, per (ball, half)
     if (gC_next != nullptr) {
-      for (int l = warp; l < nloc; l += PTS / 32) {
-        const int f0 = be_ptr[c0 + l] - fb, f1 = be_ptr[c0 + l + 1] - fb;
-        T a[VB];
+      for (int task = warp; task < 2 * nlb; task += PTS / 32) {
+        const int lb = task >> 1;
+        const int fa = bl_ptr[s0 + lb] - fb, fe = bl_ptr[s0 + lb + 1] - fb;
+        const int fm = fa + (fe - fa + 1) / 2;
+        const int f0 = (task & 1) ? fm : fa, f1 = (task & 1) ? fe : fm;
+        T a[NV];
 #pragma unroll
-        for (int v = 0; v < VB; ++v) a[v] = T(0);
+        for (int i = 0; i < NV; ++i) a[i] = T(0);
         for (int f = f0 + lane; f < f1; f += 32) {
-          const T tv = tval[f];
-          const T* yl = yb + tpt[f];
+          const T4 c = reinterpret_cast<const T4*>(zval)[f];
+          const T* yl = yb + zpt[f];
 #pragma unroll
-          for (int v = 0; v < VB; ++v) a[v] += tv * yl[v * PTS];
+          for (int v = 0; v < VB; ++v) {
+            const T y = yl[v * PTS];
+            a[v] += c.x * y;
+            a[VB + v] += c.y * y;
+            a[2 * VB + v] += c.z * y;
+            a[3 * VB + v] += c.w * y;
+          }
         }
-        const T sum = warp_transpose_sum<T, VB>(a, lane);
-        const int vg = g * VB + lane;
-        if (lane < VB && vg < Ns && sum != T(0)) {
-          const int pid = bl_proj[c0 + l];
-          atomicAdd(gC_next + (long long)pid * Ns + vg, T(gamma[pid]) * sum);
+        warp_fold<T, NV>(a, lane);
+#pragma unroll
+        for (int i = 0; i < NV / 32; ++i) {
+          const int idx = (NV / 32) * lane + i;
+          const int q = idx / VB, v = idx - q * VB;
+          const int pid = slot_pid[4 * (s0 + lb) + q];
+          const int vg = g * VB + v;
+          if (pid >= 0 && vg < Ns && a[i] != T(0))
+            atomicAdd(gC_next + (long long)pid * Ns + vg, T(gamma[pid]) * a[i]);
         }
       }
     }
@@ -926,10 +924,8 @@ static int launch_brick(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int
   const Projectors& P = ctx->proj;
   const Grid& g = ctx->grid;
   const size_t es = sizeof(T);
-  const size_t smem = (size_t)NBUF * VB * NL_BRICK_PTS * es +
-                      (size_t)NBUF * P.max_chunk_proj * (VB + 4) * es +
-                      (size_t)2 * P.max_brick_entries * es +
-                      (size_t)2 * P.max_brick_entries * sizeof(short) + 8 + NBUF * 8 + 128;
+  const size_t smem =
+      nl_pass_smem_bytes((int)es, VB, NBUF, P.max_brick_balls, P.max_brick_entries);
   if (smem > 227 * 1024) return SQ3_EINVAL;
   CUtensorMap map;
   const unsigned long long dims[4] = {(unsigned long long)g.nx, (unsigned long long)g.ny,
@@ -950,19 +946,19 @@ static int launch_brick(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int
   auto kern = nl_brick_kernel<T, VB, NBUF, MINB>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const T* pv;
-  const T* cev;
+  const T* qv;
+  const T* zv;
   if constexpr (sizeof(T) == 8) {
-    pv = reinterpret_cast<const T*>(P.bp_val);
-    cev = reinterpret_cast<const T*>(P.be_val);
+    qv = reinterpret_cast<const T*>(P.nb_pt_val);
+    zv = reinterpret_cast<const T*>(P.nb_bl_val);
   } else {
-    pv = reinterpret_cast<const T*>(P.bp_valf);
-    cev = reinterpret_cast<const T*>(P.be_valf);
+    qv = reinterpret_cast<const T*>(P.nb_pt_valf);
+    zv = reinterpret_cast<const T*>(P.nb_bl_valf);
   }
   kern<<<dim3(nb, nruns), NL_BRICK_PTS, smem, st>>>(
-      map, g.nx, g.ny, Ns, per, gC, gC_next, T(s1), P.bp_ptr, P.bp_lidx, pv, P.bl_ptr,
-      P.bl_proj, P.be_ptr, P.be_pt, cev, P.gamma, P.max_brick_entries, P.max_chunk_proj,
-      ctx->dev_status);
+      map, g.nx, g.ny, Ns, per, gC, gC_next, T(s1), P.nb_ball_ptr, P.nb_slot_pid,
+      P.nb_pt_ptr, P.nb_pt_lb, qv, P.nb_bl_ptr, P.nb_bl_pt, zv, P.gamma,
+      P.max_brick_entries, P.max_brick_balls, ctx->dev_status);
   return SQ3_OK;
 }
 
@@ -971,17 +967,8 @@ int launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
                    double s1, cudaStream_t st) {
   if (ctx->proj.n_proj == 0) return SQ3_OK;
   if ((uintptr_t)out & 15) return SQ3_EINVAL;        // TMA base alignment
-  if constexpr (sizeof(T) == 8) {
-    return launch_brick<T, 16, 2, 1>(ctx, out, gC, gC_next, Ns, s1, st);
-  } else {
-    static int vb = -1;
-    if (vb < 0) {
-      const char* e = getenv("SQ3_NL_VB");
-      vb = (e && atoi(e) == 32) ? 32 : 16;
-    }
-    if (vb == 32) return launch_brick<T, 32, 2, 1>(ctx, out, gC, gC_next, Ns, s1, st);
-    return launch_brick<T, 16, 3, 2>(ctx, out, gC, gC_next, Ns, s1, st);
-  }
+  if constexpr (sizeof(T) == 8) return launch_brick<T, 8, 2, 2>(ctx, out, gC, gC_next, Ns, s1, st);
+  else return launch_brick<T, 16, 3, 2>(ctx, out, gC, gC_next, Ns, s1, st);
 }
 
 template int launch_nl_pass<double>(const sq3_ctx*, double*, const double*, double*, int,
@@ -989,14 +976,10 @@ template int launch_nl_pass<double>(const sq3_ctx*, double*, const double*, doub
 template int launch_nl_pass<float>(const sq3_ctx*, float*, const float*, float*, int,
                                    double, cudaStream_t);
 
-template void launch_cheb_step<double>(const sq3_ctx*, const double*,
-                                       const double*, double*, const double*,
-                                       double*, int, double, double, double,
-                                       cudaStream_t);
-template void launch_cheb_step<float>(const sq3_ctx*, const float*,
-                                      const float*, float*, const float*,
-                                      float*, int, double, double, double,
-                                      cudaStream_t);
+template void launch_cheb_step<double>(const sq3_ctx*, const double*, const double*, double*,
+                                       int, double, double, double, cudaStream_t);
+template void launch_cheb_step<float>(const sq3_ctx*, const float*, const float*, float*, int,
+                                      double, double, double, cudaStream_t);
 template void launch_nl_project<double>(const sq3_ctx*, const double*, double*,
                                         int, cudaStream_t);
 template void launch_nl_project<float>(const sq3_ctx*, const float*, float*,
