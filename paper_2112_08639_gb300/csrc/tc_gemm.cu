@@ -11,9 +11,10 @@
 // 64-byte swizzle row of bf16).  Operands are K-major; each stage holds all
 // pieces of a 128 x 32 A tile and a 128 x 32 B tile, loaded by one 3-D TMA
 // copy per operand with 64-byte swizzle; four stages (three pieces) keep
-// three copies in flight while the tensor core works on the fourth.  One thread issues the TMA copies and the MMAs; a
-// multi-stage mbarrier ring overlaps the copies of later K-blocks with the
-// MMAs of the current one.  The accumulator (128 lanes x 128 FP32 columns)
+// three copies in flight while the tensor core works on the fourth.  One
+// thread issues the TMA copies and another the MMAs, so a refill never waits
+// behind an MMA issue; a multi-stage mbarrier ring overlaps the copies of
+// later K-blocks with the MMAs of the current one.  The accumulator (128 lanes x 128 FP32 columns)
 // is read back by four warps with tcgen05.ld, each warp owning 32 rows, and
 // fed to a fused epilogue:
 //   EPI_TC_ATOMIC  C(m,n) += acc (FP64 atomics; split-K Gram and X^T (H X))
@@ -123,7 +124,8 @@ __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long lo
 }
 
 // Thread roles (640 threads): warp 0 allocates TMEM and its lane 0 issues
-// the TMA copies and the MMAs; warps 4..19 are the accumulation warps.  Each
+// the TMA copies (refilling a stage as soon as its MMAs complete); lane 0 of
+// warp 1 issues the MMAs; warps 4..19 are the accumulation warps.  Each
 // K-block's piece products go into a fresh TMEM accumulator (two of them,
 // alternating), so the tensor core never adds into a long running sum; the
 // accumulation warps read every finished K-block partial and add it into
@@ -145,9 +147,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // full[s], empty[s] for the smem stages; accf[b], acce[b] for the two
   // TMEM accumulators
-  __shared__ __align__(8) uint64_t bars[2 * STAGES + 4];
+  __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed;
+  __shared__ int n_issued, n_consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.y, nt = blockIdx.x;
@@ -166,6 +169,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   const uint32_t empty0 = smem_u32(&bars[STAGES]);
   const uint32_t accf0 = smem_u32(&bars[2 * STAGES]);
   const uint32_t acce0 = smem_u32(&bars[2 * STAGES + 2]);
+  const uint32_t done0 = smem_u32(&bars[2 * STAGES + 4]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -182,7 +186,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       mbar_init(accf0 + 8 * b, 1);
       mbar_init(acce0 + 8 * b, ACC_WARPS);
     }
+    mbar_init(done0, 1);
     failed = 0;
+    n_issued = 0;
+    n_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -190,22 +197,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // ------------------------- producer / MMA issuer -----------------------
-    const uint32_t idesc = idesc_bf16();
-    int issued = 0;
-    bool ok = true;
-    auto issue = [&](int kb) {
+  if (warp == 0 && lane == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    // refills a stage as soon as the MMAs that read it have completed
+    int kb = 0;
+    for (; kb < nk; ++kb) {
       const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / STAGES) - 1) & 1))) {
+        atomicExch(&failed, 1);
+        atomicCAS(p.status, 0, DEV_TIMEOUT);
+        break;
+      }
+      if (*(volatile int*)&failed) break;
       const uint32_t sa = base + s * STAGE_BYTES;
-      const uint32_t sb = sa + PA * TILE_BYTES;
       const uint32_t fb = full0 + 8 * s;
       mbar_expect_tx(fb, STAGE_BYTES);
       tma_load_3d(sa, &mapA, fb, kbeg + kb * BK, m0, 0);
-      tma_load_3d(sb, &mapB, fb, kbeg + kb * BK, n0, 0);
-    };
-    for (; issued < nk && issued < STAGES; ++issued) issue(issued);
-    for (int kb = 0; kb < nk && ok; ++kb) {
+      tma_load_3d(sa + PA * TILE_BYTES, &mapB, fb, kbeg + kb * BK, n0, 0);
+    }
+    n_issued = kb;
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------- MMA issuer -------------------------------
+    const uint32_t idesc = idesc_bf16();
+    bool ok = true;
+    int kb = 0;
+    for (; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const int grp = kb / KPP;                 // TMEM partial this stage feeds
       const int buf = grp & 1;
@@ -231,19 +247,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       }
       mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
       if (last) mma_commit(accf0 + 8 * buf);   // partial of up to KPP stages ready
-      if (kb >= 1 && issued < nk) {
-        const int sp = (kb - 1) % STAGES;
-        if (!mbar_wait(empty0 + 8 * sp, ((kb - 1) / STAGES) & 1)) { ok = false; break; }
-        issue(issued);
-        ++issued;
-      }
     }
     if (!ok) {
       atomicExch(&failed, 1);
       atomicCAS(p.status, 0, DEV_TIMEOUT);
-      for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
-        mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
     }
+    n_consumed = kb;
+    // every MMA issued here completes before TMEM is released
+    mma_commit(done0);
+    mbar_wait(done0, 0);
   }
 
   // ------------------------------ accumulation ------------------------------
@@ -287,6 +299,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   }
   __syncthreads();
   have = have && (failed == 0);
+  if (failed && threadIdx.x == 0) {
+    // copies issued but never consumed: wait (bounded) until they land
+    for (int kb = n_consumed; kb < n_issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+  }
 
   // ------------------------------- epilogue --------------------------------
   if (accw) {
