@@ -337,6 +337,16 @@ cheb_step_vec_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
   }
 }
 
+// Row stride of the ring's window: the row plus PAD wrapped columns per
+// side, padded so that the stride is congruent to nx modulo the 128-byte
+// bank cycle; a warp whose threads straddle two rows then maps onto banks as
+// if the rows were contiguous (no bank conflicts between its quarter-warps).
+template <typename T>
+__host__ __device__ inline int ring_row_width(int nx, int pad) {
+  const int cyc = 128 / (int)sizeof(T);
+  return nx + 2 * pad + ((cyc - (2 * pad) % cyc) % cyc);
+}
+
 // Pipelined form of the vectorised step.  The same tile and register queue,
 // but every plane's inputs arrive by asynchronous copies issued A planes
 // ahead into a ring of A + 1 shared-memory entries, so each thread keeps
@@ -360,7 +370,7 @@ cheb_step_ring_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
   constexpr int KC = 4;                  // window copies per thread per plane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = nx / VW;
-  const int Wd = nx + 2 * PAD;
+  const int Wd = ring_row_width<T>(nx, PAD);
   const int rows = TY + 2 * R;
   const int wsz = rows * Wd;             // one window entry
   const int csz = TY * nx;               // one centre array
@@ -571,7 +581,8 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   if (ring && (TY + 2 * R) * rv <= 4 * TX * TY) {
     constexpr int A = 4;
     const size_t rs = (size_t)(A + 1) *
-                      ((size_t)(TY + 2 * R) * (g.nx + 2 * PAD) + 3 * (size_t)TY * g.nx) *
+                      ((size_t)(TY + 2 * R) * ring_row_width<T>(g.nx, PAD) +
+                       3 * (size_t)TY * g.nx) *
                       sizeof(T);
     if (rs <= 227 * 1024) {
       auto kr = cheb_step_ring_kernel<T, R, A>;
@@ -743,7 +754,8 @@ __device__ __forceinline__ void warp_fold(T (&a)[NV], int lane) {
 
 size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries) {
   return 128 + (size_t)NBUF * VB * NL_BRICK_PTS * es +
-         (size_t)NBUF * 4 * max_balls * (VB + 4) * es + (size_t)2 * max_entries * 4 * es +
+         (size_t)NBUF * max_balls * (4 * (VB + 4) + 16 / es) * es +
+         (size_t)2 * max_entries * 4 * es +
          (size_t)2 * max_entries * sizeof(short) + 8 + (size_t)NBUF * 8;
 }
 
@@ -760,6 +772,9 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   using T4 = typename std::conditional<sizeof(T) == 4, float4, Dbl4>::type;
   constexpr int PTS = NL_BRICK_PTS;
   constexpr int GS = VB + 4;                         // padded row of gloc
+  // a ball's four rows, padded by 16 bytes so that the blocks of different
+  // balls start on different banks (phase 1 gathers rows of several balls)
+  constexpr int BST = 4 * GS + 16 / (int)sizeof(T);
   constexpr int BOX = VB * PTS;                      // elements of one box
   constexpr int NV = 4 * VB;                         // phase-2 sums per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -773,8 +788,8 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes)
   unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   T* ybuf = reinterpret_cast<T*>(sbase);             // NBUF boxes
-  T* gloc = ybuf + NBUF * BOX;                       // NBUF x (4 max_balls) x GS
-  T* qval = gloc + (size_t)NBUF * 4 * max_balls * GS;   // point-major values (x4)
+  T* gloc = ybuf + NBUF * BOX;                       // NBUF x max_balls x BST
+  T* qval = gloc + (size_t)NBUF * max_balls * BST;   // point-major values (x4)
   T* zval = qval + (size_t)4 * max_entries;             // ball-major values (x4)
   short* qlb = reinterpret_cast<short*>(zval + (size_t)4 * max_entries);
   short* zpt = qlb + max_entries;
@@ -805,14 +820,15 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   };
   auto issue_gloc = [&](int g) {                     // all threads, one commit group
     if (g < g1) {
-      T* gl = gloc + (size_t)((g - g0) % NBUF) * 4 * max_balls * GS;
+      T* gl = gloc + (size_t)((g - g0) % NBUF) * max_balls * BST;
       for (int i = tid; i < nrows * VB; i += PTS) {
         const int r = i / VB, v = i - r * VB;
         const int vg = g * VB + v;
         const int pid = slot_pid[4 * s0 + r];
         const bool ok = pid >= 0 && vg < Ns;
         const T* src = gC + (ok ? (long long)pid * Ns + vg : 0);
-        cp_async_zfill<(int)sizeof(T)>(gl + r * GS + v, src, ok ? (int)sizeof(T) : 0);
+        cp_async_zfill<(int)sizeof(T)>(gl + (r >> 2) * BST + (r & 3) * GS + v, src,
+                                       ok ? (int)sizeof(T) : 0);
       }
     }
     cp_async_commit();
@@ -842,7 +858,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     __syncthreads();
     if (abort_flag) break;
     T* yb = ybuf + bi * BOX;
-    const T* gl = gloc + (size_t)bi * 4 * max_balls * GS;
+    const T* gl = gloc + (size_t)bi * max_balls * BST;
     // phase 1: apply, one thread per point, four projectors per entry
     if (e1 > e0) {
       T acc[VB];
@@ -850,7 +866,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       for (int v = 0; v < VB; ++v) acc[v] = T(0);
       for (int e = e0; e < e1; ++e) {
         const T4 c = reinterpret_cast<const T4*>(qval)[e];
-        const T* row = gl + 4 * qlb[e] * GS;
+        const T* row = gl + qlb[e] * BST;
         const T cq[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q)

@@ -38,7 +38,7 @@ namespace tc {
 
 constexpr int BM = 128, BN = 128;
 constexpr int BK = 32;                            // K per smem stage (64-byte rows)
-constexpr int KPP = 2;                            // stages per TMEM partial (64 of K)
+constexpr int KPP = 4;                            // stages per TMEM partial (128 of K)
 constexpr int TILE_BYTES = 128 * BK * 2;          // one piece of a 128 x 32 tile
 constexpr int SMEM_BUDGET = 196608;               // bytes of tile stages
 using namespace ac;
@@ -123,19 +123,20 @@ __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long lo
   }
 }
 
-// Thread roles (640 threads): warp 0 allocates TMEM and its lane 0 issues
+// Thread roles (576 threads): warp 0 allocates TMEM and its lane 0 issues
 // the TMA copies (refilling a stage as soon as its MMAs complete); lane 0 of
-// warp 1 issues the MMAs; warps 4..19 are the accumulation warps.  Each
-// K-block's piece products go into a fresh TMEM accumulator (two of them,
-// alternating), so the tensor core never adds into a long running sum; the
-// accumulation warps read every finished K-block partial and add it into
-// Kahan-compensated FP32 registers (warp 4 + 4h + q owns TMEM lanes
-// 32q..32q+31 and columns 32h..32h+31).  The K-block partial is the sum of
-// at most 4 nprod tensor-core steps started from zero, which bounds the
+// warp 1 issues the MMAs; warps 2..17 are the accumulation warps.  Each
+// K-block (KPP stages, 128 of K) of piece products goes into a fresh TMEM
+// accumulator (two of them, alternating), so the tensor core never adds into
+// a long running sum; the accumulation warps read every finished K-block
+// partial and add it into Kahan-compensated FP32 registers (warp w owns TMEM
+// lanes 32 (w % 4) .. + 31, the lanes it may access, and columns
+// 32 h .. 32 h + 31 with h = (w - 2) / 4).  The K-block partial is the sum of
+// at most 8 nprod tensor-core steps started from zero, which bounds the
 // accumulation error of the result by about that many half-ulps of a
 // K-block partial instead of half an ulp per step of the whole K loop.
 constexpr int ACC_WARPS = 16;
-constexpr int THREADS = 128 + 32 * ACC_WARPS;
+constexpr int THREADS = 64 + 32 * ACC_WARPS;
 constexpr int ACC_COLS = BN / (ACC_WARPS / 4);   // columns per accumulation thread
 
 template <int PA, int PB, int EPI>
@@ -259,9 +260,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   }
 
   // ------------------------------ accumulation ------------------------------
-  const bool accw = warp >= 4;
-  const int aw = warp - 4;
-  const int q4 = aw & 3, half = aw >> 2;
+  // accumulation warp w (2..17) may read only TMEM lanes 32 (w % 4) ..
+  const bool accw = warp >= 2;
+  const int q4 = warp & 3, half = (warp - 2) >> 2;
   float sum[ACC_COLS], comp[ACC_COLS];
 #pragma unroll
   for (int i = 0; i < ACC_COLS; ++i) { sum[i] = 0.f; comp[i] = 0.f; }
