@@ -311,6 +311,13 @@ __global__ void add_shift_maxdiag_kernel(double* S, int n, double rel) {
 // carries rounding errors near its smallest eigenvalues), that pass is
 // redone on S + s I with s = 1e-6 max_i S_ii (shifted Cholesky QR, Fukaya et
 // al. 2020), after which two plain passes follow.
+// Precision of the factors: a pass on the filtered block factors S in FP64
+// and inverts the factor in FP32 (its error, about cond(R) 6e-8, only
+// leaves the block slightly non-orthonormal, which the last pass removes);
+// the last pass factors S = I + E of the nearly orthonormal block by the
+// deviation Cholesky and inverts I + F in the same form, both FP32 with
+// errors relative to |E|.  Should the deviation Cholesky meet a pivot below
+// 1e-3 the last pass falls back to the FP64 factor.
 int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   const long long N = ctx->grid.N;
   MixedBuffers b;
@@ -321,9 +328,16 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes,
               ((size_t)2 * Ns * Ns + Ns) * sizeof(double));
   if (rc) return rc;
+  const size_t nn = (size_t)Ns * Ns;
+  rc = ensure((void**)&ctx->wsLin32, &ctx->wsLin32_bytes, (3 * nn + nn / 2 + 64) * sizeof(float));
+  if (rc) return rc;
   double* S = ctx->wsMat;
-  double* Rinv = S + (size_t)Ns * Ns;
-  double* diag = Rinv + (size_t)Ns * Ns;
+  double* Rinv = S + nn;
+  double* diag = Rinv + nn;
+  float* F32 = ctx->wsLin32;          // factor (FP32)
+  float* W32 = F32 + nn;              // inverse of the factor
+  float* R32 = W32 + nn;              // R^{-1} = W^T
+  float* tmp32 = R32 + nn;            // n * n / 2
   float* W = (float*)ctx->wsX;
   bool shift_now = false, shifted = false;
   int plain_left = 2;
@@ -331,27 +345,54 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
     if (rc) return rc;
-    if (shift_now) {
-      Prof p(ctx, ST_CHOL);
-      add_shift_maxdiag_kernel<<<1, 1024, 0, ctx->stream>>>(S, Ns, 1e-6);
+    const bool last = plain_left == 1 && !shift_now;
+    bool have_r32 = false;
+    if (last) {
+      {
+        const int panels = (Ns + 63) / 64;
+        Prof p(ctx, ST_CHOL, 3 * panels - 1);
+        rc = deviation_cholesky_f32(ctx, S, F32, Ns, ctx->stream);
+      }
+      if (rc) return rc;
+      rc = check_device_status(ctx);
+      if (rc == SQ3_OK) {
+        Prof p(ctx, ST_TRINV);
+        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream);
+        have_r32 = true;
+      } else if (rc != SQ3_ENOTPD) {
+        return rc;
+      }
     }
-    {
-      const int panels = (Ns + 63) / 64;
-      Prof p(ctx, ST_CHOL, 3 * panels - 1);
-      rc = cholesky_lower_f64(ctx, S, Ns, diag, ctx->stream);
+    if (!have_r32) {
+      if (shift_now) {
+        Prof p(ctx, ST_CHOL);
+        add_shift_maxdiag_kernel<<<1, 1024, 0, ctx->stream>>>(S, Ns, 1e-6);
+      }
+      {
+        const int panels = (Ns + 63) / 64;
+        Prof p(ctx, ST_CHOL, 3 * panels - 1);
+        rc = cholesky_lower_f64(ctx, S, Ns, diag, ctx->stream);
+      }
+      if (rc) return rc;
+      rc = check_device_status(ctx);
+      if (rc == SQ3_ENOTPD && !shifted && !last) {
+        shifted = shift_now = true;
+        continue;
+      }
+      if (rc) return rc;
+      if (last) {
+        // fallback of the last pass: the FP64 inverse of the FP64 factor
+        Prof p(ctx, ST_TRINV);
+        tri_inverse_transpose_f64(S, Rinv, Ns, diag, ctx->stream);
+      } else {
+        Prof p(ctx, ST_TRINV);
+        convert_f64_to_f32(S, (long long)nn, F32, ctx->stream);
+        p.launches = 1 + rinv_from_lower_f32(F32, Ns, false, W32, tmp32, R32, ctx->stream);
+        have_r32 = true;
+      }
     }
-    if (rc) return rc;
-    rc = check_device_status(ctx);
-    if (rc == SQ3_ENOTPD && !shifted) {
-      shifted = shift_now = true;
-      continue;
-    }
-    if (rc) return rc;
-    {
-      Prof p(ctx, ST_TRINV);
-      tri_inverse_transpose_f64(S, Rinv, Ns, diag, ctx->stream);
-    }
-    split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
+    if (have_r32) split_matrix<float>(ctx, R32, Ns, b.matA, b);
+    else split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
     split_block_rows(ctx, X, Ns, b);
     {
       Prof p(ctx, ST_XRINV);

@@ -375,7 +375,7 @@ void sq3_destroy(sq3_ctx* c) {
   for (auto& r : c->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
-                  c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe};
+                  c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   delete c;

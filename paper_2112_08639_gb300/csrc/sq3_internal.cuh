@@ -120,6 +120,7 @@ struct sq3_ctx {
   double* wsProj = nullptr; size_t wsProj_bytes = 0;  // projection coeffs
   void* wsSplit = nullptr; size_t wsSplit_bytes = 0;  // bf16 split operands
   double* wsFoe = nullptr; size_t wsFoe_bytes = 0;    // quadrature node values
+  float* wsLin32 = nullptr; size_t wsLin32_bytes = 0;  // FP32 factor, inverse, temporaries
 };
 
 namespace sq3 {
@@ -194,6 +195,17 @@ int cholesky_lower_f64(sq3_ctx* ctx, double* S, int n, double* diag_ws,
 void tri_inverse_transpose_f64(const double* L, double* Rinv, int n,
                                double* diag_ws, cudaStream_t st);
 void symmetrize_f64(double* A, int n, cudaStream_t st);
+// ---- FP32 linear algebra for the mixed Cholesky QR (linalg32.cu) ----
+// F = deviation Cholesky factor of S = I + E (S FP64 column-major n x n):
+// S = (I + F)(I + F)^T with F lower (diagonal included), FP32.  Sets
+// DEV_NOTPD when a pivot 1 + t is not above 1e-3.
+int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaStream_t st);
+// Rinv = L^{-T} (upper, column-major FP32) of the lower-triangular L, or of
+// I + L when dev.  W: n*n floats, tmp: n*n/2 floats of workspace.  Returns
+// the number of kernel launches.
+int rinv_from_lower_f32(const float* L, int n, bool dev, float* W, float* tmp, float* Rinv,
+                         cudaStream_t st);
+void convert_f64_to_f32(const double* A, long long tot, float* B, cudaStream_t st);
 void mirror_upper_f64(double* A, int n, cudaStream_t st);
 void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st);
