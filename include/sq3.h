@@ -212,6 +212,10 @@ const char* sq3_status_string(int status);
 /* Library build string: version and target architecture (static string). */
 const char* sq3_version(void);
 
+/* Name of the last CUDA runtime error behind an SQ3_ECUDA returned on the
+ * calling host thread ("none" if there was none; static string). */
+const char* sq3_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,63 @@ __global__ void split_rows_kernel(const float* __restrict__ src, long long lds, 
   }
 }
 
+// Same result for an FP32 source whose rows are a multiple of 4: a 64-row x
+// 64-column tile goes through shared memory; reads are 16-byte vectors along
+// the rows, and each thread writes 16 consecutive columns of one row as two
+// 16-byte vectors per piece (the column tail past `cols` element by element).
+__global__ void __launch_bounds__(256)
+split_rows_tile_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
+                       __nv_bfloat16* out, long long ld, long long ps) {
+  __shared__ float tile[64][65];
+  const long long r0 = (long long)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = 4 * (t & 15), cc = (t >> 4) + 16 * i;
+    const long long r = r0 + rr;
+    const int c = c0 + cc;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c < cols && r < rows) v = *reinterpret_cast<const float4*>(src + r + (long long)c * lds);
+    tile[cc][rr] = v.x;
+    tile[cc][rr + 1] = v.y;
+    tile[cc][rr + 2] = v.z;
+    tile[cc][rr + 3] = v.w;
+  }
+  __syncthreads();
+  const int rr = t >> 2, g = (t & 3) * 16;
+  const long long r = r0 + rr;
+  if (r >= rows) return;
+  const int c = c0 + g;
+  if (c >= cols) return;
+  __nv_bfloat16 h[3][16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float x = tile[g + k][rr];
+    h[0][k] = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h[0][k]);
+    h[1][k] = __float2bfloat16_rn(r1);
+    h[2][k] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][k]));
+  }
+  __nv_bfloat16* o = out + r * ld + c;
+  if (c + 16 <= cols) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      uint4 w[2];
+      __nv_bfloat16* wp = reinterpret_cast<__nv_bfloat16*>(w);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) wp[k] = h[q][k];
+      uint4* d = reinterpret_cast<uint4*>(o + q * ps);
+      d[0] = w[0];
+      d[1] = w[1];
+    }
+  } else {
+    for (int k = 0; k < cols - c; ++k)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) o[q * ps + k] = h[q][k];
+  }
+}
+
 __global__ void hhat_f32_kernel(const double* __restrict__ Hs, int n, const double* bounds,
                                 float* T0, float* T1, double* moments) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -230,6 +287,13 @@ static void split_block_cols(sq3_ctx* ctx, const float* X, int Ns, __nv_bfloat16
 static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBuffers& b) {
   Prof p(ctx, ST_SPLIT);
   const long long N = ctx->grid.N;
+  if (N % 4 == 0 && b.ldS % 8 == 0 && MIXED_PIECES == 3) {
+    // 16-byte column reads; rows of the pieces are 16-byte aligned (ldS % 8)
+    dim3 grid((unsigned)((N + 63) / 64), (Ns + 63) / 64);
+    split_rows_tile_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
+                                                          N * b.ldS);
+    return;
+  }
   dim3 grid((unsigned)((N + 31) / 32), (Ns + 31) / 32);
   split_rows_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
                                                            N * b.ldS, MIXED_PIECES);
@@ -323,8 +387,6 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   MixedBuffers b;
   int rc = mixed_buffers(ctx, Ns, &b);
   if (rc) return rc;
-  rc = ensure(&ctx->wsX, &ctx->wsX_bytes, (size_t)N * Ns * sizeof(float));
-  if (rc) return rc;
   rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes,
               ((size_t)2 * Ns * Ns + Ns) * sizeof(double));
   if (rc) return rc;
@@ -338,7 +400,6 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   float* W32 = F32 + nn;              // inverse of the factor
   float* R32 = W32 + nn;              // R^{-1} = W^T
   float* tmp32 = R32 + nn;            // n * n / 2
-  float* W = (float*)ctx->wsX;
   bool shift_now = false, shifted = false;
   int plain_left = 2;
   while (plain_left > 0) {
@@ -395,20 +456,15 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     else split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
     split_block_rows(ctx, X, Ns, b);
     {
+      // the product reads X only through its pieces, so it overwrites X
       Prof p(ctx, ST_XRINV);
       TcParams t{};
       t.tri = 2;
-      t.C32 = W;
+      t.C32 = X;
       t.ldc = N;
       t.alpha = 1.f;
       rc = tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
                    EPI_TC_STORE, 1, ctx->stream);
-    }
-    if (rc) return rc;
-    {
-      Prof p(ctx, ST_COPY, 0);
-      rc = cuda_err(cudaMemcpyAsync(X, W, (size_t)N * Ns * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (rc) return rc;
     if (shift_now) shift_now = false;

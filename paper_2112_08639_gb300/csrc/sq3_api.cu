@@ -13,7 +13,15 @@
 
 namespace sq3 {
 
-int cuda_err(cudaError_t e) { return e == cudaSuccess ? SQ3_OK : SQ3_ECUDA; }
+// Name of the last CUDA error seen by this host thread (reported by
+// sq3_last_cuda_error).
+static thread_local const char* g_last_cuda_error = "none";
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return SQ3_OK;
+  g_last_cuda_error = cudaGetErrorName(e);
+  return SQ3_ECUDA;
+}
 
 int ensure(void** p, size_t* have, size_t need) {
   if (need <= *have && *p != nullptr) return SQ3_OK;
@@ -325,6 +333,8 @@ using namespace sq3;
 extern "C" {
 
 const char* sq3_version(void) { return "sq3-gb300 0.1 (sm_103a)"; }
+
+const char* sq3_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char* sq3_status_string(int s) {
   switch (s) {

@@ -220,6 +220,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   } else if (warp == 1 && lane == 0) {
     // ------------------------------- MMA issuer -------------------------------
     const uint32_t idesc = idesc_bf16();
+    // piece offsets of the products in registers (a dynamically indexed
+    // parameter array would be read from local memory on every MMA issue)
+    uint32_t offa[6], offb[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      offa[q] = (uint32_t)((q < p.nprod ? p.prod_a[q] : 0) * TILE_BYTES);
+      offb[q] = (uint32_t)((q < p.nprod ? p.prod_b[q] : 0) * TILE_BYTES);
+    }
     bool ok = true;
     int kb = 0;
     for (; kb < nk; ++kb) {
@@ -238,13 +246,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       const uint32_t sa = base + s * STAGE_BYTES;
       const uint32_t sb = sa + PA * TILE_BYTES;
       const uint32_t td = tmem + (uint32_t)(buf * BN);
-      for (int q = 0; q < p.nprod; ++q) {
-        const uint32_t pa = sa + p.prod_a[q] * TILE_BYTES;
-        const uint32_t pb = sb + p.prod_b[q] * TILE_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk)
-          mma_bf16(td, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
-                   (!first || q > 0 || kk > 0) ? 1u : 0u);
+      for (int q = 0; q < 6; ++q) {
+        if (q < p.nprod) {
+          const uint32_t pa = sa + offa[q];
+          const uint32_t pb = sb + offb[q];
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            mma_bf16(td, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
+                     (!first || q > 0 || kk > 0) ? 1u : 0u);
+        }
       }
       mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
       if (last) mma_commit(accf0 + 8 * buf);   // partial of up to KPP stages ready

@@ -46,6 +46,7 @@ _sigs = {
     "sq3_density": (_i, [_p, _p, _p, _i, _i, _p]),
     "sq3_status_string": (ctypes.c_char_p, [_i]),
     "sq3_version": (ctypes.c_char_p, []),
+    "sq3_last_cuda_error": (ctypes.c_char_p, []),
     "sq3_profile_enable": (_i, [_p, _i]),
     "sq3_lanczos_bounds_noalloc": (_i, [_p, _i, _p, _p]),
     "sq3_profile_read": (_i, [_p, _p, _p, _i]),
@@ -59,7 +60,10 @@ for _name, (_res, _args) in _sigs.items():
 class SQ3Error(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {lib.sq3_status_string(code).decode()} ({code})")
+        msg = f"{where}: {lib.sq3_status_string(code).decode()} ({code})"
+        if code == ECUDA:
+            msg += f" [{lib.sq3_last_cuda_error().decode()}]"
+        super().__init__(msg)
 
 
 def _check(code: int, where: str):
