@@ -126,12 +126,15 @@ split_rows_tile_kernel(const float* __restrict__ src, long long lds, int rows, i
     const int c = c0 + cc;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < cols && r < rows) v = *reinterpret_cast<const float4*>(src + r + (long long)c * lds);
-    tile[cc][rr] = v.x;
-    tile[cc][rr + 1] = v.y;
-    tile[cc][rr + 2] = v.z;
-    tile[cc][rr + 3] = v.w;
+    const int sw = ((cc >> 5) & 1) << 3;         // row swizzle (see the reads)
+    tile[cc][(rr ^ sw)] = v.x;
+    tile[cc][(rr ^ sw) + 1] = v.y;
+    tile[cc][(rr ^ sw) + 2] = v.z;
+    tile[cc][(rr ^ sw) + 3] = v.w;
   }
   __syncthreads();
+  // a warp covers 8 rows x 4 column groups; with the odd tile stride the
+  // groups g and g + 32 would share banks, which the row swizzle separates
   const int rr = t >> 2, g = (t & 3) * 16;
   const long long r = r0 + rr;
   if (r >= rows) return;
@@ -140,7 +143,7 @@ split_rows_tile_kernel(const float* __restrict__ src, long long lds, int rows, i
   __nv_bfloat16 h[3][16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const float x = tile[g + k][rr];
+    const float x = tile[g + k][rr ^ ((((g + k) >> 5) & 1) << 3)];
     h[0][k] = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(h[0][k]);
     h[1][k] = __float2bfloat16_rn(r1);

@@ -754,6 +754,7 @@ __device__ __forceinline__ void warp_fold(T (&a)[NV], int lane) {
 
 size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries) {
   return 128 + (size_t)NBUF * VB * NL_BRICK_PTS * es +
+         (size_t)NL_BRICK_PTS * (VB + 16 / es) * es +
          (size_t)NBUF * max_balls * (4 * (VB + 4) + 16 / es) * es +
          (size_t)2 * max_entries * 4 * es +
          (size_t)2 * max_entries * sizeof(short) + 8 + (size_t)NBUF * 8;
@@ -775,6 +776,11 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   // a ball's four rows, padded by 16 bytes so that the blocks of different
   // balls start on different banks (phase 1 gathers rows of several balls)
   constexpr int BST = 4 * GS + 16 / (int)sizeof(T);
+  // the updated values of the current group again, point-major (row of VB
+  // values padded by 16 bytes), so phase 2 reads a point with 16-byte loads
+  constexpr int YT = VB + 16 / (int)sizeof(T);
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int EV = 16 / (int)sizeof(T);           // elements per 16-byte vector
   constexpr int BOX = VB * PTS;                      // elements of one box
   constexpr int NV = 4 * VB;                         // phase-2 sums per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -788,7 +794,8 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   // TMA boxes start on a 128-byte boundary (the launch adds 128 bytes)
   unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   T* ybuf = reinterpret_cast<T*>(sbase);             // NBUF boxes
-  T* gloc = ybuf + NBUF * BOX;                       // NBUF x max_balls x BST
+  T* ytr = ybuf + NBUF * BOX;                        // PTS x YT: a point's VB values
+  T* gloc = ytr + PTS * YT;                          // NBUF x max_balls x BST
   T* qval = gloc + (size_t)NBUF * max_balls * BST;   // point-major values (x4)
   T* zval = qval + (size_t)4 * max_entries;             // ball-major values (x4)
   short* qlb = reinterpret_cast<short*>(zval + (size_t)4 * max_entries);
@@ -868,13 +875,29 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
         const T4 c = reinterpret_cast<const T4*>(qval)[e];
         const T* row = gl + qlb[e] * BST;
         const T cq[4] = {c.x, c.y, c.z, c.w};
+        // coefficient rows as 16-byte vectors (BST and GS times the element
+        // size are multiples of 16, so every row starts 16-byte aligned)
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q) {
+          const V16* rq = reinterpret_cast<const V16*>(row + q * GS);
 #pragma unroll
-          for (int v = 0; v < VB; ++v) acc[v] += cq[q] * row[q * GS + v];
+          for (int j = 0; j < VB / EV; ++j) {
+            const V16 w = rq[j];
+            const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+            for (int i = 0; i < EV; ++i) acc[j * EV + i] += cq[q] * wp[i];
+          }
+        }
       }
+      T yv[VB];
 #pragma unroll
-      for (int v = 0; v < VB; ++v) yb[v * PTS + tid] += s1 * acc[v];
+      for (int v = 0; v < VB; ++v) {
+        yv[v] = yb[v * PTS + tid] + s1 * acc[v];
+        yb[v * PTS + tid] = yv[v];
+      }
+      V16* yt = reinterpret_cast<V16*>(ytr + tid * YT);
+#pragma unroll
+      for (int j = 0; j < VB / EV; ++j) yt[j] = *reinterpret_cast<const V16*>(yv + j * EV);
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -894,14 +917,20 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
         for (int i = 0; i < NV; ++i) a[i] = T(0);
         for (int f = f0 + lane; f < f1; f += 32) {
           const T4 c = reinterpret_cast<const T4*>(zval)[f];
-          const T* yl = yb + zpt[f];
+          const V16* yl = reinterpret_cast<const V16*>(ytr + zpt[f] * YT);
 #pragma unroll
-          for (int v = 0; v < VB; ++v) {
-            const T y = yl[v * PTS];
-            a[v] += c.x * y;
-            a[VB + v] += c.y * y;
-            a[2 * VB + v] += c.z * y;
-            a[3 * VB + v] += c.w * y;
+          for (int j = 0; j < VB / EV; ++j) {
+            const V16 w = yl[j];
+            const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+            for (int i = 0; i < EV; ++i) {
+              const int v = j * EV + i;
+              const T y = wp[i];
+              a[v] += c.x * y;
+              a[VB + v] += c.y * y;
+              a[2 * VB + v] += c.z * y;
+              a[3 * VB + v] += c.w * y;
+            }
           }
         }
         warp_fold<T, NV>(a, lane);

@@ -79,36 +79,30 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// tcgen05.ld of 8 columns without the wait (pair with tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-        "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
-        "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-        "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long long e,
@@ -123,18 +117,27 @@ __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long lo
   }
 }
 
+// Persistent CTAs (one per SM) walk the output tiles t = blockIdx.x +
+// i gridDim.x; the TMA producer and the MMA issuer run through the stages
+// of successive tiles back to back, so the next tile's copies and MMAs
+// overlap the previous tile's epilogue and no CTA launch separates tiles
+// (per-CTA timestamps of a one-tile-per-CTA form showed about 25 us between
+// one CTA's end and the next CTA's start on an SM).
 // Thread roles (576 threads): warp 0 allocates TMEM and its lane 0 issues
 // the TMA copies (refilling a stage as soon as its MMAs complete); lane 0 of
-// warp 1 issues the MMAs; warps 2..17 are the accumulation warps.  Each
+// warp 1 issues the MMAs; warps 2..17 accumulate and run the epilogue.  Each
 // K-block (KPP stages, 128 of K) of piece products goes into a fresh TMEM
 // accumulator (two of them, alternating), so the tensor core never adds into
-// a long running sum; the accumulation warps read every finished K-block
-// partial and add it into Kahan-compensated FP32 registers (warp w owns TMEM
-// lanes 32 (w % 4) .. + 31, the lanes it may access, and columns
-// 32 h .. 32 h + 31 with h = (w - 2) / 4).  The K-block partial is the sum of
-// at most 8 nprod tensor-core steps started from zero, which bounds the
-// accumulation error of the result by about that many half-ulps of a
-// K-block partial instead of half an ulp per step of the whole K loop.
+// a long running sum; the accumulation warps add every finished K-block
+// partial into a Kahan-compensated FP32 sum that is kept in TMEM as well
+// (columns 2 BN .. 4 BN: sum and compensation; an 18-warp CTA has at most
+// 96 registers per thread).  Warp w owns lanes 32 (w % 4) .. + 31, the lanes
+// it may access, and columns 32 h .. 32 h + 31 with h = (w - 2) / 4.  The
+// K-block partial is the sum of at most 8 nprod tensor-core steps started
+// from zero, which bounds the accumulation error of the result by about
+// that many half-ulps of a K-block partial instead of half an ulp per step
+// of the whole K loop.  tcgen05.ld/st are warp-collective (.sync.aligned):
+// every condition around them is warp-uniform.
 constexpr int ACC_WARPS = 16;
 constexpr int THREADS = 64 + 32 * ACC_WARPS;
 constexpr int ACC_COLS = BN / (ACC_WARPS / 4);   // columns per accumulation thread
@@ -147,23 +150,38 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // full[s], empty[s] for the smem stages; accf[b], acce[b] for the two
-  // TMEM accumulators
+  // TMEM accumulators; done for the MMA issuer's last commit
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed;
   __shared__ int n_issued, n_consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.y, nt = blockIdx.x;
-  const int m0 = mt * BM, n0 = nt * BN;
-  if (p.tri == 1 && nt < mt) return;   // symmetric output: upper tiles only
-
-  const int Keff = (p.tri == 2) ? min(p.K, n0 + BN) : p.K;
-  int kchunk = (Keff + (int)gridDim.z - 1) / (int)gridDim.z;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  const int kbeg = blockIdx.z * kchunk;
-  const int kend = min(Keff, kbeg + kchunk);
-  const int nk = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+  const int ntN = (p.N + BN - 1) / BN, ntM = (p.M + BM - 1) / BM;
+  // tiles of one K split: all of them, or (tri = 1, symmetric output) the
+  // upper ones nt >= mt only, enumerated row by row
+  const int per_split = (p.tri == 1) ? ntM * (2 * ntN - ntM + 1) / 2 : ntN * ntM;
+  const int total = per_split * p.splits;
+  // tile t (K split slowest; within it N tile fastest): output corner, K range
+  auto decode = [&](int t, int& m0, int& n0, int& kbeg, int& nk) {
+    const int kz = t / per_split;
+    int u = t - kz * per_split, mt = 0, nt;
+    if (p.tri == 1) {
+      while (u >= ntN - mt) { u -= ntN - mt; ++mt; }
+      nt = mt + u;
+    } else {
+      nt = u % ntN;
+      mt = u / ntN;
+    }
+    m0 = mt * BM;
+    n0 = nt * BN;
+    const int Keff = (p.tri == 2) ? min(p.K, n0 + BN) : p.K;
+    int kchunk = (Keff + p.splits - 1) / p.splits;
+    kchunk = (kchunk + BK - 1) / BK * BK;
+    kbeg = kz * kchunk;
+    const int kend = min(Keff, kbeg + kchunk);
+    nk = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+  };
 
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]);
@@ -175,7 +193,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(2 * BN));
+                 "r"(4 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
@@ -197,26 +215,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  volatile int* vfailed = &failed;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------ TMA producer ------------------------------
-    // refills a stage as soon as the MMAs that read it have completed
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / STAGES) - 1) & 1))) {
-        atomicExch(&failed, 1);
-        atomicCAS(p.status, 0, DEV_TIMEOUT);
-        break;
+    // g counts stages over all of this CTA's tiles
+    int g = 0;
+    for (int t = blockIdx.x; t < total && !*vfailed; t += gridDim.x) {
+      int m0, n0, kbeg, nk;
+      decode(t, m0, n0, kbeg, nk);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(empty0 + 8 * s, (uint32_t)(((g / STAGES) - 1) & 1))) {
+          atomicExch(&failed, 1);
+          atomicCAS(p.status, 0, DEV_TIMEOUT);
+          break;
+        }
+        if (*vfailed) break;
+        const uint32_t sa = base + s * STAGE_BYTES;
+        const uint32_t fb = full0 + 8 * s;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        tma_load_3d(sa, &mapA, fb, kbeg + kb * BK, m0, 0);
+        tma_load_3d(sa + PA * TILE_BYTES, &mapB, fb, kbeg + kb * BK, n0, 0);
       }
-      if (*(volatile int*)&failed) break;
-      const uint32_t sa = base + s * STAGE_BYTES;
-      const uint32_t fb = full0 + 8 * s;
-      mbar_expect_tx(fb, STAGE_BYTES);
-      tma_load_3d(sa, &mapA, fb, kbeg + kb * BK, m0, 0);
-      tma_load_3d(sa + PA * TILE_BYTES, &mapB, fb, kbeg + kb * BK, n0, 0);
     }
-    n_issued = kb;
+    n_issued = g;
   } else if (warp == 1 && lane == 0) {
     // ------------------------------- MMA issuer -------------------------------
     const uint32_t idesc = idesc_bf16();
@@ -229,129 +252,183 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       offb[q] = (uint32_t)((q < p.nprod ? p.prod_b[q] : 0) * TILE_BYTES);
     }
     bool ok = true;
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const int grp = kb / KPP;                 // TMEM partial this stage feeds
-      const int buf = grp & 1;
-      const bool first = (kb % KPP) == 0;
-      const bool last = (kb % KPP) == KPP - 1 || kb == nk - 1;
-      // the accumulator used two partials ago must have been drained
-      if (first && grp >= 2 && !mbar_wait(acce0 + 8 * buf, ((grp - 2) >> 1) & 1)) {
-        ok = false;
-        break;
-      }
-      if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = base + s * STAGE_BYTES;
-      const uint32_t sb = sa + PA * TILE_BYTES;
-      const uint32_t td = tmem + (uint32_t)(buf * BN);
+    int g = 0, part = 0;        // stages and K-block partials over all tiles
+    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      int m0, n0, kbeg, nk;
+      decode(t, m0, n0, kbeg, nk);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        const int buf = part & 1;
+        const bool first = (kb % KPP) == 0;
+        const bool last = (kb % KPP) == KPP - 1 || kb == nk - 1;
+        // the accumulator used two partials ago must have been drained
+        if (first && part >= 2 && !mbar_wait(acce0 + 8 * buf, ((part - 2) >> 1) & 1)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait(full0 + 8 * s, (g / STAGES) & 1)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = base + s * STAGE_BYTES;
+        const uint32_t sb = sa + PA * TILE_BYTES;
+        const uint32_t td = tmem + (uint32_t)(buf * BN);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        if (q < p.nprod) {
-          const uint32_t pa = sa + offa[q];
-          const uint32_t pb = sb + offb[q];
+        for (int q = 0; q < 6; ++q) {
+          if (q < p.nprod) {
+            const uint32_t pa = sa + offa[q];
+            const uint32_t pb = sb + offb[q];
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            mma_bf16(td, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
-                     (!first || q > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_bf16(td, smem_desc(pa + kk * 32), smem_desc(pb + kk * 32), idesc,
+                       (!first || q > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
+        if (last) {
+          mma_commit(accf0 + 8 * buf);   // partial of up to KPP stages ready
+          ++part;
         }
       }
-      mma_commit(empty0 + 8 * s);      // smem stage free once these MMAs finish
-      if (last) mma_commit(accf0 + 8 * buf);   // partial of up to KPP stages ready
+      if (*vfailed) ok = false;
     }
     if (!ok) {
       atomicExch(&failed, 1);
       atomicCAS(p.status, 0, DEV_TIMEOUT);
     }
-    n_consumed = kb;
+    n_consumed = g;
     // every MMA issued here completes before TMEM is released
     mma_commit(done0);
     mbar_wait(done0, 0);
-  }
-
-  // ------------------------------ accumulation ------------------------------
-  // accumulation warp w (2..17) may read only TMEM lanes 32 (w % 4) ..
-  const bool accw = warp >= 2;
-  const int q4 = warp & 3, half = (warp - 2) >> 2;
-  float sum[ACC_COLS], comp[ACC_COLS];
+  } else if (warp >= 2) {
+    // -------------------- accumulation and epilogue, per tile --------------------
+    const int q4 = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
+    const uint32_t tsum = trow + (uint32_t)(2 * BN + half * ACC_COLS);
+    const uint32_t tcmp = trow + (uint32_t)(3 * BN + half * ACC_COLS);
+    int part = 0;
+    bool alive = true;
+    for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
+      int m0, n0, kbeg, nk;
+      decode(t, m0, n0, kbeg, nk);
+      const int ngrp = (nk + KPP - 1) / KPP;
+      bool have = ngrp > 0;
+      for (int kg = 0; kg < ngrp; ++kg, ++part) {
+        const int buf = part & 1;
+        // one verdict per warp: the TMEM accesses below are warp-collective
+        const bool landed =
+            __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, (part >> 1) & 1));
+        if (!landed) {
+          have = false;
+          alive = false;
+          atomicExch(&failed, 1);
+          atomicCAS(p.status, 0, DEV_TIMEOUT);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ta = trow + (uint32_t)(buf * BN + half * ACC_COLS);
+        // two 8-column chunks per round, all their TMEM loads before one wait
 #pragma unroll
-  for (int i = 0; i < ACC_COLS; ++i) { sum[i] = 0.f; comp[i] = 0.f; }
-  bool have = nk > 0;
-  const int ngrp = (nk + KPP - 1) / KPP;
-  if (accw) {
-    for (int kb = 0; kb < ngrp; ++kb) {
-      const int buf = kb & 1;
-      if (!mbar_wait(accf0 + 8 * buf, (kb >> 1) & 1)) {
-        have = false;
-        atomicExch(&failed, 1);
-        atomicCAS(p.status, 0, DEV_TIMEOUT);
-        break;
+        for (int c = 0; c < ACC_COLS / 8; c += 2) {
+          uint32_t rv[2][8], rs[2][8], rc[2][8];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            tmem_ld8_nw(ta + (c + h) * 8, rv[h]);
+            if (kg > 0) {
+              tmem_ld8_nw(tsum + (c + h) * 8, rs[h]);
+              tmem_ld8_nw(tcmp + (c + h) * 8, rc[h]);
+            }
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float sm[8], cm[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float v = __uint_as_float(rv[h][i]);
+              if (kg == 0) {
+                sm[i] = v;
+                cm[i] = 0.f;
+              } else {                     // Kahan summation
+                const float s0 = __uint_as_float(rs[h][i]);
+                const float yk = v - __uint_as_float(rc[h][i]);
+                const float tt = s0 + yk;
+                cm[i] = (tt - s0) - yk;
+                sm[i] = tt;
+              }
+            }
+            tmem_st8(tsum + (c + h) * 8, sm);
+            tmem_st8(tcmp + (c + h) * 8, cm);
+          }
+        }
+        tmem_wait_st();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * buf)
+                       : "memory");
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + half * ACC_COLS);
-      float v[16];
+      if (__any_sync(0xffffffffu, *vfailed != 0)) {
+        have = false;
+        alive = false;
+      }
+      // epilogue of this tile (the MMAs of the next tile proceed meanwhile);
+      // warp-uniform condition around the TMEM loads, rows past M skip only
+      // the stores
+      const int m = m0 + q4 * 32 + lane;
+      const bool mrow = m < p.M;
+      double rsum = 0.0;
+      if (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB) {
+#pragma unroll 1
+        for (int c = 0; c < ACC_COLS / 8; ++c) {
+          float sm[8], cm[8];
+          if (have) {
+            uint32_t rs[8], rc[8];
+            tmem_ld8_nw(tsum + c * 8, rs);
+            tmem_ld8_nw(tcmp + c * 8, rc);
+            tmem_wait_ld();
 #pragma unroll
-      for (int c = 0; c < ACC_COLS / 16; ++c) {
-        tmem_ld16(ta + c * 16, v);
+            for (int i = 0; i < 8; ++i) {
+              sm[i] = __uint_as_float(rs[i]);
+              cm[i] = __uint_as_float(rc[i]);
+            }
+          }
+          if (!mrow) continue;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {   // Kahan summation
-          const float yk = v[i] - comp[c * 16 + i];
-          const float t = sum[c * 16 + i] + yk;
-          comp[c * 16 + i] = (t - sum[c * 16 + i]) - yk;
-          sum[c * 16 + i] = t;
+          for (int i = 0; i < 8; ++i) {
+            const int n = n0 + half * ACC_COLS + c * 8 + i;
+            if (n >= p.N) continue;
+            const long long e = (long long)m + (long long)n * p.ldc;
+            const double acc = have ? (double)sm[i] - (double)cm[i] : 0.0;
+            if (EPI == EPI_TC_ATOMIC) {
+              atomicAdd(p.C64 + e, acc);
+            } else if (EPI == EPI_TC_STORE) {
+              p.C32[e] = (float)((double)p.alpha * acc);
+            } else if (EPI == EPI_TC_CHEB) {
+              const float tv = (float)(2.0 * acc - (double)p.Tprev[e]);
+              p.C32[e] = tv;
+              split_store(tv, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
+                          p.next_pieces);
+              if (m == n) atomicAdd(p.trace, (double)tv);
+            } else {  // EPI_TC_RHO
+              rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * acc;
+            }
+          }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * buf)
-                     : "memory");
+      if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
     }
   }
+
   __syncthreads();
-  have = have && (failed == 0);
   if (failed && threadIdx.x == 0) {
     // copies issued but never consumed: wait (bounded) until they land
-    for (int kb = n_consumed; kb < n_issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1);
+    for (int g = n_consumed; g < n_issued; ++g)
+      mbar_wait(full0 + 8 * (g % STAGES), (g / STAGES) & 1);
   }
-
-  // ------------------------------- epilogue --------------------------------
-  if (accw) {
-    const int m = m0 + q4 * 32 + lane;
-    const bool mrow = m < p.M;
-    double rsum = 0.0;
-    if (mrow && (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB)) {
-#pragma unroll
-      for (int i = 0; i < ACC_COLS; ++i) {
-        const int n = n0 + half * ACC_COLS + i;
-        if (n >= p.N) continue;
-        const long long e = (long long)m + (long long)n * p.ldc;
-        const double acc = have ? (double)sum[i] - (double)comp[i] : 0.0;
-        if (EPI == EPI_TC_ATOMIC) {
-          atomicAdd(p.C64 + e, acc);
-        } else if (EPI == EPI_TC_STORE) {
-          p.C32[e] = (float)((double)p.alpha * acc);
-        } else if (EPI == EPI_TC_CHEB) {
-          const float t = (float)(2.0 * acc - (double)p.Tprev[e]);
-          p.C32[e] = t;
-          split_store(t, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
-                      p.next_pieces);
-          if (m == n) atomicAdd(p.trace, (double)t);
-        } else {  // EPI_TC_RHO
-          rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * acc;
-        }
-      }
-    }
-    if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
-  }
-
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * BN));
+                 "r"(4 * BN));
 }
 
 // ---------------------------------------------------------------------------
@@ -467,7 +544,21 @@ int tc_gemm(sq3_ctx* ctx, const Operand& A, const Operand& B, const Products& pr
   rc = make_map(&mb, B, BN);
   if (rc) return rc;
   if (splits < 1) splits = 1;
-  dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, splits);
+  p.splits = splits;
+  // persistent CTAs, one per SM, each walking tiles t = blockIdx.x + i gridDim.x
+  const long long tN = (p.N + BN - 1) / BN, tM = (p.M + BM - 1) / BM;
+  if (p.tri == 1 && tN < tM) return SQ3_EINVAL;   // upper tiles need N >= M
+  const long long tiles = (p.tri == 1 ? tM * (2 * tN - tM + 1) / 2 : tN * tM) * splits;
+  if (tiles > (1LL << 30)) return SQ3_EINVAL;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      sms = 152;
+  }
+  dim3 grid((unsigned)(tiles < sms ? tiles : sms));
   switch (epi) {
     case EPI_TC_ATOMIC: return launch_e<EPI_TC_ATOMIC>(A.pieces, B.pieces, ma, mb, p, grid, st);
     case EPI_TC_STORE: return launch_e<EPI_TC_STORE>(A.pieces, B.pieces, ma, mb, p, grid, st);

@@ -30,6 +30,7 @@ struct TcParams {
   int nprod;
   int prod_a[6], prod_b[6];
   int tri;               // 1: upper output tiles only; 2: B upper triangular
+  int splits;            // K splits (set by tc_gemm)
   int* status;
   // outputs (column-major with leading dimension ldc)
   double* C64;           // EPI_TC_ATOMIC
