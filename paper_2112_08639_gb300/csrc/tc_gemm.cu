@@ -148,6 +148,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapB, TcParams p) {
   constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
+  // products whose K is a block dimension (Ns: few partials per tile) sum
+  // the partials in registers; the split-K Gram products over the grid keep
+  // a Kahan sum in TMEM
+  constexpr bool REG = EPI != EPI_TC_ATOMIC;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // full[s], empty[s] for the smem stages; accf[b], acce[b] for the two
   // TMEM accumulators; done for the MMA issuer's last commit
@@ -311,6 +315,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       decode(t, m0, n0, kbeg, nk);
       const int ngrp = (nk + KPP - 1) / KPP;
       bool have = ngrp > 0;
+      float ksum[REG ? ACC_COLS : 1];
+#pragma unroll
+      for (int i = 0; i < (REG ? ACC_COLS : 1); ++i) ksum[i] = 0.f;
       for (int kg = 0; kg < ngrp; ++kg, ++part) {
         const int buf = part & 1;
         // one verdict per warp: the TMEM accesses below are warp-collective
@@ -325,6 +332,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ta = trow + (uint32_t)(buf * BN + half * ACC_COLS);
+        if (REG) {
+          // short K (a block dimension, at most a few tens of partials): a
+          // plain FP32 sum of the partials in registers, one TMEM load per
+          // 8 columns (two chunks in flight per wait)
+#pragma unroll
+          for (int c = 0; c < ACC_COLS / 8; c += 2) {
+            uint32_t rv[2][8];
+            tmem_ld8_nw(ta + c * 8, rv[0]);
+            tmem_ld8_nw(ta + (c + 1) * 8, rv[1]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int i = 0; i < 8; ++i) ksum[(c + h) * 8 + i] += __uint_as_float(rv[h][i]);
+          }
+        } else {
         // two 8-column chunks per round, all their TMEM loads before one wait
 #pragma unroll
         for (int c = 0; c < ACC_COLS / 8; c += 2) {
@@ -359,6 +382,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             tmem_st8(tcmp + (c + h) * 8, cm);
           }
         }
+        }
         tmem_wait_st();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -377,10 +401,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       const bool mrow = m < p.M;
       double rsum = 0.0;
       if (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB) {
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < ACC_COLS / 8; ++c) {
           float sm[8], cm[8];
-          if (have) {
+          if (REG) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              sm[i] = ksum[(REG ? c * 8 + i : 0)];
+              cm[i] = 0.f;
+            }
+          } else if (have) {
             uint32_t rs[8], rc[8];
             tmem_ld8_nw(tsum + c * 8, rs);
             tmem_ld8_nw(tcmp + c * 8, rc);
