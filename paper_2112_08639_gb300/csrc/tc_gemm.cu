@@ -148,10 +148,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapB, TcParams p) {
   constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
-  // products whose K is a block dimension (Ns: few partials per tile) sum
-  // the partials in registers; the split-K Gram products over the grid keep
-  // a Kahan sum in TMEM
+  // every K-block partial goes into an FP32 sum in registers; products whose
+  // K is a block dimension (Ns: a few tens of partials per tile) use that sum
+  // as it is, the split-K Gram products over the grid fold it every GROUPP
+  // partials into a Kahan-compensated sum kept in TMEM
   constexpr bool REG = EPI != EPI_TC_ATOMIC;
+  constexpr int GROUPP = 16;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // full[s], empty[s] for the smem stages; accf[b], acce[b] for the two
   // TMEM accumulators; done for the MMA issuer's last commit
@@ -315,9 +317,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       decode(t, m0, n0, kbeg, nk);
       const int ngrp = (nk + KPP - 1) / KPP;
       bool have = ngrp > 0;
-      float ksum[REG ? ACC_COLS : 1];
+      float ksum[ACC_COLS];
 #pragma unroll
-      for (int i = 0; i < (REG ? ACC_COLS : 1); ++i) ksum[i] = 0.f;
+      for (int i = 0; i < ACC_COLS; ++i) ksum[i] = 0.f;
       for (int kg = 0; kg < ngrp; ++kg, ++part) {
         const int buf = part & 1;
         // one verdict per warp: the TMEM accesses below are warp-collective
@@ -332,58 +334,53 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ta = trow + (uint32_t)(buf * BN + half * ACC_COLS);
-        if (REG) {
-          // short K (a block dimension, at most a few tens of partials): a
-          // plain FP32 sum of the partials in registers, one TMEM load per
-          // 8 columns (two chunks in flight per wait)
-#pragma unroll
-          for (int c = 0; c < ACC_COLS / 8; c += 2) {
-            uint32_t rv[2][8];
-            tmem_ld8_nw(ta + c * 8, rv[0]);
-            tmem_ld8_nw(ta + (c + 1) * 8, rv[1]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-              for (int i = 0; i < 8; ++i) ksum[(c + h) * 8 + i] += __uint_as_float(rv[h][i]);
-          }
-        } else {
-        // two 8-column chunks per round, all their TMEM loads before one wait
+        // the partial into the FP32 register sum, one TMEM load per 8 columns
+        // (two chunks in flight per wait)
 #pragma unroll
         for (int c = 0; c < ACC_COLS / 8; c += 2) {
-          uint32_t rv[2][8], rs[2][8], rc[2][8];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            tmem_ld8_nw(ta + (c + h) * 8, rv[h]);
-            if (kg > 0) {
-              tmem_ld8_nw(tsum + (c + h) * 8, rs[h]);
-              tmem_ld8_nw(tcmp + (c + h) * 8, rc[h]);
-            }
-          }
+          uint32_t rv[2][8];
+          tmem_ld8_nw(ta + c * 8, rv[0]);
+          tmem_ld8_nw(ta + (c + 1) * 8, rv[1]);
           tmem_wait_ld();
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float sm[8], cm[8];
+          for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float v = __uint_as_float(rv[h][i]);
-              if (kg == 0) {
-                sm[i] = v;
+            for (int i = 0; i < 8; ++i) ksum[(c + h) * 8 + i] += __uint_as_float(rv[h][i]);
+        }
+        if (!REG && ((kg + 1) % GROUPP == 0 || kg == ngrp - 1)) {
+          // long K: every GROUPP partials the register sum is added into a
+          // Kahan-compensated sum kept in TMEM, then restarts from zero
+          const bool first_fold = kg < GROUPP;
+#pragma unroll
+          for (int c = 0; c < ACC_COLS / 8; ++c) {
+            float sm[8], cm[8];
+            if (first_fold) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                sm[i] = ksum[c * 8 + i];
                 cm[i] = 0.f;
-              } else {                     // Kahan summation
-                const float s0 = __uint_as_float(rs[h][i]);
-                const float yk = v - __uint_as_float(rc[h][i]);
+              }
+            } else {
+              uint32_t rs[8], rc[8];
+              tmem_ld8_nw(tsum + c * 8, rs);
+              tmem_ld8_nw(tcmp + c * 8, rc);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float s0 = __uint_as_float(rs[i]);
+                const float yk = ksum[c * 8 + i] - __uint_as_float(rc[i]);
                 const float tt = s0 + yk;
                 cm[i] = (tt - s0) - yk;
                 sm[i] = tt;
               }
             }
-            tmem_st8(tsum + (c + h) * 8, sm);
-            tmem_st8(tcmp + (c + h) * 8, cm);
+            tmem_st8(tsum + c * 8, sm);
+            tmem_st8(tcmp + c * 8, cm);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ksum[c * 8 + i] = 0.f;
           }
+          tmem_wait_st();
         }
-        }
-        tmem_wait_st();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
@@ -407,7 +404,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
           if (REG) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              sm[i] = ksum[(REG ? c * 8 + i : 0)];
+              sm[i] = ksum[c * 8 + i];
               cm[i] = 0.f;
             }
           } else if (have) {
