@@ -38,24 +38,30 @@ __global__ void __launch_bounds__(256)
 potrf_diag_kernel(double* S, int n, int k0, int kb, const double* diag0,
                   int* status) {
   __shared__ double A[CH_NB][CH_NB + 1];
+  __shared__ double d0[CH_NB];
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     int i = e % kb, j = e / kb;
     A[i][j] = S[(k0 + i) + (long long)(k0 + j) * n];
   }
+  for (int i = threadIdx.x; i < kb; i += blockDim.x) d0[i] = diag0[k0 + i];
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
   for (int j = 0; j < kb; ++j) {
     double d = A[j][j];
-    if (!(d > 1e-13 * diag0[k0 + j]) || !isfinite(d)) {
+    if (!(d > 1e-13 * d0[j]) || !isfinite(d)) {
       if (threadIdx.x == 0) set_status(status, DEV_NOTPD);
       d = 1.0;
     }
-    const double sd = sqrt(d), inv = 1.0 / d;
+    // one square root and one division per column; the rest multiplies
+    const double sd = sqrt(d), rsd = 1.0 / sd, inv = rsd * rsd;
     for (int i = j + threadIdx.x; i < kb; i += blockDim.x)
-      S[(k0 + i) + (long long)(k0 + j) * n] = (i == j) ? sd : A[i][j] / sd;
-    const int m = kb - j - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e % m, l = j + 1 + e / m;
-      if (l <= i) A[i][l] -= A[i][j] * A[l][j] * inv;
+      S[(k0 + i) + (long long)(k0 + j) * n] = (i == j) ? sd : A[i][j] * rsd;
+    // trailing lower triangle: warp w takes columns l = j+1+w, j+1+w+nw, ..,
+    // its lanes the rows i >= l (no index division)
+    for (int l = j + 1 + warp; l < kb; l += nw) {
+      const double alj = A[l][j] * inv;
+      for (int i = l + lane; i < kb; i += 32) A[i][l] -= A[i][j] * alj;
     }
     __syncthreads();
   }

@@ -159,10 +159,12 @@ potrf_dev_kernel(float* E, int n, int k0, int kb, int* status) {
       if (i > j) lsh[i] = v;
     }
     __syncthreads();
-    const int m = kb - j - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e % m, c = j + 1 + e / m;
-      if (c <= i) A[i][c] -= lsh[i] * lsh[c];
+    // trailing lower triangle: warp w takes columns c = j+1+w, j+1+w+nw, ..,
+    // its lanes the rows i >= c (no index division)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = j + 1 + warp; c < kb; c += nw) {
+      const float lc = lsh[c];
+      for (int i = c + lane; i < kb; i += 32) A[i][c] -= lsh[i] * lc;
     }
     __syncthreads();
   }

@@ -95,9 +95,7 @@ __global__ void to_float_kernel(const double* a, float* b, long long n) {
 }
 
 static void free_projectors(Projectors& P) {
-  void* ptrs[] = {P.ball_ptr,   P.ball_idx,    P.ball_proj0, P.ball_nproj,
-                  P.ball_valoff, P.ball_val,   P.ball_valf,  P.gamma,
-                  P.nb_ball_ptr, P.nb_slot_pid, P.nb_pt_ptr, P.nb_pt_lb,
+  void* ptrs[] = {P.gamma,       P.nb_ball_ptr, P.nb_slot_pid, P.nb_pt_ptr, P.nb_pt_lb,
                   P.nb_pt_val,   P.nb_pt_valf, P.nb_bl_ptr,  P.nb_bl_pt,
                   P.nb_bl_val,   P.nb_bl_valf};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -135,8 +133,11 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   int rc = gc_buffer(ctx, Ns, &gC);
   if (rc) return rc;
   if (ctx->proj.n_proj) {
+    // projections of X by the nonlocal pass in projection-only mode
     Prof p(ctx, ST_NL_PROJECT);
-    launch_nl_project<T>(ctx, X, (T*)gC, Ns, ctx->stream);
+    cudaMemsetAsync(gC, 0, (size_t)ctx->proj.n_proj * Ns * sizeof(T), ctx->stream);
+    rc = launch_nl_pass<T>(ctx, const_cast<T*>(X), nullptr, (T*)gC, Ns, 0.0, ctx->stream);
+    if (rc) return rc;
   }
   {
     Prof p(ctx, ST_STENCIL);
@@ -194,8 +195,10 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
     }
   };
   if (nl) {
+    // projections of the input block (projection-only nonlocal pass)
     Prof p(ctx, ST_NL_PROJECT);
-    launch_nl_project<T>(ctx, X, gC, Ns, ctx->stream);
+    cudaMemsetAsync(gC, 0, gbytes, ctx->stream);
+    nrc = launch_nl_pass<T>(ctx, X, nullptr, gC, Ns, 0.0, ctx->stream);
   }
   step(X, nullptr, W, s1 / e, 0.0, m > 1);
   for (int k = 2; k <= m; ++k) {
@@ -473,18 +476,10 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
     bptr.push_back((int)bidx.size());
     p = q;
   }
-  std::vector<float> bvalf(bval.begin(), bval.end());
   Projectors P;
   P.n_proj = n_proj;
   P.n_ball = (int)bp0.size();
   int rc = SQ3_OK;
-  rc = rc ? rc : upload(&P.ball_ptr, bptr.data(), bptr.size());
-  rc = rc ? rc : upload(&P.ball_idx, bidx.data(), bidx.size());
-  rc = rc ? rc : upload(&P.ball_proj0, bp0.data(), bp0.size());
-  rc = rc ? rc : upload(&P.ball_nproj, bnp.data(), bnp.size());
-  rc = rc ? rc : upload(&P.ball_valoff, boff.data(), boff.size());
-  rc = rc ? rc : upload(&P.ball_val, bval.data(), bval.size());
-  rc = rc ? rc : upload(&P.ball_valf, bvalf.data(), bvalf.size());
   rc = rc ? rc : upload(&P.gamma, gamma, (size_t)n_proj);
   // brick tables for the nonlocal pass (8 x 8 x NL_BZ bricks, x fastest),
   // grouped by ball: the <= 4 projectors of one ball share its points

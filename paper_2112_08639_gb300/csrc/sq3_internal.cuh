@@ -41,23 +41,12 @@ struct Grid {
   double w[SQ3_MAX_FD_RADIUS + 1];   // second-derivative weights (unscaled)
 };
 
-// Projectors grouped into balls: every projector of a ball shares one
-// index list.  Also the transposed (per grid point) table used by the
-// fused apply inside the stencil.
+// Projectors on the device: their energies and the brick tables of the
+// nonlocal pass.  On the host the projectors that share one index list (the
+// <= 4 of an atom) are grouped into balls first; the tables are per ball.
 struct Projectors {
   int n_proj = 0;
   int n_ball = 0;
-  int max_per_ball = 0;       // projectors per ball (<= 4 used by kernels)
-  // ball b: points ball_ptr[b]..ball_ptr[b+1]-1 of ball_idx, projectors
-  // ball_proj0[b] .. ball_proj0[b]+ball_nproj[b]-1; values ball_val[p_local
-  // * nnz_ball + e] stored per projector contiguous over the ball points.
-  int* ball_ptr = nullptr;
-  int* ball_idx = nullptr;
-  int* ball_proj0 = nullptr;
-  int* ball_nproj = nullptr;
-  int* ball_valoff = nullptr;   // offset of the ball's value block in val arrays
-  double* ball_val = nullptr;   // c = chi sqrt(dV), FP64
-  float* ball_valf = nullptr;   // same, FP32
   double* gamma = nullptr;      // n_proj
   // Nonlocal-pass tables per 8 x 8 x NL_BZ brick b of the grid (bricks x
   // fastest; local point t = tx + 8 ty + 64 tz), grouped by ball:
@@ -158,15 +147,12 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out, in
 // Dynamic shared memory of the nonlocal pass for element size es, VB vectors
 // per box, NBUF boxes, and the largest brick (balls, entries).
 size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries);
-// Returns an SQ3_* status (EINVAL when a brick's tables exceed shared memory
-// or out is not 16-byte aligned).
+// With gC == nullptr the pass only projects (gC_next += gamma c^T out) and
+// leaves out untouched.  Returns an SQ3_* status (EINVAL when a brick's
+// tables exceed shared memory or out is not 16-byte aligned).
 template <typename T>
 int launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
                    double s1, cudaStream_t st);
-// gC[p * Ns + vec] = gamma_p * sum_k c_p[k] y[k + vec*N]  (projector-major)
-template <typename T>
-void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
-                       cudaStream_t st);
 
 // ---- FP64 GEMM (gemm_f64.cu) ----
 enum Epi { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_CHEB = 2, EPI_RHO = 3 };

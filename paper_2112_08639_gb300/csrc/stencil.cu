@@ -629,85 +629,6 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
 }
 
 // ---------------------------------------------------------------------------
-// Nonlocal projection gC[p * Ns + v] = gamma_p * sum_k c_p[k] y[k + v N].
-// One CTA per (ball, group of VB vectors); a ball's points are read once per
-// group and its (<= 4) projectors are accumulated together.
-// ---------------------------------------------------------------------------
-template <typename T, int VB>
-__global__ void __launch_bounds__(256)
-nl_project_kernel(long long N, int Ns, const T* __restrict__ y,
-                  const int* __restrict__ ball_ptr,
-                  const int* __restrict__ ball_idx,
-                  const int* __restrict__ ball_proj0,
-                  const int* __restrict__ ball_nproj,
-                  const int* __restrict__ ball_valoff,
-                  const T* __restrict__ ball_val,
-                  const double* __restrict__ gamma, int n_proj, T* gC) {
-  const int b = blockIdx.x;
-  const int v0 = blockIdx.y * VB;
-  const int e0 = ball_ptr[b], e1 = ball_ptr[b + 1];
-  const int nnz = e1 - e0;
-  const int np = ball_nproj[b];
-  const T* val = ball_val + ball_valoff[b];
-  T acc[VB][4];
-#pragma unroll
-  for (int v = 0; v < VB; ++v)
-#pragma unroll
-    for (int p = 0; p < 4; ++p) acc[v][p] = T(0);
-  for (int e = threadIdx.x; e < nnz; e += blockDim.x) {
-    const long long k = __ldg(ball_idx + e0 + e);
-    T cv[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) cv[p] = (p < np) ? __ldg(val + p * nnz + e) : T(0);
-#pragma unroll
-    for (int v = 0; v < VB; ++v) {
-      if (v0 + v < Ns) {
-        const T yk = __ldg(y + (long long)(v0 + v) * N + k);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc[v][p] += cv[p] * yk;
-      }
-    }
-  }
-  // block reduction of VB*4 sums
-  __shared__ T red[32][VB * 4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < VB; ++v)
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      T s = acc[v][p];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) red[warp][v * 4 + p] = s;
-    }
-  __syncthreads();
-  const int nwarps = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < VB * 4; t += blockDim.x) {
-    T s = T(0);
-    for (int w = 0; w < nwarps; ++w) s += red[w][t];
-    const int v = t / 4, p = t % 4;
-    if (p < np && v0 + v < Ns) {
-      const int pid = ball_proj0[b] + p;
-      gC[(long long)pid * Ns + v0 + v] = T(gamma[pid]) * s;
-    }
-  }
-}
-
-template <typename T>
-void launch_nl_project(const sq3_ctx* ctx, const T* y, T* gC, int Ns,
-                       cudaStream_t st) {
-  const Projectors& P = ctx->proj;
-  if (P.n_proj == 0) return;
-  constexpr int VB = 8;
-  dim3 grid(P.n_ball, (Ns + VB - 1) / VB);
-  const T* val;
-  if constexpr (sizeof(T) == 8) val = reinterpret_cast<const T*>(P.ball_val);
-  else val = reinterpret_cast<const T*>(P.ball_valf);
-  nl_project_kernel<T, VB><<<grid, 256, 0, st>>>(
-      ctx->grid.N, Ns, y, P.ball_ptr, P.ball_idx, P.ball_proj0, P.ball_nproj,
-      P.ball_valoff, val, P.gamma, P.n_proj, gC);
-}
-
-// ---------------------------------------------------------------------------
 // Nonlocal pass, in place on the output of a local stencil step:
 //   out_v[k] += s1 sum_p c_p[k] gC[p][v]                      (apply)
 //   gC_next[p][v] += gamma_p sum_k c_p[k] out_v[k]            (projection)
@@ -825,8 +746,10 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     tma_load_4d(smem_u32(ybuf + bi * BOX), &omap, bar0 + 8 * bi, bx * 8, by * 8,
                 bz * NL_BZ, g * VB);
   };
+  // gC == nullptr: projection only (no apply, the box is not written back)
+  const bool apply = gC != nullptr;
   auto issue_gloc = [&](int g) {                     // all threads, one commit group
-    if (g < g1) {
+    if (apply && g < g1) {
       T* gl = gloc + (size_t)((g - g0) % NBUF) * max_balls * BST;
       for (int i = tid; i < nrows * VB; i += PTS) {
         const int r = i / VB, v = i - r * VB;
@@ -871,7 +794,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       T acc[VB];
 #pragma unroll
       for (int v = 0; v < VB; ++v) acc[v] = T(0);
-      for (int e = e0; e < e1; ++e) {
+      for (int e = e0; apply && e < e1; ++e) {
         const T4 c = reinterpret_cast<const T4*>(qval)[e];
         const T* row = gl + qlb[e] * BST;
         const T cq[4] = {c.x, c.y, c.z, c.w};
@@ -893,7 +816,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
 #pragma unroll
       for (int v = 0; v < VB; ++v) {
         yv[v] = yb[v * PTS + tid] + s1 * acc[v];
-        yb[v * PTS + tid] = yv[v];
+        if (apply) yb[v * PTS + tid] = yv[v];
       }
       V16* yt = reinterpret_cast<V16*>(ytr + tid * YT);
 #pragma unroll
@@ -901,7 +824,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     }
     fence_proxy_async_smem();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && apply) {
       tma_store_4d(&omap, smem_u32(yb), bx * 8, by * 8, bz * NL_BZ, g * VB);
       bulk_commit();
     }
@@ -1025,9 +948,5 @@ template void launch_cheb_step<double>(const sq3_ctx*, const double*, const doub
                                        int, double, double, double, cudaStream_t);
 template void launch_cheb_step<float>(const sq3_ctx*, const float*, const float*, float*, int,
                                       double, double, double, cudaStream_t);
-template void launch_nl_project<double>(const sq3_ctx*, const double*, double*,
-                                        int, cudaStream_t);
-template void launch_nl_project<float>(const sq3_ctx*, const float*, float*,
-                                       int, cudaStream_t);
 
 }  // namespace sq3

@@ -181,6 +181,17 @@ def random_block(N: int, Ns: int, seed: int = 0) -> np.ndarray:
     return rng.standard_normal((Ns, N))
 
 
+def random_block_device(N: int, Ns: int, seed: int = 0, dtype=None, device="cuda:0"):
+    """X0 ~ N(0, 1) drawn on the device by torch's seeded generator, shape
+    (Ns, N) (N x Ns column-major); for full-size blocks that are too large to
+    draw on the host.  Tests hand the oracle copies of sampled columns."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 104729)
+    return torch.randn((Ns, N), generator=g, device=device,
+                       dtype=torch.float32 if dtype is None else dtype)
+
+
 @dataclasses.dataclass
 class Cell:
     cfg: CellConfig
