@@ -213,8 +213,14 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                            double* D, double* out_host, bool mixed) {
   cudaStream_t st = ctx->stream;
   const long long nn = (long long)Ns * Ns;
-  // workspace: T_0..T_npl (FP64, or FP32 in the mixed path), Lanczos work
-  size_t need_T = (size_t)(npl + 1) * nn * (mixed ? sizeof(float) : sizeof(double));
+  // workspace: T_0..T_npl (FP64), or in the mixed path T_0..T_h (FP32) and
+  // one more Ns x Ns FP32 matrix; Lanczos work
+  // The mixed path runs the recurrence to h = ceil(npl / 2) only: the
+  // moments and the terms of Ds above h follow from the product identity
+  // T_h T_k = (T_{h+k} + T_{h-k}) / 2 (one more tensor-core product).
+  const int h = mixed ? (npl + 1) / 2 : npl;
+  size_t need_T = mixed ? (size_t)(h + 2) * nn * sizeof(float)
+                        : (size_t)(npl + 1) * nn * sizeof(double);
   int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
   if (rc) return rc;
   const int lsteps = Ns < 40 ? Ns : 40;
@@ -239,7 +245,12 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   }
   double* T = ctx->wsT;
   if (mixed) {
-    rc = cheb_recurrence_mixed(ctx, Hs, Ns, npl, bounds, mom, (float*)ctx->wsT);
+    rc = cheb_recurrence_mixed(ctx, Hs, Ns, h, bounds, mom, (float*)ctx->wsT);
+    if (rc) return rc;
+    {
+      Prof p(ctx, ST_CHEB_GEMM, npl > h ? 1 : 0);
+      rc = moments_tail_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, mom);
+    }
     if (rc) return rc;
   } else {
   {
@@ -281,12 +292,15 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                                                          terms);
     fermi_finish_kernel<<<1, 32, 0, st>>>(terms, npl, sigma, outd, ctx->dev_status);
   }
-  Prof pd(ctx, ST_D_ACCUM, D != nullptr ? 1 : 0);
-  if (D != nullptr && mixed)
-    accumulate_d_mixed(ctx, (const float*)ctx->wsT, Ns, npl, coef, D);
-  else if (D != nullptr)
+  if (D != nullptr && mixed) {
+    rc = accumulate_d_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, coef, D,
+                            (float*)ctx->wsT + (size_t)(h + 1) * nn);
+    if (rc) return rc;
+  } else if (D != nullptr) {
+    Prof pd(ctx, ST_D_ACCUM);
     accumulate_d_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
         T, nn, Ns, npl, coef, D);
+  }
   rc = cuda_err(cudaGetLastError());
   if (rc) return rc;
   rc = cuda_err(cudaMemcpyAsync(ctx->host_scal, outd, 6 * sizeof(double),

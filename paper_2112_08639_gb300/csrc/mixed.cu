@@ -193,16 +193,6 @@ __global__ void trace_f32_kernel(const float* __restrict__ A, int n, double* out
   }
 }
 
-__global__ void accumulate_d_f32_kernel(const float* __restrict__ T, long long nn, int n,
-                                        int npl, const double* __restrict__ coef,
-                                        double* D) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= nn) return;
-  const int i = (int)(e % n), j = (int)(e / n);
-  double s = (i == j) ? 0.5 * coef[0] : 0.0;
-  for (int t = 1; t <= npl; ++t) s += coef[t] * (double)T[(long long)t * nn + e];
-  D[e] = s;
-}
 
 __global__ void add_shift_kernel(double* S, int n, double rel) {
   // S += rel * (trace(S)/n) I, computed from the diagonal in one CTA
@@ -492,8 +482,9 @@ int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs) {
 }
 
 // Recurrence of Eq. (ThreeTermRecurrenceRelation) on the tensor cores; fills
-// the FP32 T_j array (npl+1 slots) and the moments m_j (FP64).
-int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+// the FP32 T_j array for j = 0 .. h (h + 1 slots) and the moments m_0 .. m_h
+// (FP64 traces).
+int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int h,
                           const double* bounds, double* mom, float* T) {
   MixedBuffers b;
   int rc = mixed_buffers(ctx, Ns, &b);
@@ -513,8 +504,8 @@ int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   }
   __nv_bfloat16* cur = b.matB;
   __nv_bfloat16* nxt = b.matC;
-  Prof p(ctx, ST_CHEB_GEMM, npl > 1 ? npl - 1 : 0);
-  for (int j = 1; j < npl; ++j) {
+  Prof p(ctx, ST_CHEB_GEMM, h > 1 ? h - 1 : 0);
+  for (int j = 1; j < h; ++j) {
     TcParams t{};
     t.C32 = T + (long long)(j + 1) * nn;
     t.ldc = Ns;
@@ -532,11 +523,74 @@ int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   return SQ3_OK;
 }
 
-void accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, const double* coef,
-                        double* D) {
+// m_{h+k} = tr(T_{h+k}) = 2 tr(T_h T_k) - m_{h-k} for k = 1 .. npl - h, by
+// the product identity T_h T_k = (T_{h+k} + T_{h-k}) / 2; T_h and T_k are
+// symmetric, so tr(T_h T_k) = sum_e T_h[e] T_k[e].  One CTA per k.
+__global__ void __launch_bounds__(1024)
+moments_tail_kernel(const float* __restrict__ T, long long nn, int h, double* mom) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x + 1;
+  const float* Th = T + (long long)h * nn;
+  const float* Tk = T + (long long)k * nn;
+  double s = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) s += (double)Th[e] * (double)Tk[e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    mom[h + k] = 2.0 * t - mom[h - k];
+  }
+}
+
+int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom) {
+  if (npl <= h) return SQ3_OK;
+  moments_tail_kernel<<<npl - h, 1024, 0, ctx->stream>>>(T, (long long)Ns * Ns, h, mom);
+  return cuda_err(cudaGetLastError());
+}
+
+// D = sum'_{j<=h} c_j T_j - sum_{k=1}^{npl-h} c_{h+k} T_{h-k} (FP64) and
+// A2 = 2 sum_{k=1}^{npl-h} c_{h+k} T_k (FP32), so that Ds = D + T_h A2.
+__global__ void d_split_kernel(const float* __restrict__ T, long long nn, int Ns, int npl,
+                               int h, const double* __restrict__ coef, double* D,
+                               float* A2) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % Ns), j = (int)(e / Ns);
+  double d = (i == j) ? 0.5 * coef[0] : 0.0;
+  for (int t = 1; t <= h; ++t) d += coef[t] * (double)T[(long long)t * nn + e];
+  double a = 0.0;
+  for (int k = 1; k <= npl - h; ++k) {
+    d -= coef[h + k] * (double)T[(long long)(h - k) * nn + e];
+    a += coef[h + k] * (double)T[(long long)k * nn + e];
+  }
+  D[e] = d;
+  A2[e] = (float)(2.0 * a);
+}
+
+// Ds = sum'_{j<=npl} c_j T_j from T_0 .. T_h (Eq. (ChebyshevExpansion)),
+// with the terms j > h folded into one tensor-core product T_h A2.
+int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
+                       const double* coef, double* D, float* A2) {
   const long long nn = (long long)Ns * Ns;
-  accumulate_d_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(
-      T, nn, Ns, npl, coef, D);
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  {
+    Prof p(ctx, ST_D_ACCUM);
+    d_split_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(
+        T, nn, Ns, npl, h, coef, D, A2);
+  }
+  if (npl <= h) return cuda_err(cudaGetLastError());
+  split_matrix<float>(ctx, T + (long long)h * nn, Ns, b.matA, b);   // T_h
+  split_matrix<float>(ctx, A2, Ns, b.matB, b);                      // A2
+  Prof p(ctx, ST_D_ACCUM);
+  TcParams t{};
+  t.C64 = D;
+  t.ldc = Ns;
+  return tc_gemm(ctx, op_mat(b.matA, Ns, b), op_mat(b.matB, Ns, b), products(MIXED_PIECES), t,
+                 EPI_TC_ATOMIC, 1, ctx->stream);
 }
 
 int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double* rho) {

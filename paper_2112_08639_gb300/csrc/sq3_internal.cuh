@@ -205,10 +205,11 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
 int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns);
 int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns);
 int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs);
-int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
+int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int h,
                           const double* bounds, double* mom, float* T);
-void accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl,
-                        const double* coef, double* D);
+int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom);
+int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
+                       const double* coef, double* D, float* A2);
 int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns,
                   double* rho);
 
