@@ -41,6 +41,14 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal
 # unit count and maximum clock; probed 1.18 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grid point
+# and vector of one launch of the FP32 kernels, from the ncu captures
+# summarised in profiles/ (32-atom cell: 110,592 points x 640 vectors); the
+# roofline entry scales them to the bench's workload by points x vectors.
+MEASURED_TRAFFIC = {
+    "stencil": (831.3e6 / (110592 * 640), "profiles/cheb_step_ring_f32_al32_48.md"),
+    "nl_pass": (533.7e6 / (110592 * 640), "profiles/nl_brick_f32_al32_48.md"),
+}
 
 
 def parse():
@@ -271,13 +279,19 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
             return dict(bound="alu", kernel="cheb_step (FP64 stencil)", achieved=round(ach, 4),
                         frac=round(ach / FP64_PEAK_TFLOPS, 4), traffic=None, **fp64_peak)
         ach = 3.0 * N * Ns * esize / per_launch_s / 1e9
-        return dict(bound="hbm", kernel="cheb_step_vec (FP32 stencil)", achieved=round(ach, 1),
-                    frac=round(ach / pk["hbm_gbs"], 4), traffic=None, **hbm_peak)
+        bpu, src = MEASURED_TRAFFIC["stencil"]
+        return dict(bound="hbm", kernel="cheb_step_ring (FP32 stencil)", achieved=round(ach, 1),
+                    frac=round(ach / pk["hbm_gbs"], 4), traffic=round(bpu * N * Ns / 1e9, 3),
+                    traffic_unit="GB per launch", algorithmic=round(3.0 * N * Ns * esize / 1e9, 3),
+                    traffic_source=src + ", scaled by points x vectors", **hbm_peak)
     if dominant == "nl_pass":
         ach = 2.0 * n_covered * Ns * esize / per_launch_s / 1e9
-        return dict(bound="hbm", kernel="nl_pass (nonlocal apply + projection)",
-                    achieved=round(ach, 1), frac=round(ach / pk["hbm_gbs"], 4), traffic=None,
-                    **hbm_peak)
+        bpu, src = MEASURED_TRAFFIC["nl_pass"]
+        return dict(bound="hbm", kernel="nl_brick (nonlocal apply + projection)",
+                    achieved=round(ach, 1), frac=round(ach / pk["hbm_gbs"], 4),
+                    traffic=round(bpu * n_covered * Ns / 1e9, 3), traffic_unit="GB per launch",
+                    algorithmic=round(2.0 * n_covered * Ns * esize / 1e9, 3),
+                    traffic_source=src + ", scaled by points x vectors", **hbm_peak)
     gemm_flops = {"gram": N * Ns * Ns, "hs_gemm": N * Ns * Ns, "x_rinv": N * Ns * Ns,
                   "rho": 2 * N * Ns * Ns, "cheb_gemm": 2 * Ns ** 3}
     if dominant in gemm_flops:
