@@ -789,14 +789,23 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     if (abort_flag) break;
     T* yb = ybuf + bi * BOX;
     const T* gl = gloc + (size_t)bi * max_balls * BST;
-    // phase 1: apply, one thread per point, four projectors per entry
-    if (e1 > e0) {
+    // phase 1: apply, one thread per point, four projectors per entry.  The
+    // warp walks the brick's balls in one order (a point's entries are
+    // sorted by ball), so the coefficient rows it reads are the same for all
+    // lanes (shared-memory broadcasts); balls no lane of the warp touches are
+    // skipped.
+    {
       T acc[VB];
 #pragma unroll
       for (int v = 0; v < VB; ++v) acc[v] = T(0);
-      for (int e = e0; apply && e < e1; ++e) {
-        const T4 c = reinterpret_cast<const T4*>(qval)[e];
-        const T* row = gl + qlb[e] * BST;
+      int e = e0;
+      for (int lb = 0; apply && lb < nlb; ++lb) {
+        const bool has = e < e1 && qlb[e] == lb;
+        if (!__any_sync(0xffffffffu, has)) continue;
+        T4 c = reinterpret_cast<const T4*>(qval)[has ? e : 0];
+        if (!has) c.x = c.y = c.z = c.w = T(0);
+        e += has ? 1 : 0;
+        const T* row = gl + lb * BST;
         const T cq[4] = {c.x, c.y, c.z, c.w};
         // coefficient rows as 16-byte vectors (BST and GS times the element
         // size are multiples of 16, so every row starts 16-byte aligned)
@@ -812,15 +821,17 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
           }
         }
       }
-      T yv[VB];
+      if (e1 > e0) {
+        T yv[VB];
 #pragma unroll
-      for (int v = 0; v < VB; ++v) {
-        yv[v] = yb[v * PTS + tid] + s1 * acc[v];
-        if (apply) yb[v * PTS + tid] = yv[v];
+        for (int v = 0; v < VB; ++v) {
+          yv[v] = yb[v * PTS + tid] + s1 * acc[v];
+          if (apply) yb[v * PTS + tid] = yv[v];
+        }
+        V16* yt = reinterpret_cast<V16*>(ytr + tid * YT);
+#pragma unroll
+        for (int j = 0; j < VB / EV; ++j) yt[j] = *reinterpret_cast<const V16*>(yv + j * EV);
       }
-      V16* yt = reinterpret_cast<V16*>(ytr + tid * YT);
-#pragma unroll
-      for (int j = 0; j < VB / EV; ++j) yt[j] = *reinterpret_cast<const V16*>(yv + j * EV);
     }
     fence_proxy_async_smem();
     __syncthreads();
