@@ -330,8 +330,56 @@ static unsigned grid_n2(long long tot) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaStream_t st) {
-  deviation_kernel<<<grid_n2((long long)n * n), 256, 0, st>>>(S, n, F);
+// dinv[i] = 1 / sqrt(S_ii) (0 if S_ii is not positive)
+__global__ void diag_rsqrt_kernel(const double* __restrict__ S, int n, float* dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = S[i + (long long)i * n];
+    dinv[i] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 0.f;
+  }
+}
+
+// E = D^{-1} S D^{-1} - I with D = diag(S)^{1/2}: the deviation of the
+// unit-diagonal scaled Gram matrix
+__global__ void scaled_deviation_kernel(const double* __restrict__ S, int n,
+                                        const float* __restrict__ dinv, float* E) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    E[e] = (float)(S[e] * (double)dinv[i] * (double)dinv[j] - (i == j ? 1.0 : 0.0));
+  }
+}
+
+// out = sum_ij (S_ij - delta_ij)^2 (one CTA)
+__global__ void __launch_bounds__(1024) deviation_norm_kernel(const double* __restrict__ S, int n,
+                                                              double* out) {
+  __shared__ double sh[32];
+  const long long tot = (long long)n * n;
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+    const double d = S[e] - ((e % n) == (e / n) ? 1.0 : 0.0);
+    acc += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+// R(i, :) *= dinv[i]
+__global__ void scale_rows_kernel(float* R, int n, const float* __restrict__ dinv) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x)
+    R[e] *= dinv[(int)(e % n)];
+}
+
+static void deviation_factor(sq3_ctx* ctx, float* F, int n, cudaStream_t st) {
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = (n - k0 < NB) ? n - k0 : NB;
     potrf_dev_kernel<<<1, 256, 0, st>>>(F, n, k0, kb, ctx->dev_status);
@@ -347,6 +395,27 @@ int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaS
     g.tri = 3;
     gemm32(g, 1, st);
   }
+}
+
+int scaled_deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, float* dinv, int n,
+                                  cudaStream_t st) {
+  diag_rsqrt_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, n, dinv);
+  scaled_deviation_kernel<<<grid_n2((long long)n * n), 256, 0, st>>>(S, n, dinv, F);
+  deviation_factor(ctx, F, n, st);
+  return cuda_err(cudaGetLastError());
+}
+
+void deviation_norm_f64(const double* S, int n, double* out, cudaStream_t st) {
+  deviation_norm_kernel<<<1, 1024, 0, st>>>(S, n, out);
+}
+
+void scale_rows_f32(float* R, int n, const float* dinv, cudaStream_t st) {
+  scale_rows_kernel<<<grid_n2((long long)n * n), 256, 0, st>>>(R, n, dinv);
+}
+
+int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaStream_t st) {
+  deviation_kernel<<<grid_n2((long long)n * n), 256, 0, st>>>(S, n, F);
+  deviation_factor(ctx, F, n, st);
   return cuda_err(cudaGetLastError());
 }
 

@@ -384,7 +384,8 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
               ((size_t)2 * Ns * Ns + Ns) * sizeof(double));
   if (rc) return rc;
   const size_t nn = (size_t)Ns * Ns;
-  rc = ensure((void**)&ctx->wsLin32, &ctx->wsLin32_bytes, (3 * nn + nn / 2 + 64) * sizeof(float));
+  rc = ensure((void**)&ctx->wsLin32, &ctx->wsLin32_bytes,
+              (3 * nn + nn / 2 + (size_t)Ns + 64) * sizeof(float));
   if (rc) return rc;
   double* S = ctx->wsMat;
   double* Rinv = S + nn;
@@ -393,25 +394,53 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   float* W32 = F32 + nn;              // inverse of the factor
   float* R32 = W32 + nn;              // R^{-1} = W^T
   float* tmp32 = R32 + nn;            // n * n / 2
-  bool shift_now = false, shifted = false;
+  float* dinv32 = tmp32 + nn / 2 + 32;   // Ns: 1 / sqrt(S_ii)
+  double* devnorm = ctx->dev_scal + 16;  // |S - I|_F^2 of the last pass
+  bool shift_now = false, shifted = false, extra = false;
   int plain_left = 2;
   while (plain_left > 0) {
     split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
     if (rc) return rc;
     const bool last = plain_left == 1 && !shift_now;
-    bool have_r32 = false;
+    bool have_r32 = false, again = false;
     if (last) {
       {
         const int panels = (Ns + 63) / 64;
-        Prof p(ctx, ST_CHOL, 3 * panels - 1);
+        Prof p(ctx, ST_CHOL, 3 * panels);
+        deviation_norm_f64(S, Ns, devnorm, ctx->stream);
+        cudaMemcpyAsync(ctx->host_scal + 16, devnorm, sizeof(double), cudaMemcpyDeviceToHost,
+                        ctx->stream);
         rc = deviation_cholesky_f32(ctx, S, F32, Ns, ctx->stream);
+      }
+      if (rc) return rc;
+      rc = check_device_status(ctx);
+      // a block still far from orthonormal (|X^T X - I|_F > 0.3) gets one
+      // more pass: the orthogonality a pass leaves grows with cond(X)^2
+      again = !extra && ctx->host_scal[16] > 0.09;
+      if (rc == SQ3_OK) {
+        Prof p(ctx, ST_TRINV);
+        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream);
+        have_r32 = true;
+      } else if (rc != SQ3_ENOTPD) {
+        return rc;
+      }
+    } else if (!shift_now) {
+      // the filtered block: the unit-diagonal scaled Gram matrix factored by
+      // the FP32 deviation Cholesky (any upper-triangular factor keeps the
+      // column space; the last pass restores orthonormality); a pivot below
+      // 1e-3 falls back to the FP64 factor below
+      {
+        const int panels = (Ns + 63) / 64;
+        Prof p(ctx, ST_CHOL, 3 * panels);
+        rc = scaled_deviation_cholesky_f32(ctx, S, F32, dinv32, Ns, ctx->stream);
       }
       if (rc) return rc;
       rc = check_device_status(ctx);
       if (rc == SQ3_OK) {
         Prof p(ctx, ST_TRINV);
-        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream);
+        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream) + 1;
+        scale_rows_f32(R32, Ns, dinv32, ctx->stream);
         have_r32 = true;
       } else if (rc != SQ3_ENOTPD) {
         return rc;
@@ -461,6 +490,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     }
     if (rc) return rc;
     if (shift_now) shift_now = false;
+    else if (again) extra = true;       // the last pass once more
     else --plain_left;
   }
   return check_device_status(ctx);

@@ -186,6 +186,15 @@ void symmetrize_f64(double* A, int n, cudaStream_t st);
 // S = (I + F)(I + F)^T with F lower (diagonal included), FP32.  Sets
 // DEV_NOTPD when a pivot 1 + t is not above 1e-3.
 int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaStream_t st);
+// The same on the unit-diagonal scaling D^{-1} S D^{-1} = (I + F)(I + F)^T,
+// D = diag(S)^{1/2}; dinv (n floats) receives 1 / sqrt(S_ii).  Then
+// S = R^T R with R = (I + F)^T D.
+int scaled_deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, float* dinv, int n,
+                                  cudaStream_t st);
+// *out = |S - I|_F^2 (S FP64 column-major n x n)
+void deviation_norm_f64(const double* S, int n, double* out, cudaStream_t st);
+// R(i, :) *= dinv[i] (column-major n x n)
+void scale_rows_f32(float* R, int n, const float* dinv, cudaStream_t st);
 // Rinv = L^{-T} (upper, column-major FP32) of the lower-triangular L, or of
 // I + L when dev.  W: n*n floats, tmp: n*n/2 floats of workspace.  Returns
 // the number of kernel launches.
