@@ -651,28 +651,6 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
 // ---------------------------------------------------------------------------
 struct alignas(16) Dbl4 { double x, y, z, w; };
 
-template <typename T, int NV>
-__device__ __forceinline__ void warp_fold(T (&a)[NV], int lane) {
-  // on return lane L holds in a[0 .. NV/32) the sums over all lanes of
-  // a[(NV/32) L + i]
-  static_assert(NV % 32 == 0, "fold of a multiple of 32 values");
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int s = 16 >> k;
-    constexpr int n0 = NV;
-    const int half = n0 >> (k + 1);
-    const bool up = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < NV / 2; ++i) {
-      if (i < half) {
-        const T send = up ? a[i] : a[i + half];
-        const T keep = up ? a[i + half] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-      }
-    }
-  }
-}
-
 size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries) {
   return 128 + (size_t)NBUF * VB * NL_BRICK_PTS * es +
          (size_t)NL_BRICK_PTS * (VB + 16 / es) * es +
@@ -703,7 +681,6 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   constexpr int EV = 16 / (int)sizeof(T);           // elements per 16-byte vector
   constexpr int BOX = VB * PTS;                      // elements of one box
-  constexpr int NV = 4 * VB;                         // phase-2 sums per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int s0 = ball_ptr[b], nlb = ball_ptr[b + 1] - s0;
@@ -729,7 +706,13 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
   const int eb = pt_ptr[b * PTS];
   const int ne = pt_ptr[(b + 1) * PTS] - eb;
-  const int e0 = pt_ptr[b * PTS + tid] - eb, e1 = pt_ptr[b * PTS + tid + 1] - eb;
+  // phase 1 lanes: a pair of points (x, y, z) and (x, y + 2, z) of the
+  // warp's 8 x 4 slab, and one half of the group's vectors
+  constexpr int VH = VB / 2;
+  const int pp = lane & 15, vh = lane >> 4;
+  const int p1 = warp * 32 + pp, p2 = p1 + 16;
+  const int ea0 = pt_ptr[b * PTS + p1] - eb, ea1 = pt_ptr[b * PTS + p1 + 1] - eb;
+  const int eb0 = pt_ptr[b * PTS + p2] - eb, eb1 = pt_ptr[b * PTS + p2 + 1] - eb;
   const int fb = bl_ptr[s0];
   const int nrows = 4 * nlb;
   const uint32_t bar0 = smem_u32(bars);
@@ -789,48 +772,65 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
     if (abort_flag) break;
     T* yb = ybuf + bi * BOX;
     const T* gl = gloc + (size_t)bi * max_balls * BST;
-    // phase 1: apply, one thread per point, four projectors per entry.  The
-    // warp walks the brick's balls in one order (a point's entries are
-    // sorted by ball), so the coefficient rows it reads are the same for all
-    // lanes (shared-memory broadcasts); balls no lane of the warp touches are
-    // skipped.
+    // phase 1: apply, four projectors per entry.  A lane sums two points
+    // for half of the vectors, so each coefficient row it loads serves both
+    // points.  The warp walks the brick's balls in one order (a point's
+    // entries are sorted by ball), so the coefficient rows it reads are the
+    // same for all lanes of a half (shared-memory broadcasts); balls no lane
+    // of the warp touches are skipped.
     {
-      T acc[VB];
+      T acc1[VH], acc2[VH];
 #pragma unroll
-      for (int v = 0; v < VB; ++v) acc[v] = T(0);
-      int e = e0;
+      for (int v = 0; v < VH; ++v) acc1[v] = acc2[v] = T(0);
+      int ea = ea0, ebb = eb0;
       for (int lb = 0; apply && lb < nlb; ++lb) {
-        const bool has = e < e1 && qlb[e] == lb;
-        if (!__any_sync(0xffffffffu, has)) continue;
-        T4 c = reinterpret_cast<const T4*>(qval)[has ? e : 0];
-        if (!has) c.x = c.y = c.z = c.w = T(0);
-        e += has ? 1 : 0;
-        const T* row = gl + lb * BST;
-        const T cq[4] = {c.x, c.y, c.z, c.w};
-        // coefficient rows as 16-byte vectors (BST and GS times the element
-        // size are multiples of 16, so every row starts 16-byte aligned)
+        const bool h1 = ea < ea1 && qlb[ea] == lb;
+        const bool h2 = ebb < eb1 && qlb[ebb] == lb;
+        if (!__any_sync(0xffffffffu, h1 || h2)) continue;
+        T4 c1 = reinterpret_cast<const T4*>(qval)[h1 ? ea : 0];
+        T4 c2 = reinterpret_cast<const T4*>(qval)[h2 ? ebb : 0];
+        if (!h1) c1.x = c1.y = c1.z = c1.w = T(0);
+        if (!h2) c2.x = c2.y = c2.z = c2.w = T(0);
+        ea += h1 ? 1 : 0;
+        ebb += h2 ? 1 : 0;
+        const T* row = gl + lb * BST + vh * VH;
+        const T cq1[4] = {c1.x, c1.y, c1.z, c1.w};
+        const T cq2[4] = {c2.x, c2.y, c2.z, c2.w};
+        // coefficient rows as 16-byte vectors (BST, GS and VH times the
+        // element size are multiples of 16, so every piece is 16-byte aligned)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const V16* rq = reinterpret_cast<const V16*>(row + q * GS);
 #pragma unroll
-          for (int j = 0; j < VB / EV; ++j) {
+          for (int j = 0; j < VH / EV; ++j) {
             const V16 w = rq[j];
             const T* wp = reinterpret_cast<const T*>(&w);
 #pragma unroll
-            for (int i = 0; i < EV; ++i) acc[j * EV + i] += cq[q] * wp[i];
+            for (int i = 0; i < EV; ++i) {
+              acc1[j * EV + i] += cq1[q] * wp[i];
+              acc2[j * EV + i] += cq2[q] * wp[i];
+            }
           }
         }
       }
-      if (e1 > e0) {
-        T yv[VB];
+      // update and point-major copy; the two halves of the warp take the two
+      // points in opposite order, so one access covers 32 distinct banks
 #pragma unroll
-        for (int v = 0; v < VB; ++v) {
-          yv[v] = yb[v * PTS + tid] + s1 * acc[v];
-          if (apply) yb[v * PTS + tid] = yv[v];
+      for (int k = 0; k < 2; ++k) {
+        const bool second = (k ^ vh) != 0;
+        const int p = second ? p2 : p1;
+        if (second ? eb1 > eb0 : ea1 > ea0) {
+          T yv[VH];
+#pragma unroll
+          for (int i = 0; i < VH; ++i) {
+            const int v = vh * VH + i;
+            yv[i] = yb[v * PTS + p] + s1 * (second ? acc2[i] : acc1[i]);
+            if (apply) yb[v * PTS + p] = yv[i];
+          }
+          V16* yt = reinterpret_cast<V16*>(ytr + p * YT + vh * VH);
+#pragma unroll
+          for (int j = 0; j < VH / EV; ++j) yt[j] = *reinterpret_cast<const V16*>(yv + j * EV);
         }
-        V16* yt = reinterpret_cast<V16*>(ytr + tid * YT);
-#pragma unroll
-        for (int j = 0; j < VB / EV; ++j) yt[j] = *reinterpret_cast<const V16*>(yv + j * EV);
       }
     }
     fence_proxy_async_smem();
@@ -839,39 +839,59 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       tma_store_4d(&omap, smem_u32(yb), bx * 8, by * 8, bz * NL_BZ, g * VB);
       bulk_commit();
     }
-    // phase 2: projection of the updated values, per (ball, half)
+    // phase 2: projection of the updated values, per (ball, half).  A lane
+    // serves one of NSL entry slots and one 16-byte quarter of the group's
+    // vectors: NSL entries are read per step, each slot sums 4 projectors x EV
+    // vectors, and the slots are folded at the end (three shuffle rounds).
     if (gC_next != nullptr) {
+      constexpr int NQ = VB / EV;                    // 16-byte quarters of a point row
+      constexpr int NSL = 32 / NQ;                   // entry slots per warp
+      constexpr int NA = 4 * EV;                     // sums per lane
+      constexpr int NR = NA / NSL;                   // sums per lane after the fold
+      static_assert(NQ == 4 && NR * NSL == NA, "four quarters, eight slots");
+      const int qd = lane % NQ, sl = lane / NQ;
       for (int task = warp; task < 2 * nlb; task += PTS / 32) {
         const int lb = task >> 1;
         const int fa = bl_ptr[s0 + lb] - fb, fe = bl_ptr[s0 + lb + 1] - fb;
         const int fm = fa + (fe - fa + 1) / 2;
         const int f0 = (task & 1) ? fm : fa, f1 = (task & 1) ? fe : fm;
-        T a[NV];
+        T a[NA];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) a[i] = T(0);
-        for (int f = f0 + lane; f < f1; f += 32) {
+        for (int i = 0; i < NA; ++i) a[i] = T(0);
+        for (int f = f0 + sl; f < f1; f += NSL) {
           const T4 c = reinterpret_cast<const T4*>(zval)[f];
-          const V16* yl = reinterpret_cast<const V16*>(ytr + zpt[f] * YT);
+          const V16 w = reinterpret_cast<const V16*>(ytr + zpt[f] * YT)[qd];
+          const T* wp = reinterpret_cast<const T*>(&w);
 #pragma unroll
-          for (int j = 0; j < VB / EV; ++j) {
-            const V16 w = yl[j];
-            const T* wp = reinterpret_cast<const T*>(&w);
+          for (int i = 0; i < EV; ++i) {
+            a[i] += c.x * wp[i];
+            a[EV + i] += c.y * wp[i];
+            a[2 * EV + i] += c.z * wp[i];
+            a[3 * EV + i] += c.w * wp[i];
+          }
+        }
+        // fold over the slots (lane bits above the quarter index): after
+        // round k a lane keeps the half of its sums selected by its slot bit
 #pragma unroll
-            for (int i = 0; i < EV; ++i) {
-              const int v = j * EV + i;
-              const T y = wp[i];
-              a[v] += c.x * y;
-              a[VB + v] += c.y * y;
-              a[2 * VB + v] += c.z * y;
-              a[3 * VB + v] += c.w * y;
+        for (int k = 0; k < 3; ++k) {
+          const int m = 16 >> k;
+          const int half = NA >> (k + 1);
+          const bool up = (lane & m) != 0;
+#pragma unroll
+          for (int i = 0; i < NA / 2; ++i) {
+            if (i < half) {
+              const T send = up ? a[i] : a[i + half];
+              const T keep = up ? a[i + half] : a[i];
+              a[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
             }
           }
         }
-        warp_fold<T, NV>(a, lane);
+        // the lane now holds the sums of a[sl * NR + i] (projector idx / EV,
+        // vector qd * EV + idx % EV)
 #pragma unroll
-        for (int i = 0; i < NV / 32; ++i) {
-          const int idx = (NV / 32) * lane + i;
-          const int q = idx / VB, v = idx - q * VB;
+        for (int i = 0; i < NR; ++i) {
+          const int idx = sl * NR + i;
+          const int q = idx / EV, v = qd * EV + idx % EV;
           const int pid = slot_pid[4 * (s0 + lb) + q];
           const int vg = g * VB + v;
           if (pid >= 0 && vg < Ns && a[i] != T(0))
