@@ -157,7 +157,10 @@ int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
 
 /* rho_k = (2/dV) sum_i X_ki (X Ds)_ki (Sec. 3, Eq. (phi_tilde) and
  * Eq. (density:NewForm)); X Ds is formed tile by tile and never stored.
- * D: device Ns x Ns double; rho: device N doubles (overwritten). */
+ * D: device Ns x Ns double, symmetric (the density kernel is); the mixed
+ * path reads its upper triangle only (x D x^T = x B x^T with the triangular
+ * B = 2 triu(D, 1) + diag(D)), the FP64 path all of it.  rho: device N
+ * doubles (overwritten). */
 int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
                 sq3_prec prec, double* rho);
 

@@ -51,6 +51,21 @@ __global__ void split_cols_kernel(const T* __restrict__ src, long long lds, int 
   }
 }
 
+// Pieces of the upper-triangular B = 2 triu(D, 1) + diag(D) of a symmetric
+// Ns x Ns matrix D, in the layout of split_cols_kernel.  For symmetric D,
+// x D x^T = x B x^T, so the row-dot of the density needs only this B.
+__global__ void split_upper_twice_kernel(const double* __restrict__ D, int Ns,
+                                         __nv_bfloat16* out, long long ld, long long ps,
+                                         int pieces) {
+  const long long tot = (long long)Ns * Ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / Ns, r = e - c * Ns;
+    const double d = D[e];
+    split3(r < c ? 2.0 * d : (r == c ? d : 0.0), out, c * ld + r, ps, pieces);
+  }
+}
+
 // Same layout for an FP32 source, four consecutive rows per thread (16-byte
 // load, 8-byte stores per piece) on a 2-D grid (rows x columns), so no
 // 64-bit division per element.
@@ -545,6 +560,7 @@ int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int h,
     t.next_piece_stride = b.psS;
     t.next_pieces = MIXED_PIECES;
     t.trace = mom + j + 1;
+    t.tri = 1;           // T_{j+1} is symmetric: upper tiles, each stored with its mirror
     rc = tc_gemm(ctx, op_mat(b.matA, Ns, b), op_mat(cur, Ns, b), products(MIXED_PIECES), t,
                  EPI_TC_CHEB, 1, ctx->stream);
     if (rc) return rc;
@@ -619,8 +635,12 @@ int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
   TcParams t{};
   t.C64 = D;
   t.ldc = Ns;
-  return tc_gemm(ctx, op_mat(b.matA, Ns, b), op_mat(b.matB, Ns, b), products(MIXED_PIECES), t,
-                 EPI_TC_ATOMIC, 1, ctx->stream);
+  t.tri = 1;             // T_h A2 is symmetric (both are polynomials of Hhat)
+  rc = tc_gemm(ctx, op_mat(b.matA, Ns, b), op_mat(b.matB, Ns, b), products(MIXED_PIECES), t,
+               EPI_TC_ATOMIC, 1, ctx->stream);
+  if (rc) return rc;
+  mirror_upper_f64(D, Ns, ctx->stream);
+  return cuda_err(cudaGetLastError());
 }
 
 int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double* rho) {
@@ -628,7 +648,12 @@ int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double*
   MixedBuffers b;
   int rc = mixed_buffers(ctx, Ns, &b);
   if (rc) return rc;
-  split_matrix<double>(ctx, D, Ns, b.matA, b);
+  {
+    // x Ds x^T with Ds symmetric: the upper-triangular form halves the product
+    Prof p(ctx, ST_SPLIT);
+    split_upper_twice_kernel<<<grid_for((long long)Ns * Ns), 256, 0, ctx->stream>>>(
+        D, Ns, b.matA, b.ldS, b.psS, MIXED_PIECES);
+  }
   split_block_rows(ctx, X, Ns, b);
   Prof p(ctx, ST_RHO);
   cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), ctx->stream);
@@ -637,6 +662,7 @@ int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double*
   t.ldx = N;
   t.rho = rho;
   t.rho_alpha = 2.0 / ctx->dV;
+  t.tri = 2;                                         // B upper triangular
   return tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
                  EPI_TC_RHO, 1, ctx->stream);
 }

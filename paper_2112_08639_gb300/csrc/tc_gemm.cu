@@ -419,9 +419,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             }
           }
           if (!mrow) continue;
+          float tvs[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int n = n0 + half * ACC_COLS + c * 8 + i;
+            tvs[i] = 0.f;
             if (n >= p.N) continue;
             const long long e = (long long)m + (long long)n * p.ldc;
             const double acc = have ? (double)sm[i] - (double)cm[i] : 0.0;
@@ -431,12 +433,42 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
               p.C32[e] = (float)((double)p.alpha * acc);
             } else if (EPI == EPI_TC_CHEB) {
               const float tv = (float)(2.0 * acc - (double)p.Tprev[e]);
+              tvs[i] = tv;
               p.C32[e] = tv;
               split_store(tv, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
                           p.next_pieces);
               if (m == n) atomicAdd(p.trace, (double)tv);
             } else {  // EPI_TC_RHO
               rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * acc;
+            }
+          }
+          if (EPI == EPI_TC_CHEB && p.tri == 1 && n0 != m0) {
+            // symmetric T_{j+1} from its upper tiles: the mirror of an
+            // off-diagonal tile, row m of it holding this lane's 8 columns
+            const int nb = n0 + half * ACC_COLS + c * 8;
+            float* cm32 = p.C32 + (long long)m * p.ldc + nb;
+            __nv_bfloat16* bm = p.Bnext + (long long)m * p.ld_next + nb;
+            if (nb + 8 <= p.N && (p.ldc & 3) == 0) {
+              reinterpret_cast<float4*>(cm32)[0] = make_float4(tvs[0], tvs[1], tvs[2], tvs[3]);
+              reinterpret_cast<float4*>(cm32)[1] = make_float4(tvs[4], tvs[5], tvs[6], tvs[7]);
+              __align__(16) __nv_bfloat16 pc[3][8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                pc[0][i] = __float2bfloat16_rn(tvs[i]);
+                const float r1 = tvs[i] - __bfloat162float(pc[0][i]);
+                pc[1][i] = __float2bfloat16_rn(r1);
+                pc[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(pc[1][i]));
+              }
+              for (int q = 0; q < p.next_pieces && q < 3; ++q)
+                *reinterpret_cast<uint4*>(bm + q * p.next_piece_stride) =
+                    *reinterpret_cast<const uint4*>(pc[q]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                if (nb + i >= p.N) continue;
+                cm32[i] = tvs[i];
+                split_store(tvs[i], bm, i, p.next_piece_stride, p.next_pieces);
+              }
             }
           }
         }
