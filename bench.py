@@ -292,8 +292,10 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
                     traffic=round(bpu * n_covered * Ns / 1e9, 3), traffic_unit="GB per launch",
                     algorithmic=round(2.0 * n_covered * Ns * esize / 1e9, 3),
                     traffic_source=src + ", scaled by points x vectors", **hbm_peak)
+    # useful flops per launch: symmetric outputs (Gram, Hs, the recurrence)
+    # and triangular B (X R^-1, the density row-dot) count half a full product
     gemm_flops = {"gram": N * Ns * Ns, "hs_gemm": N * Ns * Ns, "x_rinv": N * Ns * Ns,
-                  "rho": 2 * N * Ns * Ns, "cheb_gemm": 2 * Ns ** 3}
+                  "rho": N * Ns * Ns, "cheb_gemm": Ns ** 3}
     if dominant in gemm_flops:
         ach = gemm_flops[dominant] / per_launch_s / 1e12
         if fp64:

@@ -224,7 +224,7 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
   if (rc) return rc;
   const int lsteps = Ns < 40 ? Ns : 40;
-  size_t need_m = ((size_t)(lsteps + 2) * Ns + 2 * lsteps + 8) * sizeof(double);
+  size_t need_m = lanczos_work_words((size_t)Ns, (size_t)lsteps) * sizeof(double);
   rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes, need_m);
   if (rc) return rc;
   if (npl > SQ3_MAX_NPL) return SQ3_EINVAL;
@@ -240,7 +240,7 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                                   cudaMemcpyHostToDevice, st));
     if (rc) return rc;
   } else {
-    Prof p(ctx, ST_LANCZOS, 2 * lsteps + 2);
+    Prof p(ctx, ST_LANCZOS, 5 * lsteps + 2);
     lanczos_bounds_f64(ctx, Hs, Ns, lsteps, bounds, ctx->wsMat, st);
   }
   double* T = ctx->wsT;

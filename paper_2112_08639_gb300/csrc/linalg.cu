@@ -265,74 +265,148 @@ lanczos_init_kernel(double* V, int n, double* kcount) {
   if (threadIdx.x == 0) kcount[0] = 0.0;
 }
 
-// w = Hs v: one warp per output row (Hs symmetric, so row i = column i).
-__global__ void __launch_bounds__(256)
-symv_kernel(const double* __restrict__ Hs, const double* __restrict__ v,
-            double* w, int n, const double* kcount, int j) {
-  if (kcount[0] < j) return;  // Lanczos already terminated
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const double* col = Hs + (long long)warp * n;
+// One Lanczos step j is five grid-wide launches over the n components
+// (LZ_T per block): w = Hs v_j with alpha_j = v_j^T w; the three-term
+// update with the first reorthogonalisation pass's projections; two
+// classical Gram-Schmidt passes against v_0 .. v_j (all projections of a
+// pass computed at once); beta_j and v_{j+1}.  Each block writes its
+// partial sums to its own slot and the next launch adds the slots in a
+// fixed order, so the result does not depend on the order in which blocks
+// run.  Every kernel returns at once after termination (kcount < j).
+constexpr int LZ_T = 256;
+constexpr int LZ_MAXQ = 64;                          // basis vectors (steps) at most
+
+struct LzParts {
+  double* alpha;                                     // [gr]   symv blocks
+  double* h1;                                        // [gv][LZ_MAXQ]
+  double* h2;                                        // [gv][LZ_MAXQ]
+  double* b2;                                        // [gv]
+};
+
+// Sum of the m values p[0], p[stride], ... by the whole block (fixed order).
+__device__ double block_sum_parts(const double* p, int m, long long stride, double* sh) {
   double s = 0.0;
-  for (int k = lane; k < n; k += 32) s += col[k] * v[k];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) w[warp] = s;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) s += p[k * stride];
+  return block_sum(s, sh);
 }
 
-// One Lanczos step after w = Hs v_j: alpha_j, three-term update, full
-// reorthogonalisation against v_0..v_j (two classical Gram-Schmidt passes,
-// all projections of a pass computed at once, one warp per basis vector),
-// beta_j and v_{j+1}.
-__global__ void __launch_bounds__(1024)
-lanczos_update_kernel(double* V, double* w, double* alpha, double* beta,
-                      double* kcount, int n, int j) {
+// w = Hs v: one warp per output row (Hs symmetric, so row i = column i);
+// the block's share of alpha = v^T w into its slot.
+__global__ void __launch_bounds__(LZ_T)
+symv_alpha_kernel(const double* __restrict__ Hs, const double* __restrict__ v,
+                  double* w, int n, const double* kcount, int j, double* apart) {
+  __shared__ double sh[LZ_T / 32];
+  if (kcount[0] < j) return;  // Lanczos already terminated
+  const int row = (blockIdx.x * LZ_T + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (row < n) {
+    const double* col = Hs + (long long)row * n;
+    for (int k = lane; k < n; k += 32) s += col[k] * v[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  if (lane == 0) {
+    if (row < n) w[row] = s;
+    sh[threadIdx.x >> 5] = row < n ? s * v[row] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int k = 0; k < LZ_T / 32; ++k) a += sh[k];
+    apart[blockIdx.x] = a;
+  }
+}
+
+// The block's partial sums of d_q (q = 0 .. nq-1, one value per thread each)
+// into out[blockIdx.x * LZ_MAXQ + q].
+__device__ void block_dots(const double* V, long long n, int i, double t, int nq, double* out) {
+  __shared__ double sh[LZ_MAXQ][LZ_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < nq; ++q) {
+    double d = i < n ? V[(long long)q * n + i] * t : 0.0;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) sh[q][wid] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double d = 0.0;
+    for (int k = 0; k < LZ_T / 32; ++k) d += sh[threadIdx.x][k];
+    out[(long long)blockIdx.x * LZ_MAXQ + threadIdx.x] = d;
+  }
+}
+
+// w -= alpha_j v_j + beta_{j-1} v_{j-1}; projections of the result on v_0..v_j.
+__global__ void __launch_bounds__(LZ_T)
+lanczos_three_term_kernel(const double* V, double* w, const double* beta, int n, int j,
+                          const double* kcount, LzParts P, int gr) {
   __shared__ double sh[32];
-  __shared__ double h[64];
   if (kcount[0] < j) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  const double* vj = V + (long long)j * n;
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += w[i] * vj[i];
-  a = block_sum(a, sh);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double t = w[i] - a * vj[i];
+  const double a = block_sum_parts(P.alpha, gr, 1, sh);
+  const int i = blockIdx.x * LZ_T + threadIdx.x;
+  double t = 0.0;
+  if (i < n) {
+    t = w[i] - a * V[(long long)j * n + i];
     if (j > 0) t -= beta[j - 1] * V[(long long)(j - 1) * n + i];
     w[i] = t;
   }
+  block_dots(V, n, i, t, j + 1, P.h1);
+}
+
+// One Gram-Schmidt pass with the projections summed from the blocks' slots
+// (hin): w -= sum_q h_q v_q; then the projections of the result (hout), or
+// after the last pass the block's share of |w|^2.
+__global__ void __launch_bounds__(LZ_T)
+lanczos_reorth_kernel(const double* V, double* w, int n, int j, const double* kcount,
+                      const double* hin, double* hout, double* b2part, int gv) {
+  __shared__ double hs[LZ_MAXQ];
+  __shared__ double sh[LZ_T / 32];
+  if (kcount[0] < j) return;
+  if (threadIdx.x <= j) {
+    double h = 0.0;
+    for (int k = 0; k < gv; ++k) h += hin[(long long)k * LZ_MAXQ + threadIdx.x];
+    hs[threadIdx.x] = h;
+  }
   __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int t = warp; t <= j; t += nw) {
-      const double* vt = V + (long long)t * n;
-      double d = 0.0;
-      for (int i = lane; i < n; i += 32) d += vt[i] * w[i];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) h[t] = d;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double t = w[i];
-      for (int q = 0; q <= j; ++q) t -= h[q] * V[(long long)q * n + i];
-      w[i] = t;
-    }
-    __syncthreads();
+  const int i = blockIdx.x * LZ_T + threadIdx.x;
+  double t = 0.0;
+  if (i < n) {
+    t = w[i];
+    for (int q = 0; q <= j; ++q) t -= hs[q] * V[(long long)q * n + i];
+    w[i] = t;
   }
-  double b = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) b += w[i] * w[i];
-  b = sqrt(block_sum(b, sh));
-  if (threadIdx.x == 0) {
-    alpha[j] = a;
-    beta[j] = b;
-    kcount[0] = (double)(j + 1);
-  }
-  double scale = fabs(a) + b;
-  if (b <= 1e-12 * (scale > 0 ? scale : 1.0) || j + 1 >= n) {
-    if (threadIdx.x == 0) kcount[0] = -(double)(j + 1);  // terminated
+  if (hout) {
+    block_dots(V, n, i, t, j + 1, hout);
     return;
   }
-  double* vn = V + (long long)(j + 1) * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) vn[i] = w[i] / b;
+  double b = t * t;
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < LZ_T / 32; ++k) s += sh[k];
+    b2part[blockIdx.x] = s;
+  }
+}
+
+// beta_j = |w|, the termination test, v_{j+1} = w / beta_j; block 0 records
+// alpha_j, beta_j and the step count.
+__global__ void __launch_bounds__(LZ_T)
+lanczos_next_kernel(double* V, const double* w, double* alpha, double* beta, double* kcount,
+                    int n, int j, LzParts P, int gr, int gv) {
+  __shared__ double sh[32];
+  if (kcount[0] < j) return;
+  const double a = block_sum_parts(P.alpha, gr, 1, sh);
+  const double b = sqrt(block_sum_parts(P.b2, gv, 1, sh));
+  const double scale = fabs(a) + b;
+  const bool stop = b <= 1e-12 * (scale > 0 ? scale : 1.0) || j + 1 >= n;
+  const int i = blockIdx.x * LZ_T + threadIdx.x;
+  if (!stop && i < n) V[(long long)(j + 1) * n + i] = w[i] / b;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    alpha[j] = a;
+    beta[j] = b;
+    kcount[0] = stop ? -(double)(j + 1) : (double)(j + 1);
+  }
 }
 
 // Number of eigenvalues of the k x k tridiagonal (alpha, beta) below x.
@@ -413,16 +487,26 @@ void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st) {
   (void)ctx;
   if (steps > n) steps = n;
+  if (steps > LZ_MAXQ) steps = LZ_MAXQ;
   double* V = work;
   double* w = V + (long long)(steps + 1) * n;
   double* alpha = w + n;
   double* beta = alpha + steps;
   double* kc = beta + steps;
+  const int gv = (n + LZ_T - 1) / LZ_T;
+  const int gr = (int)(((long long)n * 32 + LZ_T - 1) / LZ_T);
+  LzParts P;
+  P.alpha = kc + 8;
+  P.h1 = P.alpha + gr;
+  P.h2 = P.h1 + (long long)gv * LZ_MAXQ;
+  P.b2 = P.h2 + (long long)gv * LZ_MAXQ;
   lanczos_init_kernel<<<1, 1024, 0, st>>>(V, n, kc);
   for (int j = 0; j < steps; ++j) {
-    symv_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(Hs, V + (long long)j * n,
-                                                       w, n, kc, j);
-    lanczos_update_kernel<<<1, 1024, 0, st>>>(V, w, alpha, beta, kc, n, j);
+    symv_alpha_kernel<<<gr, LZ_T, 0, st>>>(Hs, V + (long long)j * n, w, n, kc, j, P.alpha);
+    lanczos_three_term_kernel<<<gv, LZ_T, 0, st>>>(V, w, beta, n, j, kc, P, gr);
+    lanczos_reorth_kernel<<<gv, LZ_T, 0, st>>>(V, w, n, j, kc, P.h1, P.h2, P.b2, gv);
+    lanczos_reorth_kernel<<<gv, LZ_T, 0, st>>>(V, w, n, j, kc, P.h2, nullptr, P.b2, gv);
+    lanczos_next_kernel<<<gv, LZ_T, 0, st>>>(V, w, alpha, beta, kc, n, j, P, gr, gv);
   }
   lanczos_finish_kernel<<<1, 32, 0, st>>>(alpha, beta, kc, d_bounds);
 }
@@ -437,8 +521,7 @@ void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
 namespace sq3 {
 namespace {
 constexpr int kNoAllocSteps = 40;
-constexpr size_t kNoAllocWords =
-    (size_t)(kNoAllocSteps + 2) * SQ3_NOALLOC_MAX_NS + 2 * kNoAllocSteps + 8;
+constexpr size_t kNoAllocWords = lanczos_work_words(SQ3_NOALLOC_MAX_NS, kNoAllocSteps);
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 
 constexpr int kMaxDevices = 64;
@@ -476,7 +559,8 @@ extern "C" int sq3_lanczos_bounds_noalloc(const double* Hs, int Ns, double* boun
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int steps = Ns < kNoAllocSteps ? Ns : kNoAllocSteps;
   // every scratch word the kernels read is written earlier in the same call
-  // (the basis, the step counter, alpha and beta), so nothing is cleared here
+  // (the basis, the step counter, alpha, beta and each step's block partial
+  // sums), so nothing is cleared here
   lanczos_bounds_f64(nullptr, Hs, Ns, steps, bounds, scratch, st);
   if (cudaGetLastError() != cudaSuccess) return SQ3_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) {

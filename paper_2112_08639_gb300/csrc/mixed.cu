@@ -123,63 +123,58 @@ __global__ void split_rows_kernel(const float* __restrict__ src, long long lds, 
   }
 }
 
-// Same result for an FP32 source whose rows are a multiple of 4: a 64-row x
-// 64-column tile goes through shared memory; reads are 16-byte vectors along
-// the rows, and each thread writes 16 consecutive columns of one row as two
-// 16-byte vectors per piece (the column tail past `cols` element by element).
+// Same result for an FP32 source whose rows are a multiple of 4, transposed
+// in registers: a lane loads a 4-row x 4-column block (four 16-byte column
+// reads; two lanes cover a 32-byte sector) and writes, for each of its 4
+// rows, its 4 columns as one 8-byte vector per piece (16 lanes write 128
+// contiguous bytes of a row).  A warp covers 8 rows x 64 columns, a CTA 64
+// rows x 64 columns.  No shared memory: the shared-memory transpose issued
+// about 2.6 load/store instructions per element, this form one.
 __global__ void __launch_bounds__(256)
-split_rows_tile_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
-                       __nv_bfloat16* out, long long ld, long long ps) {
-  __shared__ float tile[64][65];
-  const long long r0 = (long long)blockIdx.x * 64;
-  const int c0 = blockIdx.y * 64;
-  const int t = threadIdx.x;
+split_rows_reg_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
+                      __nv_bfloat16* out, long long ld, long long ps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int vq = lane & 15, pq = lane >> 4;          // column quad, row quad
+  const long long r0 = (long long)blockIdx.x * 64 + warp * 8 + pq * 4;
+  const int c0 = blockIdx.y * 64 + vq * 4;
+  if (r0 >= rows || c0 >= cols) return;
+  float x[4][4];                                     // x[column][row]
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c0 + j < cols) v = *reinterpret_cast<const float4*>(src + r0 + (long long)(c0 + j) * lds);
+    x[j][0] = v.x;
+    x[j][1] = v.y;
+    x[j][2] = v.z;
+    x[j][3] = v.w;
+  }
+  const int nc = cols - c0;                          // columns of this lane (4 unless the tail)
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int rr = 4 * (t & 15), cc = (t >> 4) + 16 * i;
-    const long long r = r0 + rr;
-    const int c = c0 + cc;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < cols && r < rows) v = *reinterpret_cast<const float4*>(src + r + (long long)c * lds);
-    const int sw = ((cc >> 5) & 1) << 3;         // row swizzle (see the reads)
-    tile[cc][(rr ^ sw)] = v.x;
-    tile[cc][(rr ^ sw) + 1] = v.y;
-    tile[cc][(rr ^ sw) + 2] = v.z;
-    tile[cc][(rr ^ sw) + 3] = v.w;
-  }
-  __syncthreads();
-  // a warp covers 8 rows x 4 column groups; with the odd tile stride the
-  // groups g and g + 32 would share banks, which the row swizzle separates
-  const int rr = t >> 2, g = (t & 3) * 16;
-  const long long r = r0 + rr;
-  if (r >= rows) return;
-  const int c = c0 + g;
-  if (c >= cols) return;
-  __nv_bfloat16 h[3][16];
+    __nv_bfloat16 h[3][4];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float x = tile[g + k][rr ^ ((((g + k) >> 5) & 1) << 3)];
-    h[0][k] = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h[0][k]);
-    h[1][k] = __float2bfloat16_rn(r1);
-    h[2][k] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][k]));
-  }
-  __nv_bfloat16* o = out + r * ld + c;
-  if (c + 16 <= cols) {
+    for (int j = 0; j < 4; ++j) {
+      h[0][j] = __float2bfloat16_rn(x[j][i]);
+      const float r1 = x[j][i] - __bfloat162float(h[0][j]);
+      h[1][j] = __float2bfloat16_rn(r1);
+      h[2][j] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][j]));
+    }
+    __nv_bfloat16* o = out + (r0 + i) * ld + c0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      uint4 w[2];
-      __nv_bfloat16* wp = reinterpret_cast<__nv_bfloat16*>(w);
+      if (nc >= 4) {
+        uint2 w;
+        w.x = (uint32_t)__bfloat16_as_ushort(h[q][0]) |
+              ((uint32_t)__bfloat16_as_ushort(h[q][1]) << 16);
+        w.y = (uint32_t)__bfloat16_as_ushort(h[q][2]) |
+              ((uint32_t)__bfloat16_as_ushort(h[q][3]) << 16);
+        *reinterpret_cast<uint2*>(o + q * ps) = w;
+      } else {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) wp[k] = h[q][k];
-      uint4* d = reinterpret_cast<uint4*>(o + q * ps);
-      d[0] = w[0];
-      d[1] = w[1];
+        for (int j = 0; j < 4; ++j)
+          if (j < nc) o[q * ps + j] = h[q][j];
+      }
     }
-  } else {
-    for (int k = 0; k < cols - c; ++k)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) o[q * ps + k] = h[q][k];
   }
 }
 
@@ -298,8 +293,8 @@ static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBu
   if (N % 4 == 0 && b.ldS % 8 == 0 && MIXED_PIECES == 3) {
     // 16-byte column reads; rows of the pieces are 16-byte aligned (ldS % 8)
     dim3 grid((unsigned)((N + 63) / 64), (Ns + 63) / 64);
-    split_rows_tile_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
-                                                          N * b.ldS);
+    split_rows_reg_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
+                                                         N * b.ldS);
     return;
   }
   dim3 grid((unsigned)((N + 31) / 32), (Ns + 31) / 32);

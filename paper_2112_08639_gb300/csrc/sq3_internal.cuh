@@ -202,6 +202,14 @@ int rinv_from_lower_f32(const float* L, int n, bool dev, float* W, float* tmp, f
                          cudaStream_t st);
 void convert_f64_to_f32(const double* A, long long tot, float* B, cudaStream_t st);
 void mirror_upper_f64(double* A, int n, cudaStream_t st);
+// Words of Lanczos scratch for vectors of length n and `steps` (<= 64)
+// steps: the basis (steps + 1 vectors), w, alpha, beta, the step counter and
+// the per-block partial sums of one step (alpha over the n / 8 mat-vec
+// blocks; two passes of 64 projections and beta^2 over the n / 256 blocks).
+constexpr size_t lanczos_work_words(size_t n, size_t steps) {
+  return (steps + 2) * n + 2 * steps + 8 + (n * 32 + 255) / 256 +
+         ((n + 255) / 256) * (2 * 64 + 1);
+}
 void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st);
 
