@@ -219,7 +219,9 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   // moments and the terms of Ds above h follow from the product identity
   // T_h T_k = (T_{h+k} + T_{h-k}) / 2 (one more tensor-core product).
   const int h = mixed ? (npl + 1) / 2 : npl;
-  size_t need_T = mixed ? (size_t)(h + 2) * nn * sizeof(float)
+  // (mixed: then the block sums of the moment tail, 8-byte aligned)
+  const size_t tail_off = (((size_t)(h + 2) * nn * sizeof(float) + 7) / 8) * 8;
+  size_t need_T = mixed ? tail_off + moments_tail_part_words(npl, h) * sizeof(double)
                         : (size_t)(npl + 1) * nn * sizeof(double);
   int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
   if (rc) return rc;
@@ -248,8 +250,9 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
     rc = cheb_recurrence_mixed(ctx, Hs, Ns, h, bounds, mom, (float*)ctx->wsT);
     if (rc) return rc;
     {
-      Prof p(ctx, ST_CHEB_GEMM, npl > h ? 1 : 0);
-      rc = moments_tail_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, mom);
+      Prof p(ctx, ST_CHEB_GEMM, npl > h ? 2 : 0);
+      rc = moments_tail_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, mom,
+                              (double*)((char*)ctx->wsT + tail_off));
     }
     if (rc) return rc;
   } else {

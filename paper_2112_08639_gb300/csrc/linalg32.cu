@@ -159,12 +159,16 @@ potrf_dev_kernel(float* E, int n, int k0, int kb, int* status) {
       if (i > j) lsh[i] = v;
     }
     __syncthreads();
-    // trailing lower triangle: warp w takes columns c = j+1+w, j+1+w+nw, ..,
-    // its lanes the rows i >= c (no index division)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = j + 1 + warp; c < kb; c += nw) {
-      const float lc = lsh[c];
-      for (int i = c + lane; i < kb; i += 32) A[i][c] -= lsh[i] * lc;
+    // trailing lower triangle: thread (row r, column group cg) updates
+    // A[r][c] for c = j+1+cg, j+5+cg, .. <= r; the updates of a thread are
+    // independent (no chain of shared-memory round trips per column)
+    {
+      const int r = threadIdx.x & (NB - 1), cg = threadIdx.x / NB;
+      if (r > j && r < kb) {
+        const float lr = lsh[r];
+#pragma unroll 4
+        for (int c = j + 1 + cg; c <= r; c += 256 / NB) A[r][c] -= lr * lsh[c];
+      }
     }
     __syncthreads();
   }
@@ -352,14 +356,20 @@ __global__ void scaled_deviation_kernel(const double* __restrict__ S, int n,
 }
 
 // out = sum_ij (S_ij - delta_ij)^2 (one CTA)
+// |S - I|_F^2: block b sums the squares of the columns b, b + DN_BLOCKS, ..
+// into part[b]; deviation_norm_finish_kernel adds the DN_BLOCKS partial sums
+// in order (the result does not depend on the order in which blocks run).
+constexpr int DN_BLOCKS = 32;
 __global__ void __launch_bounds__(1024) deviation_norm_kernel(const double* __restrict__ S, int n,
-                                                              double* out) {
+                                                              double* part) {
   __shared__ double sh[32];
-  const long long tot = (long long)n * n;
   double acc = 0.0;
-  for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-    const double d = S[e] - ((e % n) == (e / n) ? 1.0 : 0.0);
-    acc += d * d;
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const double* col = S + (long long)j * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double d = col[i] - (i == j ? 1.0 : 0.0);
+      acc += d * d;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -367,8 +377,14 @@ __global__ void __launch_bounds__(1024) deviation_norm_kernel(const double* __re
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    *out = t;
+    part[blockIdx.x] = t;
   }
+}
+
+__global__ void deviation_norm_finish_kernel(const double* part, double* out) {
+  double t = 0.0;
+  for (int b = 0; b < DN_BLOCKS; ++b) t += part[b];
+  *out = t;
 }
 
 // R(i, :) *= dinv[i]
@@ -405,8 +421,9 @@ int scaled_deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, float
   return cuda_err(cudaGetLastError());
 }
 
-void deviation_norm_f64(const double* S, int n, double* out, cudaStream_t st) {
-  deviation_norm_kernel<<<1, 1024, 0, st>>>(S, n, out);
+void deviation_norm_f64(const double* S, int n, double* out, double* part, cudaStream_t st) {
+  deviation_norm_kernel<<<DN_BLOCKS, 1024, 0, st>>>(S, n, part);
+  deviation_norm_finish_kernel<<<1, 1, 0, st>>>(part, out);
 }
 
 void scale_rows_f32(float* R, int n, const float* dinv, cudaStream_t st) {

@@ -406,6 +406,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   float* tmp32 = R32 + nn;            // n * n / 2
   float* dinv32 = tmp32 + nn / 2 + 32;   // Ns: 1 / sqrt(S_ii)
   double* devnorm = ctx->dev_scal + 16;  // |S - I|_F^2 of the last pass
+  double* devpart = ctx->dev_scal + 24;  // its 32 block sums (slots 24 .. 55)
   bool shift_now = false, shifted = false, extra = false;
   int plain_left = 2;
   while (plain_left > 0) {
@@ -418,7 +419,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       {
         const int panels = (Ns + 63) / 64;
         Prof p(ctx, ST_CHOL, 3 * panels);
-        deviation_norm_f64(S, Ns, devnorm, ctx->stream);
+        deviation_norm_f64(S, Ns, devnorm, devpart, ctx->stream);
         cudaMemcpyAsync(ctx->host_scal + 16, devnorm, sizeof(double), cudaMemcpyDeviceToHost,
                         ctx->stream);
         rc = deviation_cholesky_f32(ctx, S, F32, Ns, ctx->stream);
@@ -566,45 +567,80 @@ int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int h,
 
 // m_{h+k} = tr(T_{h+k}) = 2 tr(T_h T_k) - m_{h-k} for k = 1 .. npl - h, by
 // the product identity T_h T_k = (T_{h+k} + T_{h-k}) / 2; T_h and T_k are
-// symmetric, so tr(T_h T_k) = sum_e T_h[e] T_k[e].  One CTA per k.
-__global__ void __launch_bounds__(1024)
-moments_tail_kernel(const float* __restrict__ T, long long nn, int h, double* mom) {
-  __shared__ double sh[32];
+// symmetric, so tr(T_h T_k) = sum_e T_h[e] T_k[e].  Block (k, s) sums the
+// s-th of MT_SPLITS slices of the elements into part[(k-1) MT_SPLITS + s];
+// moments_tail_finish_kernel adds the slices in order.
+constexpr int MT_SPLITS = 16;
+__global__ void __launch_bounds__(256)
+moments_tail_kernel(const float* __restrict__ T, long long nn, int h, double* part) {
+  __shared__ double sh[8];
   const int k = blockIdx.x + 1;
   const float* Th = T + (long long)h * nn;
   const float* Tk = T + (long long)k * nn;
+  const long long chunk = (nn + MT_SPLITS - 1) / MT_SPLITS;
+  const long long e0 = blockIdx.y * chunk;
+  const long long e1 = e0 + chunk < nn ? e0 + chunk : nn;
   double s = 0.0;
-  for (long long e = threadIdx.x; e < nn; e += blockDim.x) s += (double)Th[e] * (double)Tk[e];
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+    s += (double)Th[e] * (double)Tk[e];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    part[(long long)(k - 1) * MT_SPLITS + blockIdx.y] = t;
+  }
+}
+
+__global__ void moments_tail_finish_kernel(const double* part, int h, int K, double* mom) {
+  for (int k = 1 + blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int s = 0; s < MT_SPLITS; ++s) t += part[(long long)(k - 1) * MT_SPLITS + s];
     mom[h + k] = 2.0 * t - mom[h - k];
   }
 }
 
-int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom) {
+size_t moments_tail_part_words(int npl, int h) {
+  return npl > h ? (size_t)(npl - h) * MT_SPLITS : 0;
+}
+
+int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom,
+                       double* part) {
   if (npl <= h) return SQ3_OK;
-  moments_tail_kernel<<<npl - h, 1024, 0, ctx->stream>>>(T, (long long)Ns * Ns, h, mom);
+  const int K = npl - h;
+  moments_tail_kernel<<<dim3(K, MT_SPLITS), 256, 0, ctx->stream>>>(T, (long long)Ns * Ns, h,
+                                                                   part);
+  moments_tail_finish_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(part, h, K, mom);
   return cuda_err(cudaGetLastError());
 }
 
 // D = sum'_{j<=h} c_j T_j - sum_{k=1}^{npl-h} c_{h+k} T_{h-k} (FP64) and
-// A2 = 2 sum_{k=1}^{npl-h} c_{h+k} T_k (FP32), so that Ds = D + T_h A2.
-__global__ void d_split_kernel(const float* __restrict__ T, long long nn, int Ns, int npl,
-                               int h, const double* __restrict__ coef, double* D,
-                               float* A2) {
+// A2 = 2 sum_{k=1}^{npl-h} c_{h+k} T_k (FP32), so that Ds = D + T_h A2.  The
+// two sums over T_0 .. T_h are folded into one weight per T_t,
+// w_t = c_t - c_{2h-t} [h - t <= npl - h] (w_0 with c_0 / 2; T_0 = I is
+// stored), so each T_t is read once: h + 1 loads and at most 2 h + 1 FP64
+// FMAs per element.
+__global__ void __launch_bounds__(256)
+d_split_kernel(const float* __restrict__ T, long long nn, int npl, int h,
+               const double* __restrict__ coef, double* D, float* A2) {
+  __shared__ double w[SQ3_MAX_NPL + 1];
+  __shared__ double ca[SQ3_MAX_NPL + 1];
+  const int K = npl - h;
+  for (int t = threadIdx.x; t <= h; t += blockDim.x) {
+    double v = (t == 0 ? 0.5 : 1.0) * coef[t];
+    if (t < h && h - t <= K) v -= coef[2 * h - t];
+    w[t] = v;
+    ca[t] = (t >= 1 && t <= K) ? coef[h + t] : 0.0;
+  }
+  __syncthreads();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= nn) return;
-  const int i = (int)(e % Ns), j = (int)(e / Ns);
-  double d = (i == j) ? 0.5 * coef[0] : 0.0;
-  for (int t = 1; t <= h; ++t) d += coef[t] * (double)T[(long long)t * nn + e];
-  double a = 0.0;
-  for (int k = 1; k <= npl - h; ++k) {
-    d -= coef[h + k] * (double)T[(long long)(h - k) * nn + e];
-    a += coef[h + k] * (double)T[(long long)k * nn + e];
+  double d = 0.0, a = 0.0;
+  for (int t = 0; t <= h; ++t) {
+    const double x = (double)T[(long long)t * nn + e];
+    d += w[t] * x;
+    if (t >= 1 && t <= K) a += ca[t] * x;
   }
   D[e] = d;
   A2[e] = (float)(2.0 * a);
@@ -621,7 +657,7 @@ int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
   {
     Prof p(ctx, ST_D_ACCUM);
     d_split_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(
-        T, nn, Ns, npl, h, coef, D, A2);
+        T, nn, npl, h, coef, D, A2);
   }
   if (npl <= h) return cuda_err(cudaGetLastError());
   split_matrix<float>(ctx, T + (long long)h * nn, Ns, b.matA, b);   // T_h

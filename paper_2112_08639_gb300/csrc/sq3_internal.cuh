@@ -192,7 +192,8 @@ int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaS
 int scaled_deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, float* dinv, int n,
                                   cudaStream_t st);
 // *out = |S - I|_F^2 (S FP64 column-major n x n)
-void deviation_norm_f64(const double* S, int n, double* out, cudaStream_t st);
+// |S - I|_F^2 into *out; part: 32 doubles of device scratch (block sums)
+void deviation_norm_f64(const double* S, int n, double* out, double* part, cudaStream_t st);
 // R(i, :) *= dinv[i] (column-major n x n)
 void scale_rows_f32(float* R, int n, const float* dinv, cudaStream_t st);
 // Rinv = L^{-T} (upper, column-major FP32) of the lower-triangular L, or of
@@ -224,7 +225,10 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns);
 int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs);
 int cheb_recurrence_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int h,
                           const double* bounds, double* mom, float* T);
-int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom);
+// part: moments_tail_part_words(npl, h) doubles of device scratch
+size_t moments_tail_part_words(int npl, int h);
+int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, double* mom,
+                       double* part);
 int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
                        const double* coef, double* D, float* A2);
 int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns,
