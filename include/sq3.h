@@ -114,6 +114,21 @@ int sq3_hamiltonian_apply(sq3_ctx* ctx, const void* X, void* Y, int Ns,
 int sq3_cheb_filter(sq3_ctx* ctx, void* X, int Ns, int degree,
                     double a, double b, double a0, sq3_prec prec);
 
+/* The Chebyshev filter of sq3_cheb_filter for a block held in host memory:
+ * X_host (N x Ns column-major, element type of prec, read only) is copied to
+ * the device block X (same layout, overwritten) in two chunks of whole
+ * vectors (the first ceil(Ns/8), then the rest) on a stream of the context's
+ * own, and each chunk is filtered on the context's stream as soon as its
+ * copy has landed, so the copy of the second chunk overlaps the filtering
+ * of the first (the filter
+ * acts on every vector separately; the paper has no counterpart, it
+ * concerns only where the block lives).  On return X holds p_m(H) X_host
+ * and no copy is in flight.  X_host should be page-locked for the copies to
+ * overlap; pageable memory gives the same result without the overlap.
+ * Parameters and errors as sq3_cheb_filter (SQ3_ECUDA if a copy fails). */
+int sq3_cheb_filter_from_host(sq3_ctx* ctx, const void* X_host, void* X, int Ns,
+                              int degree, double a, double b, double a0, sq3_prec prec);
+
 /* Orthonormalise X in place by Cholesky QR: S = X^T X = R^T R (R upper
  * triangular, FP64 Cholesky on the device), X <- X R^{-1} (Sec. 4: "followed
  * by orthonormalization"; the method is this library's reading).  In

@@ -387,6 +387,9 @@ void sq3_destroy(sq3_ctx* c) {
   free_projectors(c->proj);
   for (auto& r : c->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  for (auto e : c->upload_ev) if (e) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
                   c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -605,6 +608,59 @@ int sq3_cheb_filter(sq3_ctx* c, void* X, int Ns, int degree, double a,
   if (prec == SQ3_FP64) rc = cheb_filter_t<double>(c, (double*)X, Ns, degree, a, b, a0);
   else if (prec == SQ3_MIXED) rc = cheb_filter_t<float>(c, (float*)X, Ns, degree, a, b, a0);
   else return SQ3_EINVAL;
+  return finish(c, rc);
+}
+
+int sq3_cheb_filter_from_host(sq3_ctx* c, const void* X_host, void* X, int Ns, int degree,
+                              double a, double b, double a0, sq3_prec prec) {
+  if (!ready(c)) return SQ3_ENOTSETUP;
+  if (!X_host || !X || Ns <= 0 || Ns > 65535 || degree < 1 || !(a0 < a) || !(a < b))
+    return SQ3_EINVAL;
+  if (prec != SQ3_FP64 && prec != SQ3_MIXED) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  if (!c->copy_stream) {
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->copy_stream = nullptr;
+      cudaGetLastError();
+      return SQ3_ECUDA;
+    }
+    for (auto& e : c->upload_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        e = nullptr;
+        cudaGetLastError();
+        return SQ3_ECUDA;
+      }
+  }
+  // every vector is filtered on its own (the filter is p_m(H) applied column
+  // by column), so a chunk of the vectors is filtered as soon as its upload
+  // has landed while the rest is still being copied.  Two chunks: the first
+  // eighth of the vectors, whose filtering (m stencil and nonlocal steps)
+  // outlasts the copy of the other seven eighths, then those in one piece,
+  // which keeps the filter's launches as large as possible (a nonlocal pass
+  // over few vectors stages its brick tables for fewer vector groups).
+  const size_t es = prec == SQ3_FP64 ? sizeof(double) : sizeof(float);
+  const size_t vbytes = (size_t)c->grid.N * es;
+  const int cut = (Ns + 7) / 8;
+  const int v0s[SQ3_UPLOAD_CHUNKS] = {0, cut};
+  const int nvs[SQ3_UPLOAD_CHUNKS] = {cut, Ns - cut};
+  int rc = SQ3_OK;
+  for (int k = 0; k < SQ3_UPLOAD_CHUNKS && nvs[k] > 0 && rc == SQ3_OK; ++k) {
+    const int v0 = v0s[k], nv = nvs[k];
+    rc = cuda_err(cudaMemcpyAsync((char*)X + v0 * vbytes, (const char*)X_host + v0 * vbytes,
+                                  nv * vbytes, cudaMemcpyHostToDevice, c->copy_stream));
+    if (rc == SQ3_OK) rc = cuda_err(cudaEventRecord(c->upload_ev[k], c->copy_stream));
+  }
+  for (int k = 0; k < SQ3_UPLOAD_CHUNKS && nvs[k] > 0 && rc == SQ3_OK; ++k) {
+    const int v0 = v0s[k], nv = nvs[k];
+    rc = cuda_err(cudaStreamWaitEvent(c->stream, c->upload_ev[k], 0));
+    if (rc) break;
+    if (prec == SQ3_FP64)
+      rc = cheb_filter_t<double>(c, (double*)X + (size_t)v0 * c->grid.N, nv, degree, a, b, a0);
+    else
+      rc = cheb_filter_t<float>(c, (float*)X + (size_t)v0 * c->grid.N, nv, degree, a, b, a0);
+  }
+  // no copy of this call is left in flight when it returns
+  if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess && rc == SQ3_OK) rc = SQ3_ECUDA;
   return finish(c, rc);
 }
 

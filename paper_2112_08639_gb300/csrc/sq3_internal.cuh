@@ -17,6 +17,8 @@
 #define MIXED_PIECES 3
 // largest Ns accepted by sq3_lanczos_bounds_noalloc (static scratch size)
 #define SQ3_NOALLOC_MAX_NS 8192
+// chunks of vectors a host block is uploaded in (sq3_cheb_filter_from_host)
+#define SQ3_UPLOAD_CHUNKS 2
 // nonlocal pass: points per CTA (an 8 x 8 x NL_BZ brick)
 #define NL_BZ 4
 #define NL_BRICK_PTS (64 * NL_BZ)
@@ -110,6 +112,10 @@ struct sq3_ctx {
   void* wsSplit = nullptr; size_t wsSplit_bytes = 0;  // bf16 split operands
   double* wsFoe = nullptr; size_t wsFoe_bytes = 0;    // quadrature node values
   float* wsLin32 = nullptr; size_t wsLin32_bytes = 0;  // FP32 factor, inverse, temporaries
+  // uploads of a host block (sq3_cheb_filter_from_host): a stream of their
+  // own and one event per chunk, created on first use
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t upload_ev[SQ3_UPLOAD_CHUNKS] = {};
 };
 
 namespace sq3 {

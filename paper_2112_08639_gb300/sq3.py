@@ -39,6 +39,7 @@ _sigs = {
     "sq3_set_projectors": (_i, [_p, _i, _p, _p, _p, _p]),
     "sq3_hamiltonian_apply": (_i, [_p, _p, _p, _i, _i]),
     "sq3_cheb_filter": (_i, [_p, _p, _i, _i, _d, _d, _d, _i]),
+    "sq3_cheb_filter_from_host": (_i, [_p, _p, _p, _i, _i, _d, _d, _d, _i]),
     "sq3_orthonormalise": (_i, [_p, _p, _i, _i]),
     "sq3_project": (_i, [_p, _p, _i, _i, _p]),
     "sq3_kernel_from_hs": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p]),
@@ -157,6 +158,19 @@ class Context:
     def cheb_filter(self, X: torch.Tensor, degree: int, a: float, b: float, a0: float, prec=FP64):
         _check(lib.sq3_cheb_filter(self._h, _ptr(X), X.shape[0], degree, a, b, a0, prec),
                "sq3_cheb_filter")
+        return X
+
+    def cheb_filter_from_host(self, X_host: torch.Tensor, X: torch.Tensor, degree: int, a: float,
+                              b: float, a0: float, prec=FP64):
+        """Filter the host block X_host into the device block X (same shape
+        and dtype); the upload overlaps the filtering of earlier chunks."""
+        if X_host.is_cuda or not X.is_cuda or X_host.shape != X.shape or X_host.dtype != X.dtype:
+            raise ValueError("X_host: host tensor, X: device tensor of the same shape and dtype")
+        if not (X_host.is_contiguous() and X.is_contiguous()):
+            raise ValueError("contiguous blocks expected")
+        _check(lib.sq3_cheb_filter_from_host(self._h, ctypes.c_void_p(X_host.data_ptr()), _ptr(X),
+                                             X.shape[0], degree, a, b, a0, prec),
+               "sq3_cheb_filter_from_host")
         return X
 
     def orthonormalise(self, X: torch.Tensor, prec=FP64):
