@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--config", default="al108_72")
     p.add_argument("--impl", default="sq3", choices=["sq3", "reference"])
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-clocks", action="store_true")
     return p.parse_args()
 
@@ -207,14 +207,19 @@ def run_sq3(args, rank, world):
     Xh = X.cpu().pin_memory()
     Vh = V.cpu().pin_memory()
     rho_h = torch.empty(cfg.N, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+
+    def e2e_step():
         V.copy_(Vh, non_blocking=True)
         ctx.set_potential(V)
         step(X, Xh)
         rho_h.copy_(rho, non_blocking=True)
         torch.cuda.synchronize()
+
+    e2e_step()          # untimed: first use of the host buffers and the copy stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     h2d = Xh.numel() * Xh.element_size() + Vh.numel() * 8
     d2h = cfg.N * 8 + 6 * 8

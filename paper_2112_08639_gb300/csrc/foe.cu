@@ -76,20 +76,36 @@ __device__ double bsum(double v, double* sh) {
   return s;
 }
 
-// One CTA: moment-weighted node sums w_k = sum'_j m_j T_j(x_k), bisection for
-// mu on 2 (2/M) sum_k g(xi x_k + chi; mu) w_k = Ne, then the three functions
-// at the nodes for the coefficient kernel.
-// out[0] = mu, out[3] = chi, out[4] = xi; fvals[0..3M) = g, eps g, entropy.
+// The Fermi level by multisection on the electron count of Eq.
+// (FermiLevelCalc), N(mu) = 2 (2/M) sum_k g(xi x_k + chi; mu) w_k with the
+// moment-weighted node sums w_k = sum'_j m_j T_j(x_k).  fermi_prep_kernel
+// (one CTA) forms x_k and w_k, checks the moments and the initial bracket;
+// each round fermi_count_kernel evaluates N at FL_POINTS interior points of
+// the bracket, one block per point, and fermi_bracket_kernel keeps the
+// sub-interval where N crosses Ne (the bracket shrinks FL_POINTS + 1 fold
+// per round; rounds stop once it no longer shrinks).  fermi_values_kernel
+// then writes mu and the three functions at the nodes.  Every count is one
+// block's sum in a fixed order, so mu does not depend on scheduling.
+// fl[0..M) = w_k, fl[M..2M) = x_k, fl[2M] = lo, fl[2M+1] = hi,
+// fl[2M+2] = done flag, fl[2M+3 ..] = the round's counts.
+constexpr int FL_POINTS = 63;
+constexpr int FL_ROUNDS = 12;
+
+__device__ double fermi_count(const double* fl, int M, double chi, double xi, double mu,
+                              double sigma, double* sh) {
+  const double* wq = fl;
+  const double* xk = fl + M;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x)
+    s += fermi_dev(xi * xk[k] + chi, mu, sigma) * wq[k];
+  return 2.0 * (2.0 / M) * bsum(s, sh);
+}
+
 __global__ void __launch_bounds__(1024)
-fermi_level_kernel(const double* __restrict__ moments, int npl, int M, double sigma,
-                   double Ne, int n, const double* bounds, double* fvals, double* out,
-                   int* status) {
-  extern __shared__ double smem[];
-  double* wq = smem;            // M : w_k
-  double* xk = smem + M;        // M : nodes cos(theta_k)
+fermi_prep_kernel(const double* __restrict__ moments, int npl, int M, double sigma, double Ne,
+                  int n, const double* bounds, double* fl, int* status) {
   __shared__ double sh[32];
   const double chi = bounds[0], xi = bounds[1];
-
   // moment sanity: |tr T_j| <= n unless the spectrum left [-1, 1]
   for (int j = threadIdx.x; j <= npl; j += blockDim.x) {
     const double mj = moments[j];
@@ -98,7 +114,7 @@ fermi_level_kernel(const double* __restrict__ moments, int npl, int M, double si
   }
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     const double x = cospi((2.0 * k + 1.0) / (2.0 * M));
-    xk[k] = x;
+    fl[M + k] = x;
     double tp = 1.0, t = x;                  // T_0, T_1 at x
     double acc = 0.5 * moments[0] + (npl >= 1 ? moments[1] * x : 0.0);
     for (int j = 2; j <= npl; ++j) {
@@ -106,37 +122,60 @@ fermi_level_kernel(const double* __restrict__ moments, int npl, int M, double si
       tp = t; t = tn;
       acc += moments[j] * t;
     }
-    wq[k] = acc;
+    fl[k] = acc;
   }
   __syncthreads();
-
-  auto count = [&](double mu) {
-    double s = 0.0;
-    for (int k = threadIdx.x; k < M; k += blockDim.x)
-      s += fermi_dev(xi * xk[k] + chi, mu, sigma) * wq[k];
-    return 2.0 * (2.0 / M) * bsum(s, sh);
-  };
-
-  double lo = chi - xi - 40.0 * sigma, hi = chi + xi + 40.0 * sigma;
-  const double clo = count(lo), chi_ = count(hi);
-  if (!(clo < Ne && chi_ > Ne)) {
-    if (threadIdx.x == 0) atomicCAS(status, 0, DEV_NOCONV);
+  const double lo = chi - xi - 40.0 * sigma, hi = chi + xi + 40.0 * sigma;
+  const double clo = fermi_count(fl, M, chi, xi, lo, sigma, sh);
+  const double chi_ = fermi_count(fl, M, chi, xi, hi, sigma, sh);
+  if (threadIdx.x == 0) {
+    if (!(clo < Ne && chi_ > Ne)) atomicCAS(status, 0, DEV_NOCONV);
+    fl[2 * M] = lo;
+    fl[2 * M + 1] = hi;
+    fl[2 * M + 2] = 0.0;
   }
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    const double cm = count(mid);
-    if (cm < Ne) lo = mid; else hi = mid;
+}
+
+__global__ void __launch_bounds__(256)
+fermi_count_kernel(int M, double sigma, const double* bounds, double* fl) {
+  __shared__ double sh[32];
+  if (fl[2 * M + 2] != 0.0) return;          // converged in an earlier round
+  const double lo = fl[2 * M], hi = fl[2 * M + 1];
+  const double mu = lo + (hi - lo) * (blockIdx.x + 1) / (FL_POINTS + 1.0);
+  const double c = fermi_count(fl, M, bounds[0], bounds[1], mu, sigma, sh);
+  if (threadIdx.x == 0) fl[2 * M + 3 + blockIdx.x] = c;
+}
+
+__global__ void fermi_bracket_kernel(int M, double Ne, double* fl) {
+  if (fl[2 * M + 2] != 0.0) return;
+  const double lo = fl[2 * M], hi = fl[2 * M + 1];
+  int first = FL_POINTS;                      // first point with N >= Ne
+  for (int b = 0; b < FL_POINTS; ++b)
+    if (fl[2 * M + 3 + b] >= Ne) { first = b; break; }
+  const double nlo = first == 0 ? lo : lo + (hi - lo) * first / (FL_POINTS + 1.0);
+  const double nhi = first == FL_POINTS ? hi : lo + (hi - lo) * (first + 1) / (FL_POINTS + 1.0);
+  if (!(nhi - nlo < hi - lo) || !(nlo < nhi)) {
+    fl[2 * M + 2] = 1.0;                      // no longer shrinks
+    return;
   }
-  const double mu = 0.5 * (lo + hi);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    const double eps = xi * xk[k] + chi;
+  fl[2 * M] = nlo;
+  fl[2 * M + 1] = nhi;
+}
+
+// out[0] = mu, out[3] = chi, out[4] = xi; fvals[0..3M) = g, eps g, entropy.
+__global__ void __launch_bounds__(256)
+fermi_values_kernel(int M, double sigma, const double* bounds, const double* fl,
+                    double* fvals, double* out, int* status) {
+  const double chi = bounds[0], xi = bounds[1];
+  const double mu = 0.5 * (fl[2 * M] + fl[2 * M + 1]);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const double eps = xi * fl[M + k] + chi;
     const double g = fermi_dev(eps, mu, sigma);
     fvals[k] = g;
     fvals[M + k] = eps * g;
     fvals[2 * M + k] = entropy_dev(eps, mu, sigma);
   }
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     out[0] = mu;
     out[3] = chi;
     out[4] = xi;
@@ -279,18 +318,21 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   }
   const int M = (8 * (npl + 1) > 1024) ? 8 * (npl + 1) : 1024;
   rc = ensure((void**)&ctx->wsFoe, &ctx->wsFoe_bytes,
-              ((size_t)3 * M + 3 * (npl + 1)) * sizeof(double));
+              ((size_t)5 * M + 3 * (npl + 1) + 3 + FL_POINTS) * sizeof(double));
   if (rc) return rc;
   double* fvals = ctx->wsFoe;
   double* terms = fvals + 3 * M;
-  size_t smem = (size_t)2 * M * sizeof(double);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(fermi_level_kernel,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  double* fl = terms + 3 * (npl + 1);
   {
-    Prof p(ctx, ST_FERMI, 3);
-    fermi_level_kernel<<<1, 1024, smem, st>>>(mom, npl, M, sigma, Ne, Ns, bounds,
-                                              fvals, outd, ctx->dev_status);
+    Prof p(ctx, ST_FERMI, 4 + 2 * FL_ROUNDS);
+    fermi_prep_kernel<<<1, 1024, 0, st>>>(mom, npl, M, sigma, Ne, Ns, bounds, fl,
+                                          ctx->dev_status);
+    for (int r = 0; r < FL_ROUNDS; ++r) {
+      fermi_count_kernel<<<FL_POINTS, 256, 0, st>>>(M, sigma, bounds, fl);
+      fermi_bracket_kernel<<<1, 1, 0, st>>>(M, Ne, fl);
+    }
+    fermi_values_kernel<<<(M + 255) / 256, 256, 0, st>>>(M, sigma, bounds, fl, fvals, outd,
+                                                         ctx->dev_status);
     cheb_coeff_kernel<<<(npl + 1 + 7) / 8, 256, 0, st>>>(fvals, mom, npl, M, coef,
                                                          terms);
     fermi_finish_kernel<<<1, 32, 0, st>>>(terms, npl, sigma, outd, ctx->dev_status);

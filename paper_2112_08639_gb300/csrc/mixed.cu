@@ -128,8 +128,9 @@ __global__ void split_rows_kernel(const float* __restrict__ src, long long lds, 
 // reads; two lanes cover a 32-byte sector) and writes, for each of its 4
 // rows, its 4 columns as one 8-byte vector per piece (16 lanes write 128
 // contiguous bytes of a row).  A warp covers 8 rows x 64 columns, a CTA 64
-// rows x 64 columns.  No shared memory: the shared-memory transpose issued
-// about 2.6 load/store instructions per element, this form one.
+// rows x 64 columns (128-row CTAs were measured slower).  No shared memory:
+// the shared-memory transpose issued about 2.6 load/store instructions per
+// element, this form one.
 __global__ void __launch_bounds__(256)
 split_rows_reg_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
                       __nv_bfloat16* out, long long ld, long long ps) {
