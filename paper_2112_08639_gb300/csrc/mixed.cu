@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <utility>
+
 #include "sq3_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -88,12 +90,16 @@ __global__ void split_cols_f32x4_kernel(const float* __restrict__ src, long long
       h[1][i] = __float2bfloat16_rn(r1);
       h[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][i]));
     }
-    for (int q = 0; q < pieces; ++q) {
-      __nv_bfloat162 lo = __halves2bfloat162(h[q][0], h[q][1]);
-      __nv_bfloat162 hi = __halves2bfloat162(h[q][2], h[q][3]);
+    // unrolled over the three pieces (a loop bounded by `pieces` alone would
+    // index h dynamically and put it in local memory)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q >= pieces) break;
       uint2 pk;
-      pk.x = *reinterpret_cast<unsigned*>(&lo);
-      pk.y = *reinterpret_cast<unsigned*>(&hi);
+      pk.x = (uint32_t)__bfloat16_as_ushort(h[q][0]) |
+             ((uint32_t)__bfloat16_as_ushort(h[q][1]) << 16);
+      pk.y = (uint32_t)__bfloat16_as_ushort(h[q][2]) |
+             ((uint32_t)__bfloat16_as_ushort(h[q][3]) << 16);
       *reinterpret_cast<uint2*>(out + e + q * ps) = pk;
     }
   } else {
@@ -227,6 +233,7 @@ struct MixedBuffers {
   __nv_bfloat16* colX;   // X as K-major over the grid: rows = vectors
   __nv_bfloat16* colY;   // second block (H X) in the same layout
   __nv_bfloat16* rowX;   // X as K-major over vectors: rows = grid points
+  __nv_bfloat16* rowX2;  // a second one (written by X R^-1 for the next pass)
   __nv_bfloat16* matA;   // Ns x Ns operands
   __nv_bfloat16* matB;
   __nv_bfloat16* matC;
@@ -240,13 +247,14 @@ static int mixed_buffers(sq3_ctx* ctx, int Ns, MixedBuffers* b) {
   b->psN = (long long)Ns * b->ldN;          // colX: Ns rows of ldN
   const long long psR = N * b->ldS;         // rowX: N rows of ldS
   b->psS = (long long)Ns * b->ldS;
-  const size_t need = (size_t)MIXED_PIECES * (2 * b->psN + psR + 3 * b->psS) * 2 + 4096;
+  const size_t need = (size_t)MIXED_PIECES * (2 * b->psN + 2 * psR + 3 * b->psS) * 2 + 4096;
   int rc = ensure(&ctx->wsSplit, &ctx->wsSplit_bytes, need);
   if (rc) return rc;
   __nv_bfloat16* p = (__nv_bfloat16*)ctx->wsSplit;
   b->colX = p; p += MIXED_PIECES * b->psN;
   b->colY = p; p += MIXED_PIECES * b->psN;
   b->rowX = p; p += MIXED_PIECES * psR;
+  b->rowX2 = p; p += MIXED_PIECES * psR;
   b->matA = p; p += MIXED_PIECES * b->psS;
   b->matB = p; p += MIXED_PIECES * b->psS;
   b->matC = p;
@@ -288,18 +296,20 @@ static void split_block_cols(sq3_ctx* ctx, const float* X, int Ns, __nv_bfloat16
   }
 }
 
-static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBuffers& b) {
+static void split_block_rows(sq3_ctx* ctx, const float* X, int Ns, const MixedBuffers& b,
+                             __nv_bfloat16* out = nullptr) {
   Prof p(ctx, ST_SPLIT);
   const long long N = ctx->grid.N;
+  if (!out) out = b.rowX;
   if (N % 4 == 0 && b.ldS % 8 == 0 && MIXED_PIECES == 3) {
     // 16-byte column reads; rows of the pieces are 16-byte aligned (ldS % 8)
     dim3 grid((unsigned)((N + 63) / 64), (Ns + 63) / 64);
-    split_rows_reg_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
+    split_rows_reg_kernel<<<grid, 256, 0, ctx->stream>>>(X, N, (int)N, Ns, out, b.ldS,
                                                          N * b.ldS);
     return;
   }
   dim3 grid((unsigned)((N + 31) / 32), (Ns + 31) / 32);
-  split_rows_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, N, (int)N, Ns, b.rowX, b.ldS,
+  split_rows_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, N, (int)N, Ns, out, b.ldS,
                                                            N * b.ldS, MIXED_PIECES);
 }
 
@@ -314,8 +324,9 @@ static void split_matrix(sq3_ctx* ctx, const T* A, int Ns, __nv_bfloat16* out,
 static Operand op_cols(const __nv_bfloat16* base, int Ns, long long N, const MixedBuffers& b) {
   return Operand{base, Ns, (int)N, b.ldN, b.psN, MIXED_PIECES};
 }
-static Operand op_rows(const MixedBuffers& b, long long N, int Ns) {
-  return Operand{b.rowX, (int)N, Ns, b.ldS, N * b.ldS, MIXED_PIECES};
+static Operand op_rows(const MixedBuffers& b, long long N, int Ns,
+                       const __nv_bfloat16* base = nullptr) {
+  return Operand{base ? base : b.rowX, (int)N, Ns, b.ldS, N * b.ldS, MIXED_PIECES};
 }
 static Operand op_mat(const __nv_bfloat16* base, int Ns, const MixedBuffers& b) {
   return Operand{base, Ns, Ns, b.ldS, b.psS, MIXED_PIECES};
@@ -410,8 +421,13 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   double* devpart = ctx->dev_scal + 24;  // its 32 block sums (slots 24 .. 55)
   bool shift_now = false, shifted = false, extra = false;
   int plain_left = 2;
+  // the pieces of X for the next pass, written by the X R^-1 product of the
+  // pass before (colX for the Gram, rows for the next X R^-1)
+  bool have_pieces = false;
+  __nv_bfloat16* rowA = b.rowX;       // rows of the current X
+  __nv_bfloat16* rowB = b.rowX2;      // rows of the next X
   while (plain_left > 0) {
-    split_block_cols(ctx, X, Ns, b.colX, b);
+    if (!have_pieces) split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
     if (rc) return rc;
     const bool last = plain_left == 1 && !shift_now;
@@ -472,7 +488,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       rc = check_device_status(ctx);
       if (rc == SQ3_ENOTPD && !shifted && !last) {
         shifted = shift_now = true;
-        continue;
+        continue;                        // X unchanged: its pieces stay valid
       }
       if (rc) return rc;
       if (last) {
@@ -488,7 +504,9 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     }
     if (have_r32) split_matrix<float>(ctx, R32, Ns, b.matA, b);
     else split_matrix<double>(ctx, Rinv, Ns, b.matA, b);
-    split_block_rows(ctx, X, Ns, b);
+    if (!have_pieces) split_block_rows(ctx, X, Ns, b, rowA);
+    // another pass follows this one: its inputs' pieces come from this product
+    const bool follows = shift_now || again || plain_left > 1;
     {
       // the product reads X only through its pieces, so it overwrites X
       Prof p(ctx, ST_XRINV);
@@ -497,10 +515,20 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       t.C32 = X;
       t.ldc = N;
       t.alpha = 1.f;
-      rc = tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
-                   EPI_TC_STORE, 1, ctx->stream);
+      if (follows) {
+        t.colP = b.colX;
+        t.col_ld = b.ldN;
+        t.col_ps = b.psN;
+        t.rowP = rowB;
+        t.row_ld = b.ldS;
+        t.row_ps = N * b.ldS;
+      }
+      rc = tc_gemm(ctx, op_rows(b, N, Ns, rowA), op_mat(b.matA, Ns, b), products(MIXED_PIECES),
+                   t, EPI_TC_STORE, 1, ctx->stream);
     }
     if (rc) return rc;
+    have_pieces = follows;
+    if (follows) std::swap(rowA, rowB);
     if (shift_now) shift_now = false;
     else if (again) extra = true;       // the last pass once more
     else --plain_left;
@@ -581,9 +609,17 @@ moments_tail_kernel(const float* __restrict__ T, long long nn, int h, double* pa
   const long long chunk = (nn + MT_SPLITS - 1) / MT_SPLITS;
   const long long e0 = blockIdx.y * chunk;
   const long long e1 = e0 + chunk < nn ? e0 + chunk : nn;
+  // FP32 products of the FP32 matrices in runs of 16 (FMA), each run folded
+  // into the FP64 sum: GB300 issues few FP64 FMAs per SM, and the entries
+  // are FP32 already
   double s = 0.0;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-    s += (double)Th[e] * (double)Tk[e];
+  long long e = e0 + threadIdx.x;
+  while (e < e1) {
+    float r = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < 16 && e < e1; ++i, e += blockDim.x) r = fmaf(Th[e], Tk[e], r);
+    s += (double)r;
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -616,32 +652,43 @@ int moments_tail_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h, dou
   return cuda_err(cudaGetLastError());
 }
 
-// D = sum'_{j<=h} c_j T_j - sum_{k=1}^{npl-h} c_{h+k} T_{h-k} (FP64) and
+// D = sum'_{j<=h} c_j T_j - sum_{k=1}^{npl-h} c_{h+k} T_{h-k} and
 // A2 = 2 sum_{k=1}^{npl-h} c_{h+k} T_k (FP32), so that Ds = D + T_h A2.  The
 // two sums over T_0 .. T_h are folded into one weight per T_t,
 // w_t = c_t - c_{2h-t} [h - t <= npl - h] (w_0 with c_0 / 2; T_0 = I is
-// stored), so each T_t is read once: h + 1 loads and at most 2 h + 1 FP64
-// FMAs per element.
+// stored), so each T_t is read once.  The terms are FP32 products of the
+// FP32 T_t (weights rounded to FP32) summed in runs of 8 and each run
+// folded into an FP64 sum: GB300 issues few FP64 FMAs per SM, and the T_t
+// carry FP32 accuracy already.
 __global__ void __launch_bounds__(256)
 d_split_kernel(const float* __restrict__ T, long long nn, int npl, int h,
                const double* __restrict__ coef, double* D, float* A2) {
-  __shared__ double w[SQ3_MAX_NPL + 1];
-  __shared__ double ca[SQ3_MAX_NPL + 1];
+  __shared__ float w[SQ3_MAX_NPL + 1];
+  __shared__ float ca[SQ3_MAX_NPL + 1];
   const int K = npl - h;
   for (int t = threadIdx.x; t <= h; t += blockDim.x) {
     double v = (t == 0 ? 0.5 : 1.0) * coef[t];
     if (t < h && h - t <= K) v -= coef[2 * h - t];
-    w[t] = v;
-    ca[t] = (t >= 1 && t <= K) ? coef[h + t] : 0.0;
+    w[t] = (float)v;
+    ca[t] = (t >= 1 && t <= K) ? (float)coef[h + t] : 0.f;
   }
   __syncthreads();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= nn) return;
   double d = 0.0, a = 0.0;
-  for (int t = 0; t <= h; ++t) {
-    const double x = (double)T[(long long)t * nn + e];
-    d += w[t] * x;
-    if (t >= 1 && t <= K) a += ca[t] * x;
+  for (int t0 = 0; t0 <= h; t0 += 8) {
+    float dr = 0.f, ar = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int t = t0 + i;
+      if (t <= h) {
+        const float x = T[(long long)t * nn + e];
+        dr = fmaf(w[t], x, dr);
+        ar = fmaf(ca[t], x, ar);
+      }
+    }
+    d += (double)dr;
+    a += (double)ar;
   }
   D[e] = d;
   A2[e] = (float)(2.0 * a);

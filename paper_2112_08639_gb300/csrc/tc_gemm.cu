@@ -121,6 +121,31 @@ __device__ __forceinline__ void split_store(float t, __nv_bfloat16* out, long lo
   }
 }
 
+// The three BF16 pieces of 8 consecutive values of a row (row r of a piece
+// array at base + r * ld): one 16-byte store per piece when all 8 are inside
+// the row and 16-byte aligned, element stores for the first nvalid otherwise.
+__device__ __forceinline__ void store_row_pieces(const float (&v)[8], __nv_bfloat16* base,
+                                                 long long piece_stride, int nvalid,
+                                                 bool aligned16) {
+  if (nvalid >= 8 && aligned16) {
+    __align__(16) __nv_bfloat16 pc[3][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      pc[0][i] = __float2bfloat16_rn(v[i]);
+      const float r1 = v[i] - __bfloat162float(pc[0][i]);
+      pc[1][i] = __float2bfloat16_rn(r1);
+      pc[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(pc[1][i]));
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      *reinterpret_cast<uint4*>(base + q * piece_stride) = *reinterpret_cast<const uint4*>(pc[q]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < nvalid) split_store(v[i], base, i, piece_stride, 3);
+  }
+}
+
 // Persistent CTAs (one per SM) walk the output tiles t = blockIdx.x +
 // i gridDim.x; the TMA producer and the MMA issuer run through the stages
 // of successive tiles back to back, so the next tile's copies and MMAs
@@ -434,7 +459,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             if (EPI == EPI_TC_ATOMIC) {
               atomicAdd(p.C64 + e, acc);
             } else if (EPI == EPI_TC_STORE) {
-              p.C32[e] = (float)((double)p.alpha * acc);
+              const float v = (float)((double)p.alpha * acc);
+              p.C32[e] = v;
+              tvs[i] = v;
+              if (p.colP) split_store(v, p.colP, (long long)n * p.col_ld + m, p.col_ps, 3);
             } else if (EPI == EPI_TC_CHEB) {
               const float tv = (float)(2.0 * acc - (double)p.Tprev[e]);
               tvs[i] = tv;
@@ -451,29 +479,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             // off-diagonal tile, row m of it holding this lane's 8 columns
             const int nb = n0 + half * ACC_COLS + c * 8;
             float* cm32 = p.C32 + (long long)m * p.ldc + nb;
-            __nv_bfloat16* bm = p.Bnext + (long long)m * p.ld_next + nb;
             if (nb + 8 <= p.N && (p.ldc & 3) == 0) {
               reinterpret_cast<float4*>(cm32)[0] = make_float4(tvs[0], tvs[1], tvs[2], tvs[3]);
               reinterpret_cast<float4*>(cm32)[1] = make_float4(tvs[4], tvs[5], tvs[6], tvs[7]);
-              __align__(16) __nv_bfloat16 pc[3][8];
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                pc[0][i] = __float2bfloat16_rn(tvs[i]);
-                const float r1 = tvs[i] - __bfloat162float(pc[0][i]);
-                pc[1][i] = __float2bfloat16_rn(r1);
-                pc[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(pc[1][i]));
-              }
-              for (int q = 0; q < p.next_pieces && q < 3; ++q)
-                *reinterpret_cast<uint4*>(bm + q * p.next_piece_stride) =
-                    *reinterpret_cast<const uint4*>(pc[q]);
             } else {
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                if (nb + i >= p.N) continue;
-                cm32[i] = tvs[i];
-                split_store(tvs[i], bm, i, p.next_piece_stride, p.next_pieces);
-              }
+              for (int i = 0; i < 8; ++i)
+                if (nb + i < p.N) cm32[i] = tvs[i];
             }
+            store_row_pieces(tvs, p.Bnext + (long long)m * p.ld_next + nb, p.next_piece_stride,
+                             p.N - nb, (p.ld_next & 7) == 0);
+          }
+          if (EPI == EPI_TC_STORE && p.rowP) {
+            // the pieces of row m of the result, this lane's 8 columns
+            const int nb = n0 + half * ACC_COLS + c * 8;
+            store_row_pieces(tvs, p.rowP + (long long)m * p.row_ld + nb, p.row_ps, p.N - nb,
+                             (p.row_ld & 7) == 0);
           }
         }
       }

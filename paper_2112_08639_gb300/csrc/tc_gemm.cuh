@@ -43,6 +43,12 @@ struct TcParams {
   long long ld_next, next_piece_stride;
   int next_pieces;
   double* trace;
+  // EPI_TC_STORE, optional: the three BF16 pieces of the stored values in
+  // two layouts, colP[q*col_ps + n*col_ld + m] and rowP[q*row_ps + m*row_ld + n]
+  __nv_bfloat16* colP;
+  long long col_ld, col_ps;
+  __nv_bfloat16* rowP;
+  long long row_ld, row_ps;
   // EPI_TC_RHO: rho[m] += rho_alpha * sum_n X[m + n*ldx] acc(m, n)
   const float* X;
   long long ldx;
