@@ -3,8 +3,8 @@
 One step = one fixed-potential SQ3 iteration of the 108-atom Al-like cell
 (72^3 grid, Ns = 2200, filter degree 30, Fermi degree 120, s/p projectors):
 Chebyshev filter, Cholesky-QR orthonormalisation, Hs = X^T H X, Lanczos
-bounds, Chebyshev Fermi-operator expansion with on-device Fermi-level
-bisection, Ds, and the fused density rho = 2 rowdot(X, X Ds)/dV.  Every step
+bounds, Chebyshev Fermi-operator expansion with the Fermi level found on
+the device, Ds, and the fused density rho = 2 rowdot(X, X Ds)/dV.  Every step
 runs through the C ABI of libsq3 (ctypes binding); inputs are seeded and
 synthetic and resident in HBM when the timed region starts (X alone is
 larger than L2).

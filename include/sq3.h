@@ -48,7 +48,7 @@ typedef enum {
   SQ3_FP64 = 0,   /* X double; every step in FP64                           */
   SQ3_MIXED = 1   /* X float; stencil FP32; Gram/projection/recurrence/XD on
                      tcgen05 BF16 split products with FP32 accumulation;
-                     Cholesky, bisection, energies and reductions in FP64    */
+                     Cholesky, Fermi level, energies and reductions in FP64  */
 } sq3_prec;
 
 enum {
@@ -57,7 +57,7 @@ enum {
   SQ3_ENOTSETUP = -2,   /* grid or potential not set                          */
   SQ3_ECUDA = -3,       /* a CUDA runtime/driver call failed                  */
   SQ3_ENOTPD = -4,      /* Cholesky pivot <= 0: X^T X not positive definite   */
-  SQ3_ENOCONV = -5,     /* bisection or spectral-bound check failed           */
+  SQ3_ENOCONV = -5,     /* Fermi-level bracket or spectral-bound check failed */
   SQ3_ETIMEOUT = -6,    /* a bounded device-side wait ran out                 */
   SQ3_ENONFINITE = -7,  /* NaN/Inf detected in an output                      */
   SQ3_ENOMEM = -8       /* workspace allocation failed                        */
@@ -144,19 +144,21 @@ int sq3_project(sq3_ctx* ctx, const void* X, int Ns, sq3_prec prec,
  *   Hhat = (Hs - chi I)/xi; T_0 = I, T_1 = Hhat, T_{j+1} = 2 Hhat T_j - T_{j-1}
  *   (Eq. (ThreeTermRecurrenceRelation)); moments m_j = tr T_j;
  *   c_j(mu), d_j, e_j by Chebyshev-Gauss quadrature of Eq. (ChebyshevCoeff)
- *   with M = max(1024, 8(npl+1)) nodes; mu by bisection on
+ *   with M = max(1024, 8(npl+1)) nodes; mu by multisection (the bracket
+ *   shrinks 64-fold per round, to double precision) on
  *   2 sum'_j c_j(mu) m_j = Ne (Eq. (FermiLevelCalc));
  *   Ds = sum'_j c_j T_j (Eq. (ChebyshevExpansion));
  *   E_band = 2 sum'_j d_j m_j; E_ent = 2 sigma sum'_j e_j m_j.
  * prec: SQ3_FP64 runs the recurrence in FP64; SQ3_MIXED keeps T_j in FP32
- * with BF16-split tensor-core products (traces, bisection and Ds in FP64).
+ * with BF16-split tensor-core products (the Fermi level in FP64; traces and
+ * Ds summed in FP64).
  * Hs: device Ns x Ns double (symmetric).  kT: sigma in Ha.  bounds_in: HOST
  * pointer to {chi, xi} to use as given, or NULL to estimate them with a
  * 40-step Lanczos on Hs (extremal Ritz values widened by their residual
  * bounds, then xi *= 1.001).  D: device Ns x Ns double output (may be NULL).
  * out: HOST array of 6 doubles receiving {mu, E_band, E_ent, chi, xi,
  * 2 tr Ds}.  Requires npl >= 1 and 0 < Ne < 2 Ns.
- * Errors: SQ3_EINVAL, SQ3_ENOCONV (bisection did not bracket a root, or the
+ * Errors: SQ3_EINVAL, SQ3_ENOCONV (the initial bracket holds no root, or the
  * moments exceed the bound |m_j| <= Ns by more than 1e-6 relative, which
  * means the spectrum left [-1, 1]). */
 int sq3_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,

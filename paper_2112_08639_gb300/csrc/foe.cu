@@ -12,8 +12,9 @@
 // theta_k = (k + 1/2) pi / M, M = max(1024, 8 (npl + 1)).  With that rule the
 // electron count is a double sum over j and k; this implementation sums over
 // j first, w_k = sum'_j m_j T_j(cos theta_k) (independent of mu), so every
-// bisection step costs M Fermi evaluations and one block reduction, all on
-// the GPU in FP64.  All T_j are kept (they fit in HBM for the sizes used), so
+// evaluation of the count costs M Fermi evaluations and one block
+// reduction; mu is found by a multisection that evaluates 63 counts per
+// round, one block each, all on the GPU in FP64.  All T_j are kept (they fit in HBM for the sizes used), so
 // Ds is a weighted sum of stored matrices instead of a second recurrence.
 #include <math.h>
 

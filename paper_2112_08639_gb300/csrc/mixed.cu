@@ -9,7 +9,8 @@
 //                    (shifted Cholesky QR) before the two plain passes.
 //   project          H X by the FP32 stencil, Hs = X^T (H X) (tcgen05)
 //   kernel           Hhat and T_j in FP32 with BF16-split products, traces
-//                    and the Fermi-level bisection in FP64, Ds in FP64
+//                    and the Fermi-level multisection in FP64, Ds summed in
+//                    FP64 from FP32 products
 //   density          X Ds (tcgen05) with the FP64 row-dot epilogue
 // The split of an FP32 value x into bf16 pieces is x_0 = bf16(x),
 // x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1), all round-to-nearest-even.

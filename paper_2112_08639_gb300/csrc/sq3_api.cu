@@ -346,7 +346,7 @@ const char* sq3_status_string(int s) {
     case SQ3_ENOTSETUP: return "grid or potential not set";
     case SQ3_ECUDA: return "CUDA error";
     case SQ3_ENOTPD: return "Cholesky pivot not positive (X^T X not positive definite)";
-    case SQ3_ENOCONV: return "bisection or spectral bound check failed";
+    case SQ3_ENOCONV: return "Fermi-level bracket or spectral bound check failed";
     case SQ3_ETIMEOUT: return "bounded device wait timed out";
     case SQ3_ENONFINITE: return "non-finite value detected";
     case SQ3_ENOMEM: return "workspace allocation failed";

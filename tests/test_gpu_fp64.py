@@ -108,7 +108,7 @@ def _random_hs(Ns, seed, lo=-0.6, hi=2.0):
 @pytest.mark.parametrize("Ns,npl", [(64, 60), (75, 11), (130, 25), (5, 3)])
 def test_kernel_from_hs_given_bounds_matches_foe_oracle(Ns, npl):
     """With the oracle's exact chi, xi passed in, the GPU's recurrence,
-    moments, bisection, coefficients and sums reproduce the oracle's
+    moments, Fermi level, coefficients and sums reproduce the oracle's
     Chebyshev expansion, including its truncation error at low npl."""
     sigma = inputs.ev_to_ha(10.0)
     Ne = min(12.0, 1.2 * Ns)

@@ -1,5 +1,5 @@
 """GPU parity of the mixed-precision path (FP32 block, BF16-split tcgen05
-GEMMs with FP32 accumulation, FP64 Cholesky/bisection/energies).
+GEMMs with FP32 accumulation, FP64 Cholesky fallback, Fermi level and energies).
 
 Single steps are compared with the FP64 oracle on the same inputs at
 tolerances set by FP32 storage (2^-24 ~ 6e-8 per element) times the
