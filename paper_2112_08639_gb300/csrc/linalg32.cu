@@ -174,14 +174,21 @@ potrf_dev_kernel(float* E, int n, int k0, int kb, int* status) {
   }
 }
 
-// L21 = E21 (I + F11)^{-T}: each thread solves one row of the panel below.
+// L21 = E21 (I + F11)^{-T}: each thread solves one row of the panel below,
+// right-looking: once x_c is known it is subtracted from every later entry
+// (independent FMAs), so the dependent chain is one multiply per column
+// instead of a dot product per column; each entry still receives its terms
+// in increasing column order.  The pivots' reciprocals are formed once.
 __global__ void __launch_bounds__(128)
 trsm_dev_kernel(float* E, int n, int k0, int kb) {
   __shared__ float L[NB][NB + 1];
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int i = e % kb, j = e / kb;
-    L[i][j] = (i >= j) ? E[(k0 + i) + (long long)(k0 + j) * n] : 0.f;
+  __shared__ float rinv[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e % NB, j = e / NB;
+    L[i][j] = (i < kb && j <= i) ? E[(k0 + i) + (long long)(k0 + j) * n] : 0.f;
   }
+  for (int c = threadIdx.x; c < kb; c += blockDim.x)
+    rinv[c] = 1.f / (1.f + E[(k0 + c) + (long long)(k0 + c) * n]);
   __syncthreads();
   const int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
   const bool ok = i < n;
@@ -191,10 +198,9 @@ trsm_dev_kernel(float* E, int n, int k0, int kb) {
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < kb) {
-      float s = x[c];
+      x[c] *= rinv[c];
 #pragma unroll
-      for (int j = 0; j < c; ++j) s -= x[j] * L[c][j];
-      x[c] = s / (1.f + L[c][c]);
+      for (int j = c + 1; j < NB; ++j) x[j] -= x[c] * L[j][c];
     }
   }
   if (ok) {
