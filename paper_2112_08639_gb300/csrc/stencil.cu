@@ -641,11 +641,13 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
 // the projection).  Each group's values, a VB x NL_BZ x 8 x 8 box of the
 // block, arrive by one 4-D TMA load into a ring of NBUF buffers (issued
 // NBUF groups ahead); the group's coefficients gC arrive by cp.async.
-//   phase 1: one thread per point applies the term in shared memory; the
-//            box goes back to global memory with one TMA store;
-//   phase 2: warps take (ball, half of its points) tasks, lanes over points,
-//            4 VB partial sums per lane folded across the warp by a halving
-//            butterfly; one atomic per (projector, vector) and task.
+//   phase 1: a lane applies the term to two points for half of the
+//            vectors in shared memory and keeps a point-major copy of the
+//            results for phase 2; the box goes back to global memory with
+//            one TMA store;
+//   phase 2: a warp takes a ball, its lanes eight entry slots and four
+//            16-byte quarters of the vectors, the slots folded by three
+//            shuffle rounds; one atomic per (projector, vector) and ball.
 // The box store writes unchanged points back unchanged; elements outside
 // the grid or beyond Ns are zero-filled on load and skipped on store.
 // ---------------------------------------------------------------------------
@@ -839,7 +841,9 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       tma_store_4d(&omap, smem_u32(yb), bx * 8, by * 8, bz * NL_BZ, g * VB);
       bulk_commit();
     }
-    // phase 2: projection of the updated values, per (ball, half).  A lane
+    // phase 2: projection of the updated values, one warp per ball (a brick
+    // has about 6 balls for 8 warps; halves of balls were measured slower:
+    // twice the folds and atomics for the same longest warp).  A lane
     // serves one of NSL entry slots and one 16-byte quarter of the group's
     // vectors: NSL entries are read per step, each slot sums 4 projectors x EV
     // vectors, and the slots are folded at the end (three shuffle rounds).
@@ -850,11 +854,8 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       constexpr int NR = NA / NSL;                   // sums per lane after the fold
       static_assert(NQ == 4 && NR * NSL == NA, "four quarters, eight slots");
       const int qd = lane % NQ, sl = lane / NQ;
-      for (int task = warp; task < 2 * nlb; task += PTS / 32) {
-        const int lb = task >> 1;
-        const int fa = bl_ptr[s0 + lb] - fb, fe = bl_ptr[s0 + lb + 1] - fb;
-        const int fm = fa + (fe - fa + 1) / 2;
-        const int f0 = (task & 1) ? fm : fa, f1 = (task & 1) ? fe : fm;
+      for (int lb = warp; lb < nlb; lb += PTS / 32) {
+        const int f0 = bl_ptr[s0 + lb] - fb, f1 = bl_ptr[s0 + lb + 1] - fb;
         T a[NA];
 #pragma unroll
         for (int i = 0; i < NA; ++i) a[i] = T(0);
