@@ -939,9 +939,9 @@ static int launch_brick(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int
   const int nb = ((g.nx + 7) / 8) * ((g.ny + 7) / 8) * ((g.nz + NL_BZ - 1) / NL_BZ);
   const int ngroups = (Ns + VB - 1) / VB;
   // runs of groups: several CTAs per SM-slot in total, each run long enough
-  // to amortise staging the brick's tables
+  // to amortise staging the brick's tables (few groups: runs of up to 8)
   int per = (ngroups + 7) / 8;
-  if (per < 4) per = ngroups < 4 ? ngroups : 4;
+  if (ngroups < 32) per = ngroups < 8 ? ngroups : 8;
   const int nruns = (ngroups + per - 1) / per;
   auto kern = nl_brick_kernel<T, VB, NBUF, MINB>;
   if (smem > 48 * 1024)
