@@ -208,7 +208,13 @@ def run_sq3(args, rank, world):
     Vh = V.cpu().pin_memory()
     rho_h = torch.empty(cfg.N, dtype=torch.float64).pin_memory()
 
+    # every end-to-end step starts from the same host block and the same
+    # filter bounds (the steps would otherwise alternate between two bound
+    # settings, since each one restarts from that block)
+    bounds0 = dict(state)
+
     def e2e_step():
+        state.update(bounds0)
         V.copy_(Vh, non_blocking=True)
         ctx.set_potential(V)
         step(X, Xh)
