@@ -101,7 +101,7 @@ gemm_f64_kernel(GemmArgs g) {
     }
   }
 
-  if (EPI == EPI_RHO) {
+  if constexpr (EPI == EPI_RHO) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int m = m0 + ty + 16 * i;
@@ -116,27 +116,27 @@ gemm_f64_kernel(GemmArgs g) {
       for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (tx == 0 && m < g.M) atomicAdd(g.rho + m, g.alpha * s);
     }
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
-    if (m >= g.M) continue;
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
-      if (n >= g.N) continue;
-      double* c = g.C + m + (long long)n * g.ldc;
-      if (EPI == EPI_STORE) {
-        double v = g.alpha * acc[i][j];
-        if (g.beta != 0.0) v += g.beta * *c;
-        *c = v;
-      } else if (EPI == EPI_ATOMIC) {
-        atomicAdd(c, g.alpha * acc[i][j]);
-      } else {  // EPI_CHEB
-        const double v = 2.0 * acc[i][j] - g.P[m + (long long)n * g.ldp];
-        *c = v;
-        if (m == n && g.trace != nullptr) atomicAdd(g.trace, v);
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n >= g.N) continue;
+        double* c = g.C + m + (long long)n * g.ldc;
+        if (EPI == EPI_STORE) {
+          double v = g.alpha * acc[i][j];
+          if (g.beta != 0.0) v += g.beta * *c;
+          *c = v;
+        } else if (EPI == EPI_ATOMIC) {
+          atomicAdd(c, g.alpha * acc[i][j]);
+        } else {  // EPI_CHEB
+          const double v = 2.0 * acc[i][j] - g.P[m + (long long)n * g.ldp];
+          *c = v;
+          if (m == n && g.trace != nullptr) atomicAdd(g.trace, v);
+        }
       }
     }
   }

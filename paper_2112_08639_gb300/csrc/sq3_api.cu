@@ -113,7 +113,6 @@ static int upload(T** dst, const T* src, size_t n) {
   return cuda_err(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
 }
 
-static int elem_size(sq3_prec p) { return p == SQ3_FP64 ? 8 : 4; }
 
 // Two gC workspaces (current and next step) for the nonlocal projections.
 static int gc_buffer(sq3_ctx* ctx, int Ns, void** out, void** out2 = nullptr) {

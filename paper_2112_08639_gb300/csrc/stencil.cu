@@ -213,7 +213,6 @@ cheb_step_vec_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = nx / VW;
   const int Wd = nx + 2 * PAD;
-  const int rows = TY + 2 * R;
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
@@ -502,15 +501,7 @@ static int pick_ty(int nx, int ny, int target) {
   return best;
 }
 
-static int stencil_vb(int esize) {
-  static int forced = -1;
-  if (forced < 0) {
-    const char* e = getenv("SQ3_STENCIL_VB");
-    forced = e ? atoi(e) : 0;
-  }
-  if (forced == 1 || forced == 2 || forced == 4) return forced;
-  return esize == 8 ? 1 : 2;
-}
+static int stencil_vb(int esize) { return esize == 8 ? 1 : 2; }
 
 template <typename T, int R, int VB>
 static void launch_rv(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
@@ -546,12 +537,6 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   constexpr int VW = Vec16<T>::W;
   constexpr int PAD = ((R + VW - 1) / VW) * VW;
   const Grid& g = ctx->grid;
-  static int disabled = -1;
-  if (disabled < 0) {
-    const char* e = getenv("SQ3_STENCIL_GENERIC");
-    disabled = (e && atoi(e) == 1) ? 1 : 0;
-  }
-  if (disabled) return false;
   if (g.nx % VW || g.nx < PAD) return false;
   // 16-byte vector accesses need 16-byte aligned blocks
   if (((uintptr_t)y | (uintptr_t)out | (uintptr_t)(yprev ? yprev : y)) & 15) return false;
@@ -572,13 +557,8 @@ static bool launch_vec(const sq3_ctx* ctx, const T* y, const T* yprev, T* out,
   const T* V;
   if constexpr (sizeof(T) == 8) V = reinterpret_cast<const T*>(ctx->V);
   else V = reinterpret_cast<const T*>(ctx->Vf);
-  static int ring = -1;
-  if (ring < 0) {
-    const char* e = getenv("SQ3_STENCIL_RING");
-    ring = (e && atoi(e) == 0) ? 0 : 1;
-  }
   const int rv = TX + 2 * (PAD / VW);
-  if (ring && (TY + 2 * R) * rv <= 4 * TX * TY) {
+  if ((TY + 2 * R) * rv <= 4 * TX * TY) {
     constexpr int A = 4;
     const size_t rs = (size_t)(A + 1) *
                       ((size_t)(TY + 2 * R) * ring_row_width<T>(g.nx, PAD) +
