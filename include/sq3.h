@@ -181,6 +181,16 @@ int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
 int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
                 sq3_prec prec, double* rho);
 
+/* Self-test of the device-side failure path (no counterpart in the paper):
+ * one CTA waits on an mbarrier that nothing completes, through the bounded
+ * wait (about one second of wall time) that every TMA and tensor-core wait
+ * of the library uses; the wait runs out, the kernel records a timeout in
+ * the context's status word and returns, and the host reads it.  Returns
+ * SQ3_ETIMEOUT when the path works (the status word is cleared, so the
+ * context stays usable), SQ3_OK if the wait did not run out, SQ3_EINVAL for
+ * a NULL context, SQ3_ECUDA on a CUDA error.  No fault, trap or hang. */
+int sq3_selftest_timeout(sq3_ctx* ctx);
+
 /* Per-stage timing (tracing).  When enabled, the library records a CUDA
  * event pair on the context's stream around the launches of each stage of
  * the path; sq3_profile_read synchronises the stream, writes for each stage

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "sq3_internal.cuh"
 
 namespace sq3 {
@@ -608,6 +609,34 @@ int sq3_cheb_filter(sq3_ctx* c, void* X, int Ns, int degree, double a,
   else if (prec == SQ3_MIXED) rc = cheb_filter_t<float>(c, (float*)X, Ns, degree, a, b, a0);
   else return SQ3_EINVAL;
   return finish(c, rc);
+}
+
+namespace sq3 {
+// One CTA waits on an mbarrier that nothing completes, through the same
+// bounded wait (ac::mbar_wait, about one second) that the library's kernels
+// use for their TMA and tensor-core barriers; when it runs out the kernel
+// records DEV_TIMEOUT and returns.
+__global__ void timeout_selftest_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = ac::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    ac::mbar_init(b, 1);
+    ac::mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !ac::mbar_wait(b, 0)) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+}
+}  // namespace sq3
+
+int sq3_selftest_timeout(sq3_ctx* c) {
+  if (!c) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  timeout_selftest_kernel<<<1, 32, 0, c->stream>>>(c->dev_status);
+  const int rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  // SQ3_ETIMEOUT when the wait ran out as it should; the status word is
+  // cleared by the check, so the context stays usable
+  return check_device_status(c);
 }
 
 int sq3_cheb_filter_from_host(sq3_ctx* c, const void* X_host, void* X, int Ns, int degree,

@@ -50,6 +50,7 @@ _sigs = {
     "sq3_last_cuda_error": (ctypes.c_char_p, []),
     "sq3_profile_enable": (_i, [_p, _i]),
     "sq3_lanczos_bounds_noalloc": (_i, [_p, _i, _p, _p]),
+    "sq3_selftest_timeout": (_i, [_p]),
     "sq3_profile_read": (_i, [_p, _p, _p, _i]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -221,6 +222,11 @@ class Context:
 
     STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
               "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy", "nl_pass")
+
+    def selftest_timeout(self) -> int:
+        """Runs the bounded-wait failure path; returns the status code
+        (ETIMEOUT when it works)."""
+        return lib.sq3_selftest_timeout(self._h)
 
     def profile(self, enable: bool = True):
         _check(lib.sq3_profile_enable(self._h, int(enable)), "sq3_profile_enable")
