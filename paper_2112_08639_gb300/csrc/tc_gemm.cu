@@ -587,13 +587,10 @@ static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& 
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
   const int smem = STAGES * STAGE_BYTES + 1024;
   auto k = tc_gemm_kernel<PA, PB, EPI>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-      return SQ3_ECUDA;
-    attr = true;
-  }
+  // per launch (about a microsecond), so that every device the process uses
+  // has the attribute set
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return SQ3_ECUDA;
   k<<<grid, THREADS, smem, st>>>(a, b, p);
   return cuda_err(cudaGetLastError());
 }
@@ -634,13 +631,12 @@ int tc_gemm(sq3_ctx* ctx, const Operand& A, const Operand& B, const Products& pr
   if (p.tri == 1 && tN < tM) return SQ3_EINVAL;   // upper tiles need N >= M
   const long long tiles = (p.tri == 1 ? tM * (2 * tN - tM + 1) / 2 : tN * tM) * splits;
   if (tiles > (1LL << 30)) return SQ3_EINVAL;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        sms < 1)
-      sms = 152;
+  int dev = 0, sms = 0;                            // the current device's SM count
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 152;
   }
   dim3 grid((unsigned)(tiles < sms ? tiles : sms));
   switch (epi) {
