@@ -25,6 +25,12 @@ What it computes, and where the paper defines it:
 * ``subspace``    -- orthonormalisation by Cholesky QR, Hs = X^T H X
                      (Sec. 3, Eq. (DsHsRelation)), and rho from the kernel
                      (Eq. (phi_tilde), Eq. (density:NewForm)).
+* ``scf``         -- the self-consistent loop around the fixed-potential
+                     iteration: Gaussian pseudocharges and the FD Poisson
+                     equation (Sec. 2, Eq. (poisson)), the LDA, Kerker-
+                     preconditioned periodic Pulay mixing (cited in Sec. 5)
+                     and the free energy (Eq. (ON:FreeEnergy),
+                     Eq. (FreeEnergy:NewForm)).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, library routines or brute force; none is marked "parity
