@@ -181,6 +181,58 @@ int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
 int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
                 sq3_prec prec, double* rho);
 
+/* ---- Self-consistent-field pieces (no Hamiltonian or potential needed;
+ * the grid must be set).  All arrays are device arrays of N doubles in grid
+ * order (x fastest), owned by the caller.  Each call returns after its work
+ * on the context's stream is done.  Every sum runs in a fixed order, so
+ * repeated calls agree bit for bit. ---- */
+
+/* Electrostatic potential (Sec. 2, Eq. (poisson)): phi with
+ * -L_h phi = 4 pi (rho + b - mean(rho + b)), L_h the grid's finite-difference
+ * Laplacian (the one of the Hamiltonian), solved exactly in the real Fourier
+ * basis of the grid (in which L_h is diagonal); phi has zero mean (the
+ * constant mode is dropped: a neutral total charge fixes phi up to a
+ * constant).  b may be NULL (phi of rho alone).  phi may alias rho or b.
+ * Errors: SQ3_EINVAL (null rho or phi), SQ3_ENOTSETUP, SQ3_ENOMEM,
+ * SQ3_ECUDA. */
+int sq3_poisson(sq3_ctx* ctx, const double* rho, const double* b, double* phi);
+
+/* Effective potential V_eff = phi[rho + b] + V_xc[rho] (Sec. 2,
+ * Eq. (KSeqn) and Eq. (poisson)) with the LDA: Slater exchange and the
+ * Perdew-Wang 1992 correlation of the spin-unpolarised electron gas, rho
+ * clamped below at 1e-14.  veff: output (may alias rho).  phi: optional
+ * output of the electrostatic potential (NULL = not returned; must not
+ * alias rho, b or veff).  b may be NULL.  terms: optional HOST array of 3
+ * doubles receiving E_xc = int eps_xc rho, int V_xc rho and
+ * 1/2 int (b - rho) phi (the terms of the free energy that depend on rho;
+ * integrals are sums times the grid's volume element).  Feed veff to
+ * sq3_set_potential for the next iteration.
+ * Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOMEM, SQ3_ECUDA,
+ * SQ3_ENONFINITE (a term is not finite). */
+int sq3_effective_potential(sq3_ctx* ctx, const double* rho, const double* b,
+                            double* veff, double* phi, double* terms);
+
+/* Free energy (Sec. 3, Eq. (FreeEnergy:NewForm); Sec. 2,
+ * Eq. (ON:FreeEnergy)):
+ *   F = E_band + E_xc[rho] - int V_xc[rho] rho + 1/2 int (b - rho) phi[rho + b]
+ *       - E_self + E_ent,
+ * with the overlap correction E_c = 0 (the pseudocharges b are the nuclei's
+ * charges themselves).  rho: the electron density of the iteration that gave
+ * E_band and E_ent (sq3_density, sq3_density_kernel); b: the pseudocharge
+ * density (sum b dV = -N_e); e_self: the pseudocharges' self energy, which
+ * the caller knows in closed form (Z^2 / (sqrt(2 pi) r_c) per Gaussian).
+ * out: HOST array of 4 doubles: F, E_xc, int V_xc rho, 1/2 int (b - rho) phi.
+ * Errors: as sq3_effective_potential. */
+int sq3_free_energy(sq3_ctx* ctx, const double* rho, const double* b,
+                    double e_band, double e_ent, double e_self, double* out);
+
+/* Kerker preconditioner of the density mixing (Sec. 5 cites the real-space
+ * Kerker preconditioner): out = K r with K(G) = G^2 / (G^2 + k0^2) on the
+ * periodic cell's reciprocal vectors (K(0) = 0: the result has zero mean),
+ * applied in the real Fourier basis of the grid.  k0 > 0 in 1/bohr.  out
+ * may alias r.  Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOMEM, SQ3_ECUDA. */
+int sq3_kerker(sq3_ctx* ctx, const double* r, double* out, double k0);
+
 /* Self-test of the device-side failure path (no counterpart in the paper):
  * one CTA waits on an mbarrier that nothing completes, through the bounded
  * wait (about one second of wall time) that every TMA and tensor-core wait

@@ -391,7 +391,8 @@ void sq3_destroy(sq3_ctx* c) {
   for (auto e : c->upload_ev) if (e) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
-                  c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32};
+                  c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32,
+                  c->scfTab, c->wsScf};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   delete c;
@@ -417,6 +418,7 @@ int sq3_setup_grid(sq3_ctx* c, int nx, int ny, int nz, double Lx, double Ly,
   c->dV = g.hx * g.hy * g.hz;
   c->grid_ok = true;
   c->pot_ok = false;
+  c->scf_tab_ok = false;
   if (c->V) cudaFree(c->V);
   if (c->Vf) cudaFree(c->Vf);
   c->V = nullptr; c->Vf = nullptr;

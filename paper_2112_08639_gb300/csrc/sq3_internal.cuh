@@ -112,6 +112,11 @@ struct sq3_ctx {
   void* wsSplit = nullptr; size_t wsSplit_bytes = 0;  // bf16 split operands
   double* wsFoe = nullptr; size_t wsFoe_bytes = 0;    // quadrature node values
   float* wsLin32 = nullptr; size_t wsLin32_bytes = 0;  // FP32 factor, inverse, temporaries
+  // self-consistent-field pieces (scf.cu): real Fourier basis tables of the
+  // grid (rebuilt after sq3_setup_grid) and two N-point buffers + partials
+  double* scfTab = nullptr; size_t scfTab_bytes = 0;
+  bool scf_tab_ok = false;
+  double* wsScf = nullptr; size_t wsScf_bytes = 0;
   // uploads of a host block (sq3_cheb_filter_from_host): a stream of their
   // own and one event per chunk, created on first use
   cudaStream_t copy_stream = nullptr;

@@ -52,6 +52,10 @@ _sigs = {
     "sq3_lanczos_bounds_noalloc": (_i, [_p, _i, _p, _p]),
     "sq3_selftest_timeout": (_i, [_p]),
     "sq3_profile_read": (_i, [_p, _p, _p, _i]),
+    "sq3_poisson": (_i, [_p, _p, _p, _p]),
+    "sq3_effective_potential": (_i, [_p, _p, _p, _p, _p, _p]),
+    "sq3_free_energy": (_i, [_p, _p, _p, _d, _d, _d, _p]),
+    "sq3_kerker": (_i, [_p, _p, _p, _d]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -219,6 +223,46 @@ class Context:
         _check(lib.sq3_density(self._h, _ptr(X), _ptr(D), X.shape[0], prec, _ptr(rho)),
                "sq3_density")
         return rho
+
+    def _grid_vec(self, t: torch.Tensor | None):
+        if t is not None and (t.dtype != torch.float64 or t.numel() != self.N):
+            raise ValueError("expected a float64 CUDA tensor of N grid points")
+        return _ptr(t)
+
+    def poisson(self, rho: torch.Tensor, b: torch.Tensor | None = None,
+                phi: torch.Tensor | None = None) -> torch.Tensor:
+        """phi of rho + b (b optional) on the grid, zero mean."""
+        if phi is None:
+            phi = torch.empty_like(rho)
+        _check(lib.sq3_poisson(self._h, self._grid_vec(rho), self._grid_vec(b),
+                               self._grid_vec(phi)), "sq3_poisson")
+        return phi
+
+    def effective_potential(self, rho: torch.Tensor, b: torch.Tensor | None = None,
+                            veff: torch.Tensor | None = None, phi: torch.Tensor | None = None):
+        """(veff, terms): V_eff = phi[rho + b] + V_xc[rho] and the terms
+        {e_xc, vxc_rho, e_es} of the free energy."""
+        if veff is None:
+            veff = torch.empty_like(rho)
+        t = (ctypes.c_double * 3)()
+        _check(lib.sq3_effective_potential(self._h, self._grid_vec(rho), self._grid_vec(b),
+                                           self._grid_vec(veff), self._grid_vec(phi), t),
+               "sq3_effective_potential")
+        return veff, {"e_xc": t[0], "vxc_rho": t[1], "e_es": t[2]}
+
+    def free_energy(self, rho: torch.Tensor, b: torch.Tensor, e_band: float, e_ent: float,
+                    e_self: float) -> dict:
+        out = (ctypes.c_double * 4)()
+        _check(lib.sq3_free_energy(self._h, self._grid_vec(rho), self._grid_vec(b), e_band,
+                                   e_ent, e_self, out), "sq3_free_energy")
+        return {"F": out[0], "e_xc": out[1], "vxc_rho": out[2], "e_es": out[3]}
+
+    def kerker(self, r: torch.Tensor, k0: float = 0.8,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(r)
+        _check(lib.sq3_kerker(self._h, self._grid_vec(r), self._grid_vec(out), k0), "sq3_kerker")
+        return out
 
     STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
               "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy", "nl_pass")

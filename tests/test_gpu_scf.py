@@ -1,0 +1,177 @@
+"""Parity of the self-consistent-field pieces on the GPU (sq3_poisson,
+sq3_effective_potential, sq3_free_energy, sq3_kerker) against the oracle
+(``oracle.scf``), on the same seeded inputs: cubic grids element by element
+(the 18^3 four-atom cell and the full 72^3 grid of the 108-atom cell),
+non-cubic grids with odd and even sides through the oracle's real-space FD
+Laplacian, and the error paths.  All FP64; the GPU solves in the real
+Fourier basis of the grid, the oracle with numpy's FFT, so they agree to
+rounding (1e-12 relative)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fd, scf
+from paper_2112_08639_gb300 import inputs
+
+from gpu_common import need_gpu, sq3
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _ctx(nx, ny, nz, Lx, Ly, Lz, order=12):
+    c = sq3().Context(0)
+    c.setup_grid(nx, ny, nz, Lx, Ly, Lz, order)
+    return c
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to("cuda:0")
+
+
+def _rel_max(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _cell_density(cfg, seed):
+    """A smooth positive density with the cell's electron count and the
+    pseudocharges of its atoms."""
+    pos = inputs.fcc_positions(cfg.ncell, disp_sigma=cfg.disp_sigma, seed=cfg.seed)
+    b, _ = scf.pseudocharge(cfg.n, cfg.L, pos, inputs.Z_VALENCE, inputs.RC_LOCAL, Ne=cfg.Ne)
+    rng = np.random.default_rng(seed)
+    rho = np.exp(0.3 * rng.normal(size=cfg.N)) - 0.9 * b / np.abs(b).max()
+    rho *= cfg.Ne / (rho.sum() * cfg.dV)
+    return pos, b, rho
+
+
+@pytest.mark.parametrize("cfg", [inputs.C1, inputs.C3], ids=lambda c: c.name)
+def test_poisson_matches_oracle_on_cubic_cells(cfg):
+    _, b, rho = _cell_density(cfg, seed=1)
+    ctx = _ctx(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L)
+    phi = ctx.poisson(_dev(rho), _dev(b)).cpu().numpy()
+    ref = scf.poisson_fd(rho + b, cfg.n, cfg.L)
+    assert _rel_max(phi, ref) < TOL
+    # b optional: phi of rho alone
+    phi1 = ctx.poisson(_dev(rho)).cpu().numpy()
+    assert _rel_max(phi1, scf.poisson_fd(rho, cfg.n, cfg.L)) < TOL
+
+
+@pytest.mark.parametrize("dims,order", [((9, 10, 7), 12), ((16, 5, 11), 8), ((3, 2, 1), 2)])
+def test_poisson_noncubic_solves_the_fd_equation(dims, order):
+    nx, ny, nz = dims
+    Lx, Ly, Lz = 0.7 * nx, 0.75 * ny, 0.8 * nz
+    rng = np.random.default_rng(sum(dims))
+    rho = rng.normal(size=nx * ny * nz)
+    ctx = _ctx(nx, ny, nz, Lx, Ly, Lz, order)
+    phi = ctx.poisson(_dev(rho)).cpu().numpy()
+    Lap = fd.laplacian_3d(nx, ny, nz, Lx / nx, Ly / ny, Lz / nz, order)
+    res = -(Lap @ phi) / (4 * np.pi) - (rho - rho.mean())
+    assert np.max(np.abs(res)) < 1e-11 * np.max(np.abs(rho))
+    assert abs(phi.mean()) < 1e-12 * np.max(np.abs(phi))
+
+
+def test_poisson_in_place_and_repeatable():
+    cfg = inputs.C1
+    _, b, rho = _cell_density(cfg, seed=2)
+    ctx = _ctx(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L)
+    r = _dev(rho)
+    p1 = ctx.poisson(r, _dev(b))
+    p2 = ctx.poisson(r, _dev(b))
+    assert torch.equal(p1, p2)
+    ctx.poisson(r, _dev(b), phi=r)          # phi aliases rho
+    assert torch.equal(r, p1)
+
+
+def test_effective_potential_and_terms_match_oracle():
+    cfg = inputs.C1
+    _, b, rho = _cell_density(cfg, seed=3)
+    ctx = _ctx(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L)
+    phi_d = torch.empty(cfg.N, dtype=torch.float64, device="cuda:0")
+    veff, terms = ctx.effective_potential(_dev(rho), _dev(b), phi=phi_d)
+    phi = scf.poisson_fd(rho + b, cfg.n, cfg.L)
+    _, vxc = scf.lda_xc(rho)
+    assert _rel_max(phi_d.cpu().numpy(), phi) < TOL
+    assert _rel_max(veff.cpu().numpy(), phi + vxc) < TOL
+    ref = scf.free_energy(0.0, 0.0, rho, b, phi, cfg.dV, 4, inputs.Z_VALENCE, inputs.RC_LOCAL)
+    for k in ("e_xc", "vxc_rho", "e_es"):
+        assert abs(terms[k] - ref[k]) < TOL * abs(ref[k]), k
+    # veff may alias rho; a repeated call gives the same bits
+    r = _dev(rho)
+    _, t2 = ctx.effective_potential(r, _dev(b), veff=r)
+    assert torch.equal(r, veff) and t2 == terms
+
+
+def test_lda_on_a_wide_density_range_including_the_floor():
+    """Densities from 0 (clamped at 1e-14) to 10 e/bohr^3, and negative
+    values (clamped too), against the oracle's LDA point by point."""
+    n, L = 8, 5.0
+    rho = np.concatenate([np.zeros(8), -np.logspace(-3, 0, 8), np.logspace(-14, 1, n ** 3 - 16)])
+    ctx = _ctx(n, n, n, L, L, L)
+    phi_d = torch.empty(n ** 3, dtype=torch.float64, device="cuda:0")
+    # b = -rho: the total charge is exactly zero, so phi = 0 and veff = V_xc
+    veff, _ = ctx.effective_potential(_dev(rho), _dev(-rho), phi=phi_d)
+    assert not phi_d.any()
+    _, vxc = scf.lda_xc(rho)
+    np.testing.assert_allclose(veff.cpu().numpy(), vxc, rtol=1e-12, atol=0)
+
+
+def test_free_energy_matches_oracle_at_a_converged_scf():
+    """F of the oracle's converged 4-atom SCF (12^3 grid, kT = 10 eV) from
+    its density, band and entropy energies."""
+    n, L = 12, inputs.A0_FCC
+    pos = inputs.fcc_positions(1, disp_sigma=0.05, seed=0)
+    res = scf.scf(n, L, pos, Ns=40, sigma=inputs.ev_to_ha(10.0), Z=inputs.Z_VALENCE,
+                  rc=inputs.RC_LOCAL, tol=1e-9)
+    ctx = _ctx(n, n, n, L, L, L)
+    out = ctx.free_energy(_dev(res["rho"]), _dev(res["b"]), res["e_band"], res["e_ent"],
+                          scf.self_energy(4, inputs.Z_VALENCE, inputs.RC_LOCAL))
+    assert abs(out["F"] - res["F"]) < TOL * abs(res["F"])
+    for k in ("e_xc", "vxc_rho", "e_es"):
+        assert abs(out[k] - res[k]) < TOL * abs(res[k]), k
+
+
+@pytest.mark.parametrize("n,L,k0", [(18, inputs.A0_FCC, 0.8), (11, 6.3, 1.5)])
+def test_kerker_matches_oracle(n, L, k0):
+    rng = np.random.default_rng(n)
+    r = rng.normal(size=n ** 3)
+    ctx = _ctx(n, n, n, L, L, L)
+    out = ctx.kerker(_dev(r), k0).cpu().numpy()
+    assert _rel_max(out, scf.kerker(r, n, L, k0)) < TOL
+    rd = _dev(r)
+    ctx.kerker(rd, k0, out=rd)                # in place
+    assert _rel_max(rd.cpu().numpy(), out) < 1e-15
+
+
+def test_kerker_noncubic_scales_a_single_mode():
+    nx, ny, nz, Lx, Ly, Lz, k0 = 10, 7, 6, 8.0, 5.0, 4.5, 0.8
+    idx = np.arange(nx * ny * nz)
+    y = ((idx // nx) % ny) * (Ly / ny)
+    mode = np.sin(2 * np.pi * 2 * y / Ly)
+    ctx = _ctx(nx, ny, nz, Lx, Ly, Lz)
+    out = ctx.kerker(_dev(1.5 + mode), k0).cpu().numpy()
+    g2 = (2 * np.pi * 2 / Ly) ** 2
+    np.testing.assert_allclose(out, g2 / (g2 + k0 ** 2) * mode, atol=1e-13)
+
+
+def test_error_paths():
+    m = sq3()
+    c = m.Context(0)
+    x = torch.zeros(8, dtype=torch.float64, device="cuda:0")
+    p = ctypes.c_void_p(x.data_ptr())
+    assert m.lib.sq3_poisson(c._h, p, None, p) == m.ENOTSETUP
+    assert m.lib.sq3_kerker(c._h, p, p, 0.8) == m.ENOTSETUP
+    c.setup_grid(2, 2, 2, 1.0, 1.0, 1.0, 2)
+    assert m.lib.sq3_poisson(c._h, None, None, p) == m.EINVAL
+    assert m.lib.sq3_kerker(c._h, p, p, 0.0) == m.EINVAL
+    assert m.lib.sq3_effective_potential(c._h, p, None, p, p, None) == m.EINVAL   # phi = veff
+    assert m.lib.sq3_free_energy(c._h, p, None, 0.0, 0.0, 0.0, None) == m.EINVAL
+    # the context stays usable
+    assert m.lib.sq3_poisson(c._h, p, None, p) == m.OK
