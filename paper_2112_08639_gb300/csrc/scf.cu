@@ -15,7 +15,7 @@
 // division by (s_x + s_y + s_z) / (4 pi) per mode with the zero mode set to
 // zero (the total charge is zero; phi has zero mean), and three inverse
 // basis changes.  Each basis change is a contraction of length n along one
-// axis; the whole solve is 12 n FMAs per point, far below the cost of the
+// axis; the whole solve is 6 n FMAs per point, far below the cost of the
 // rest of an iteration, so the kernels read their operands through the
 // cache instead of staging them.
 //
