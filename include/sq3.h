@@ -226,6 +226,28 @@ int sq3_effective_potential(sq3_ctx* ctx, const double* rho, const double* b,
 int sq3_free_energy(sq3_ctx* ctx, const double* rho, const double* b,
                     double e_band, double e_ent, double e_self, double* out);
 
+/* Density mixer (Sec. 5 cites periodic Pulay mixing with a Kerker
+ * preconditioner).  sq3_mixer_setup (re)starts it: history = number of
+ * past differences kept (1..8), period = a Pulay extrapolation every
+ * period-th step (1 = every step), beta = mixing parameter (> 0), k0 =
+ * Kerker wave number in 1/bohr (<= 0: no preconditioner).  Its device
+ * state is (3 + 2 history) N doubles, held by the context until it is
+ * destroyed; sq3_setup_grid stops the mixer.
+ * sq3_mixer_step takes one step from the input x_in of an iteration and its
+ * output x_out (device, N doubles each) and writes the next input x_next
+ * (may alias x_in or x_out).  With f = x_out - x_in and the differences
+ * DX, DF of the previous inputs and residuals: every period-th step that
+ * has a history, x_next = x_bar + beta K f_bar with x_bar = x_in - DX c,
+ * f_bar = f - DF c and c the least-squares solution of DF c ~ f (normal
+ * equations by Cholesky; a difference that depends linearly on the earlier
+ * ones, pivot below 1e-12 of its diagonal, is dropped); otherwise
+ * x_next = x_in + beta K f.  K: the Kerker preconditioner below, or the
+ * identity.  Errors: SQ3_EINVAL, SQ3_ENOTSETUP (no grid, or no
+ * sq3_mixer_setup since the last grid), SQ3_ENOMEM, SQ3_ECUDA. */
+int sq3_mixer_setup(sq3_ctx* ctx, int history, int period, double beta, double k0);
+int sq3_mixer_step(sq3_ctx* ctx, const double* x_in, const double* x_out,
+                   double* x_next);
+
 /* Kerker preconditioner of the density mixing (Sec. 5 cites the real-space
  * Kerker preconditioner): out = K r with K(G) = G^2 / (G^2 + k0^2) on the
  * periodic cell's reciprocal vectors (K(0) = 0: the result has zero mean),

@@ -24,6 +24,7 @@
 // for bit.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sq3_internal.cuh"
@@ -309,6 +310,232 @@ int potential_and_terms(sq3_ctx* ctx, const double* rho, const double* b, double
   return check_device_status(ctx);
 }
 
+
+// ---- Periodic Pulay mixing of the density (the mixing Sec. 5 cites) ----
+//
+// State (per context, reset by sq3_mixer_setup and sq3_setup_grid): the
+// previous input and residual, and a ring of up to MIX_MAXH differences
+// dX_a = x_k - x_{k-1}, dF_a = f_k - f_{k-1} (f = x_out - x_in).  Every
+// period-th step the next input is x_bar + beta K f_bar with
+// x_bar = x - DX c, f_bar = f - DF c and c the least-squares solution of
+// DF c ~ f; the other steps mix linearly, x + beta K f.  K is the Kerker
+// preconditioner (identity when k0 <= 0).  c solves the normal equations
+// (DF^T DF) c = DF^T f by a Cholesky factorisation that drops a column whose
+// pivot falls below 1e-12 of its diagonal (a difference that depends
+// linearly on the earlier ones); with a full-rank history that is the
+// least-squares solution, and with a deficient one it is still a
+// least-squares solution (the same f_bar).
+
+constexpr int MIX_MAXH = 8;
+constexpr int MIX_NPAIR = MIX_MAXH * (MIX_MAXH + 1) / 2;
+constexpr int MIX_NQ = MIX_NPAIR + MIX_MAXH;    // Gram entries + right-hand side
+constexpr int MIX_BLOCKS = 304;
+
+struct MixPtrs {
+  const double* dX[MIX_MAXH];
+  const double* dF[MIX_MAXH];
+  int m;
+};
+
+// f = x_out - x_in; with a previous step, dX[slot] = x_in - x_prev and
+// dF[slot] = f - f_prev; then x_prev = x_in, f_prev = f.  Point-wise, each
+// point read before it is written by the same thread (no __restrict__:
+// callers may pass aliased inputs).
+__global__ void mix_prepare_kernel(const double* x_in, const double* x_out, double* xp,
+                                   double* fp, double* dX, double* dF, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double xi = x_in[i];
+    const double f = x_out[i] - xi;
+    if (dX) {
+      dX[i] = xi - xp[i];
+      dF[i] = f - fp[i];
+    }
+    xp[i] = xi;
+    fp[i] = f;
+  }
+}
+
+// Per-block partial sums of dF_a . dF_b (a <= b) and dF_a . f.
+__global__ void __launch_bounds__(256)
+mix_dots_kernel(MixPtrs mp, const double* __restrict__ f, long long N,
+                double* __restrict__ part) {
+  double acc[MIX_NQ];
+#pragma unroll
+  for (int q = 0; q < MIX_NQ; ++q) acc[q] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v[MIX_MAXH];
+#pragma unroll
+    for (int a = 0; a < MIX_MAXH; ++a) v[a] = a < mp.m ? mp.dF[a][i] : 0.0;
+    const double fi = f[i];
+    int q = 0;
+#pragma unroll
+    for (int a = 0; a < MIX_MAXH; ++a)
+#pragma unroll
+      for (int b = a; b < MIX_MAXH; ++b) {
+        acc[q] = fma(v[a], v[b], acc[q]);
+        ++q;
+      }
+#pragma unroll
+    for (int a = 0; a < MIX_MAXH; ++a) acc[MIX_NPAIR + a] = fma(v[a], fi, acc[MIX_NPAIR + a]);
+  }
+  __shared__ double sh[8][MIX_NQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < MIX_NQ; ++q) {
+    double x = acc[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[warp][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < MIX_NQ) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sh[w][threadIdx.x];
+    part[(size_t)blockIdx.x * MIX_NQ + threadIdx.x] = s;
+  }
+}
+
+// Sums the partials in block order, then one thread solves the m x m
+// normal equations; c[a] = 0 for a dropped column.
+__global__ void mix_solve_kernel(const double* __restrict__ part, int m,
+                                 double* __restrict__ c) {
+  __shared__ double tot[MIX_NQ];
+  const int t = threadIdx.x;
+  if (t < MIX_NQ) {
+    double s = 0.0;
+    for (int k = 0; k < MIX_BLOCKS; ++k) s += part[(size_t)k * MIX_NQ + t];
+    tot[t] = s;
+  }
+  __syncthreads();
+  if (t != 0) return;
+  double G[MIX_MAXH][MIX_MAXH], r[MIX_MAXH], L[MIX_MAXH][MIX_MAXH], y[MIX_MAXH];
+  bool keep[MIX_MAXH];
+  int q = 0;
+  for (int a = 0; a < MIX_MAXH; ++a)
+    for (int b = a; b < MIX_MAXH; ++b, ++q) G[a][b] = G[b][a] = tot[q];
+  for (int a = 0; a < MIX_MAXH; ++a) r[a] = tot[MIX_NPAIR + a];
+  for (int j = 0; j < m; ++j) {
+    double d = G[j][j];
+    for (int k = 0; k < j; ++k) if (keep[k]) d -= L[j][k] * L[j][k];
+    keep[j] = d > 1e-12 * G[j][j] && G[j][j] > 0.0;
+    const double ljj = keep[j] ? sqrt(d) : 0.0;
+    L[j][j] = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      double v = G[i][j];
+      for (int k = 0; k < j; ++k) if (keep[k]) v -= L[i][k] * L[j][k];
+      L[i][j] = keep[j] ? v / ljj : 0.0;
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double v = r[i];
+    for (int k = 0; k < i; ++k) if (keep[k]) v -= L[i][k] * y[k];
+    y[i] = keep[i] ? v / L[i][i] : 0.0;
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < m; ++k) if (keep[k]) v -= L[k][i] * c[k];
+    c[i] = keep[i] ? v / L[i][i] : 0.0;
+  }
+}
+
+// x_bar = x_in - sum_a c_a dX_a, f_bar = f - sum_a c_a dF_a (c == null: the
+// linear step, x_bar = x_in, f_bar = f).  Without a preconditioner the next
+// input x_bar + beta f_bar is written; with one, x_bar goes to x_next and
+// f_bar to fbar for the Kerker step.
+__global__ void mix_combine_kernel(MixPtrs mp, const double* c, const double* x_in,
+                                   const double* f, double* x_next, double* fbar,
+                                   double beta, long long N) {
+  double cc[MIX_MAXH];
+#pragma unroll
+  for (int a = 0; a < MIX_MAXH; ++a) cc[a] = (c && a < mp.m) ? c[a] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double xb = x_in[i], fb = f[i];
+#pragma unroll
+    for (int a = 0; a < MIX_MAXH; ++a)
+      if (a < mp.m && c) {
+        xb = fma(-cc[a], mp.dX[a][i], xb);
+        fb = fma(-cc[a], mp.dF[a][i], fb);
+      }
+    if (fbar) {
+      x_next[i] = xb;
+      fbar[i] = fb;
+    } else {
+      x_next[i] = fma(beta, fb, xb);
+    }
+  }
+}
+
+__global__ void axpy_kernel(double* y, const double* __restrict__ x, double a, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// Mixer buffers: x_prev | f_prev | f_bar | dX ring (h) | dF ring (h) |
+// partials | c.
+int mixer_buffers(sq3_ctx* ctx) {
+  const size_t N = (size_t)ctx->grid.N;
+  const size_t words = (3 + 2 * (size_t)ctx->mix.h) * N + (size_t)MIX_BLOCKS * MIX_NQ + MIX_MAXH;
+  return ensure((void**)&ctx->wsMix, &ctx->wsMix_bytes, words * sizeof(double));
+}
+
+int mixer_step(sq3_ctx* ctx, const double* x_in, const double* x_out, double* x_next) {
+  auto& M = ctx->mix;
+  const long long N = ctx->grid.N;
+  double* xp = ctx->wsMix;
+  double* fp = xp + N;
+  double* fbar = fp + N;
+  double* dXr = fbar + N;
+  double* dFr = dXr + (size_t)M.h * N;
+  double* part = dFr + (size_t)M.h * N;
+  double* cbuf = part + (size_t)MIX_BLOCKS * MIX_NQ;
+  cudaStream_t st = ctx->stream;
+  const unsigned blocks = (unsigned)std::min<long long>((N + 255) / 256, 152LL * 8);
+  // ring slot of the new difference (the oldest is overwritten when full)
+  int slot = -1;
+  if (M.have_prev) {
+    if (M.m < M.h) slot = (M.head + M.m) % M.h;
+    else slot = M.head;
+  }
+  mix_prepare_kernel<<<blocks, 256, 0, st>>>(
+      x_in, x_out, xp, fp, slot >= 0 ? dXr + (size_t)slot * N : nullptr,
+      slot >= 0 ? dFr + (size_t)slot * N : nullptr, N);
+  if (slot >= 0) {
+    if (M.m < M.h) ++M.m;
+    else M.head = (M.head + 1) % M.h;
+  }
+  M.have_prev = true;
+  ++M.k;
+  MixPtrs mp{};
+  mp.m = M.m;
+  for (int a = 0; a < M.m; ++a) {
+    const int ph = (M.head + a) % M.h;   // logical order: oldest first
+    mp.dX[a] = dXr + (size_t)ph * N;
+    mp.dF[a] = dFr + (size_t)ph * N;
+  }
+  const bool pulay = M.m > 0 && M.k % M.period == 0;
+  if (pulay) {
+    mix_dots_kernel<<<MIX_BLOCKS, 256, 0, st>>>(mp, fp, N, part);
+    mix_solve_kernel<<<1, 64, 0, st>>>(part, M.m, cbuf);
+  } else {
+    mp.m = 0;
+  }
+  const bool precond = M.k0 > 0.0;
+  mix_combine_kernel<<<blocks, 256, 0, st>>>(mp, pulay ? cbuf : nullptr, x_in, fp, x_next,
+                                             precond ? fbar : nullptr, M.beta, N);
+  if (precond) {
+    int rc = ensure_tables(ctx);
+    if (rc) return rc;
+    double *A, *B, *p2, *res;
+    rc = scf_scratch(ctx, &A, &B, &p2, &res);
+    if (rc) return rc;
+    spectral_apply(ctx, fbar, nullptr, fbar, SCALE_KERKER, M.k0 * M.k0, A, B);
+    axpy_kernel<<<blocks, 256, 0, st>>>(x_next, fbar, M.beta, N);
+  }
+  return cuda_err(cudaGetLastError());
+}
 }  // namespace
 
 }  // namespace sq3
@@ -329,6 +556,37 @@ int sq3_poisson(sq3_ctx* c, const double* rho, const double* b, double* phi) {
   if (rc) return rc;
   spectral_apply(c, rho, b, phi, SCALE_POISSON, 0.0, A, B);
   rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  rc = cuda_err(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  return check_device_status(c);
+}
+
+int sq3_mixer_setup(sq3_ctx* c, int history, int period, double beta, double k0) {
+  int rc = check_grid(c);
+  if (rc) return rc;
+  if (history < 1 || history > MIX_MAXH || period < 1 || !(beta > 0) || !isfinite(beta) ||
+      !isfinite(k0))
+    return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  c->mix = sq3_ctx::MixState{};
+  c->mix.h = history;
+  c->mix.period = period;
+  c->mix.beta = beta;
+  c->mix.k0 = k0 > 0 ? k0 : 0.0;
+  rc = mixer_buffers(c);
+  if (rc) return rc;
+  c->mix.ready = true;
+  return SQ3_OK;
+}
+
+int sq3_mixer_step(sq3_ctx* c, const double* x_in, const double* x_out, double* x_next) {
+  int rc = check_grid(c);
+  if (rc) return rc;
+  if (!c->mix.ready) return SQ3_ENOTSETUP;
+  if (!x_in || !x_out || !x_next) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  rc = mixer_step(c, x_in, x_out, x_next);
   if (rc) return rc;
   rc = cuda_err(cudaStreamSynchronize(c->stream));
   if (rc) return rc;

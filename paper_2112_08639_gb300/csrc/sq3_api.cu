@@ -392,7 +392,7 @@ void sq3_destroy(sq3_ctx* c) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
                   c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32,
-                  c->scfTab, c->wsScf};
+                  c->scfTab, c->wsScf, c->wsMix};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   delete c;
@@ -419,6 +419,7 @@ int sq3_setup_grid(sq3_ctx* c, int nx, int ny, int nz, double Lx, double Ly,
   c->grid_ok = true;
   c->pot_ok = false;
   c->scf_tab_ok = false;
+  c->mix.ready = false;
   if (c->V) cudaFree(c->V);
   if (c->Vf) cudaFree(c->Vf);
   c->V = nullptr; c->Vf = nullptr;

@@ -117,6 +117,15 @@ struct sq3_ctx {
   double* scfTab = nullptr; size_t scfTab_bytes = 0;
   bool scf_tab_ok = false;
   double* wsScf = nullptr; size_t wsScf_bytes = 0;
+  // density mixer (sq3_mixer_setup / sq3_mixer_step): settings, step count
+  // and the ring of history differences in wsMix
+  struct MixState {
+    bool ready = false, have_prev = false;
+    int h = 0, period = 1, m = 0, head = 0;
+    long long k = 0;
+    double beta = 0.0, k0 = 0.0;
+  } mix;
+  double* wsMix = nullptr; size_t wsMix_bytes = 0;
   // uploads of a host block (sq3_cheb_filter_from_host): a stream of their
   // own and one event per chunk, created on first use
   cudaStream_t copy_stream = nullptr;

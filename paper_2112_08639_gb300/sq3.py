@@ -56,6 +56,8 @@ _sigs = {
     "sq3_effective_potential": (_i, [_p, _p, _p, _p, _p, _p]),
     "sq3_free_energy": (_i, [_p, _p, _p, _d, _d, _d, _p]),
     "sq3_kerker": (_i, [_p, _p, _p, _d]),
+    "sq3_mixer_setup": (_i, [_p, _i, _i, _d, _d]),
+    "sq3_mixer_step": (_i, [_p, _p, _p, _p]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -263,6 +265,18 @@ class Context:
             out = torch.empty_like(r)
         _check(lib.sq3_kerker(self._h, self._grid_vec(r), self._grid_vec(out), k0), "sq3_kerker")
         return out
+
+    def mixer_setup(self, history: int = 7, period: int = 2, beta: float = 0.3,
+                    k0: float = 0.8):
+        _check(lib.sq3_mixer_setup(self._h, history, period, beta, k0), "sq3_mixer_setup")
+
+    def mixer_step(self, x_in: torch.Tensor, x_out: torch.Tensor,
+                   x_next: torch.Tensor | None = None) -> torch.Tensor:
+        if x_next is None:
+            x_next = torch.empty_like(x_in)
+        _check(lib.sq3_mixer_step(self._h, self._grid_vec(x_in), self._grid_vec(x_out),
+                                  self._grid_vec(x_next)), "sq3_mixer_step")
+        return x_next
 
     STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
               "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy", "nl_pass")
