@@ -31,6 +31,9 @@ What it computes, and where the paper defines it:
                      preconditioned periodic Pulay mixing (cited in Sec. 5)
                      and the free energy (Eq. (ON:FreeEnergy),
                      Eq. (FreeEnergy:NewForm)).
+* ``forces``      -- Hellmann-Feynman forces on the nuclei, Eq. (force:NewForm)
+                     (Sec. 3; Eq. (ON:forces) in Sec. 2): the pseudocharge
+                     term and the nonlocal term in the paper's form.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, library routines or brute force; none is marked "parity

@@ -7,8 +7,11 @@ TEST INFRASTRUCTURE ONLY, like the rest of this package: only ``tests/``
 
 * ``pseudocharge``  -- b = sum_J b_J with b_J(r) = -Z exp(-r^2/rc^2) /
                        (pi^(3/2) rc^3), the pseudocharge whose potential is
-                       the local pseudopotential (Sec. 2, Eq. (poisson)), by
-                       minimum image, rescaled so that sum b dV = -N_e.
+                       the local pseudopotential (Sec. 2, Eq. (poisson)),
+                       summed over each atom and its periodic images (as
+                       the force expression of Eq. (ON:forces) sums them),
+                       rescaled so that sum b dV = -N_e; and its gradients
+                       grad_x b_J for the forces.
 * ``poisson_fd``    -- phi with -L_h phi / (4 pi) = rho + b (Sec. 2,
                        Eq. (poisson)), L_h the finite-difference Laplacian of
                        the Hamiltonian, solved in Fourier space through its
@@ -54,29 +57,56 @@ def _grid3(n: int):
     return np.meshgrid(m, m, m, indexing="ij")
 
 
+def _periodic_gaussian_1d(n: int, L: float, r0: float, rc: float, deriv: bool = False):
+    """sum over images m of exp(-(x - r0 - m L)^2 / rc^2) at the n grid
+    points x = k L / n (or its x-derivative); images while the term can
+    exceed 1e-300 of the peak."""
+    x = np.arange(n) * (L / n)
+    kmax = int(np.ceil(27.0 * rc / L)) + 1
+    g = np.zeros(n)
+    for m in range(-kmax, kmax + 1):
+        d = x - r0 - m * L
+        e = np.exp(-d * d / (rc * rc))
+        g += (-2.0 * d / (rc * rc)) * e if deriv else e
+    return g
+
+
 def pseudocharge(n: int, L: float, positions: np.ndarray, Z: float, rc: float,
                  Ne: float | None = None) -> tuple[np.ndarray, float]:
-    """Gaussian pseudocharges on the grid (length n^3, grid order), and the
-    sum b dV before rescaling.  Minimum image while r < 10 rc; with Ne the
-    array is rescaled so that its sum times dV is exactly -Ne."""
+    """Gaussian pseudocharges on the grid (length n^3, grid order), summed
+    over every atom and all its periodic images (the Gaussian factorises by
+    axis, so each axis is summed over images), and the sum b dV before
+    rescaling.  With Ne the array is rescaled so that its sum times dV is
+    exactly -Ne (the factor differs from 1 by the grid's aliasing of the
+    Gaussian, below 1e-9 for h < 0.7 rc)."""
     h = L / n
-    idx = np.arange(n) * h
-    z, y, x = np.meshgrid(idx, idx, idx, indexing="ij")
     b = np.zeros((n, n, n))
     norm = -Z / (np.pi ** 1.5 * rc ** 3)
     for R in positions:
-        d2 = np.zeros_like(x)
-        for comp, r0 in zip((x, y, z), R):
-            d = comp - r0
-            d -= L * np.round(d / L)
-            d2 += d * d
-        b += np.where(d2 < (10 * rc) ** 2, norm * np.exp(-d2 / rc ** 2), 0.0)
+        gx, gy, gz = (_periodic_gaussian_1d(n, L, R[a], rc) for a in range(3))
+        b += norm * np.einsum("l,j,i->lji", gz, gy, gx)
     b = b.ravel()
     dV = h ** 3
     total = float(b.sum() * dV)
     if Ne is not None:
         b *= -Ne / total
     return b, total
+
+
+def pseudocharge_gradients(n: int, L: float, positions: np.ndarray, Z: float, rc: float,
+                           scale: float = 1.0) -> np.ndarray:
+    """grad_x b_I on the grid for each atom I (with its periodic images):
+    array (natoms, 3, n^3), times `scale` (the rescaling factor of
+    ``pseudocharge``)."""
+    norm = scale * -Z / (np.pi ** 1.5 * rc ** 3)
+    out = np.zeros((len(positions), 3, n ** 3))
+    for I, R in enumerate(positions):
+        g = [_periodic_gaussian_1d(n, L, R[a], rc) for a in range(3)]
+        dg = [_periodic_gaussian_1d(n, L, R[a], rc, deriv=True) for a in range(3)]
+        out[I, 0] = norm * np.einsum("l,j,i->lji", g[2], g[1], dg[0]).ravel()
+        out[I, 1] = norm * np.einsum("l,j,i->lji", g[2], dg[1], g[0]).ravel()
+        out[I, 2] = norm * np.einsum("l,j,i->lji", dg[2], g[1], g[0]).ravel()
+    return out
 
 
 def fd_symbol(n: int, order: int = 12) -> np.ndarray:

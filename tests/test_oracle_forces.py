@@ -1,0 +1,194 @@
+"""Pins of the force oracle (``oracle.forces``, Eq. (force:NewForm)): the
+first-derivative FD weights against their exact rational moments, the grid
+gradient against its closed-form symbol and discrete antisymmetry, the
+pseudocharge gradients against central differences of the pseudocharges in
+R, and the forces against -dF/dR by central differences of the oracle's
+self-consistent free energy (local part alone, and with smooth projectors).
+The nonlocal term follows the paper's form, with the gradient on the
+kernel-transformed functions; on the grid it differs from the exact
+derivative (gradient on the projector, analytic) by the FD truncation of
+that gradient, which a separate pin measures and bounds."""
+import functools
+from fractions import Fraction
+from math import factorial
+
+import numpy as np
+
+from oracle import fermi, forces, scf
+from paper_2112_08639_gb300 import inputs
+
+N_GRID, NS = 12, 57                   # a 4-atom cell; Ns at a spectral gap
+SIGMA = inputs.ev_to_ha(10.0)
+Z, RC = inputs.Z_VALENCE, inputs.RC_LOCAL
+L = inputs.A0_FCC
+DV = (L / N_GRID) ** 3
+POS = inputs.fcc_positions(1, disp_sigma=0.05, seed=0)
+
+
+def test_first_derivative_weights_exact_moments():
+    """sum_p a_p (p^k - (-p)^k) = [k == 1] for k = 0..order, not k = order + 1."""
+    for order in (2, 4, 8, 12):
+        n = order // 2
+        a = [Fraction((-1) ** (p + 1) * factorial(n) ** 2,
+                      p * factorial(n - p) * factorial(n + p)) for p in range(1, n + 1)]
+        for k in range(order + 1):
+            m = sum(ap * (Fraction(p) ** k - Fraction(-p) ** k) for p, ap in enumerate(a, 1))
+            assert m == (1 if k == 1 else 0), (order, k)
+        m = sum(ap * (Fraction(p) ** (order + 1) - Fraction(-p) ** (order + 1))
+                for p, ap in enumerate(a, 1))
+        assert m != 0
+        np.testing.assert_allclose(forces.fd_first_weights(order), [float(x) for x in a],
+                                   rtol=1e-15)
+
+
+def test_gradient_symbol_and_antisymmetry():
+    n, Lc = 10, 6.0
+    h = Lc / n
+    a = forces.fd_first_weights(12)
+    idx = np.arange(n ** 3)
+    ix, iy, iz = idx % n, (idx // n) % n, idx // (n * n)
+    m = (1, 2, 3)
+    theta = [2 * np.pi * mm / n for mm in m]
+    wave = np.sin(theta[0] * ix + theta[1] * iy + theta[2] * iz)
+    G = forces.gradient_fd(wave, n, Lc)
+    cosw = np.cos(theta[0] * ix + theta[1] * iy + theta[2] * iz)
+    for comp in range(3):
+        sym = 2.0 * sum(w * np.sin(p * theta[comp]) for p, w in enumerate(a, 1)) / h
+        np.testing.assert_allclose(G[comp], sym * cosw, atol=1e-12)
+    rng = np.random.default_rng(0)
+    f, g = rng.normal(size=(2, n ** 3))
+    Gf, Gg = forces.gradient_fd(f, n, Lc), forces.gradient_fd(g, n, Lc)
+    for comp in range(3):
+        assert abs(Gf[comp] @ g + f @ Gg[comp]) < 1e-11 * np.abs(Gf[comp] @ g).max()
+
+
+def test_pseudocharge_gradients_are_minus_the_r_derivative():
+    g = scf.pseudocharge_gradients(N_GRID, L, POS, Z, RC)
+    d = 1e-5
+    for I, a in ((1, 2), (3, 0)):
+        p, q = POS.copy(), POS.copy()
+        p[I, a] += d
+        q[I, a] -= d
+        bp, _ = scf.pseudocharge(N_GRID, L, p, Z, RC)
+        bq, _ = scf.pseudocharge(N_GRID, L, q, Z, RC)
+        np.testing.assert_allclose(-(bp - bq) / (2 * d), g[I, a], atol=1e-9 * np.abs(g[I, a]).max())
+
+
+def _img1d(x, r0, rp, kind):
+    """Sum over images of e = exp(-d^2/rp^2) (kind 0), d e (1), d/dx e (2),
+    d/dx (d e) (3), d = x - r0 - m L."""
+    out = np.zeros_like(x)
+    for m in range(-4, 5):
+        d = x - r0 - m * L
+        e = np.exp(-d * d / (rp * rp))
+        out += (e, d * e, -2 * d / (rp * rp) * e, (1 - 2 * d * d / (rp * rp)) * e)[kind]
+    return out
+
+
+def _smooth_projectors(pos, rp, with_grad=False):
+    """s and p Gaussian projectors per atom over every grid point (no cutoff,
+    periodic images, analytic continuum normalisation): smooth in R, so the
+    free energy is differentiable in the positions.  Optionally their
+    analytic x, y, z derivatives."""
+    n = N_GRID
+    x = np.arange(n) * (L / n)
+    ns = (np.pi * rp * rp / 2) ** -0.75
+    npp = ns * 2.0 / rp
+    ptr, idx, val, gam, grads = [0], [], [], [], []
+    for R in pos:
+        def prod(kx, ky, kz):
+            return np.einsum("l,j,i->lji", _img1d(x, R[2], rp, kz), _img1d(x, R[1], rp, ky),
+                             _img1d(x, R[0], rp, kx)).ravel()
+        for kinds, nrm, g in (((0, 0, 0), ns, 0.5), ((1, 0, 0), npp, 0.3),
+                              ((0, 1, 0), npp, 0.3), ((0, 0, 1), npp, 0.3)):
+            idx.append(np.arange(n ** 3, dtype=np.int32))
+            val.append(nrm * prod(*kinds))
+            gam.append(g)
+            ptr.append(ptr[-1] + n ** 3)
+            if with_grad:
+                gr = []
+                for a in range(3):
+                    k = list(kinds)
+                    k[a] = {0: 2, 1: 3}[k[a]]
+                    gr.append(nrm * prod(*k))
+                grads.append(np.stack(gr))
+    table = inputs.ProjectorTable(np.asarray(ptr, np.int32), np.concatenate(idx),
+                                  np.concatenate(val), np.asarray(gam))
+    return (table, grads) if with_grad else table
+
+
+@functools.lru_cache(maxsize=None)
+def _scf(rp, shift=None):
+    pos = POS.copy()
+    if shift is not None:
+        I, a, d = shift
+        pos[I, a] += d
+    proj = _smooth_projectors(pos, rp) if rp else None
+    rho0 = _scf(rp)["rho"] if shift is not None else None
+    return scf.scf(N_GRID, L, pos, Ns=NS, sigma=SIGMA, Z=Z, rc=RC, proj=proj, rho0=rho0,
+                   tol=1e-12)
+
+
+def _hf_forces(rp):
+    res = _scf(rp)
+    _, tot = scf.pseudocharge(N_GRID, L, POS, Z, RC)
+    gb = scf.pseudocharge_gradients(N_GRID, L, POS, Z, RC, scale=-12.0 / tot)
+    phi = scf.poisson_fd(res["rho"] + res["b"], N_GRID, L)
+    f = forces.local_forces(gb, phi, DV)
+    if rp:
+        g = fermi.fermi(res["lam"], res["mu"], SIGMA)
+        f = f + forces.nonlocal_forces(res["U"], np.diag(g), _smooth_projectors(POS, rp),
+                                       N_GRID, L, len(POS))
+    return f
+
+
+def _fd_force(rp, I, a, d=1e-3):
+    return -(_scf(rp, (I, a, d))["F"] - _scf(rp, (I, a, -d))["F"]) / (2 * d)
+
+
+def test_local_force_is_minus_the_derivative_of_the_free_energy():
+    """No projectors: the pseudocharge term alone (f_sc = 0).  Measured
+    agreement 5e-10..1.2e-9 Ha/bohr on forces of ~1e-3."""
+    f = _hf_forces(0.0)
+    assert abs(_fd_force(0.0, 1, 2) - f[1, 2]) < 1e-8
+    assert np.abs(f).max() > 1e-3
+
+
+def test_force_with_projectors_is_minus_the_derivative_of_the_free_energy():
+    """Smooth projectors (width 1.6 bohr): the paper's form of the nonlocal
+    term agrees with -dF/dR to the FD truncation of its gradient (4e-8
+    measured against a nonlocal part of 4e-4; evaluated with the analytic
+    gradient on the projector instead, the same force agreed to 1e-9 when
+    this pin was set up; the next pin bounds the difference of the two
+    forms directly)."""
+    f = _hf_forces(1.6)
+    assert abs(_fd_force(1.6, 1, 2) - f[1, 2]) < 2e-7
+
+
+def test_nonlocal_paper_form_against_the_exact_derivative():
+    """For any orthonormal X and symmetric Ds, the paper's form
+    -4 sum gamma (c . u_i)(c . grad_h u~_i) and the exact derivative
+    +4 sum gamma (c . u~_i)(grad c . u_i) (gradient on the projector,
+    analytic) differ only by the FD truncation of grad_h on the projector
+    (by the discrete antisymmetry of grad_h and the symmetry of X Ds X^T).
+    With a random subspace (all frequencies present) the relative gap is
+    1.8e-3, 2.5e-4, 3.4e-5 for widths 1.6, 2.0, 2.4 bohr: it falls as the
+    projector gets smoother; a sign, axis or pairing mistake would be O(1)."""
+    rng = np.random.default_rng(1)
+    X, _ = np.linalg.qr(rng.normal(size=(N_GRID ** 3, 20)))
+    A = rng.normal(size=(20, 20))
+    Ds = (A + A.T) / 40
+
+    def both(width):
+        table, grads = _smooth_projectors(POS, width, with_grad=True)
+        paper = forces.nonlocal_forces(X, Ds, table, N_GRID, L, len(POS))
+        exact = np.zeros_like(paper)
+        Xt = X @ Ds
+        for p in range(len(table.gamma)):
+            c = table.val[table.ptr[p]:table.ptr[p + 1]] * np.sqrt(DV)
+            for a in range(3):
+                exact[p // 4, a] += 4 * table.gamma[p] * float((c @ Xt) @ (grads[p][a] * np.sqrt(DV) @ X))
+        return np.abs(paper - exact).max() / np.abs(exact).max()
+
+    e = [both(w) for w in (1.6, 2.0, 2.4)]
+    assert e[0] < 5e-3 and e[1] < e[0] / 4 and e[2] < e[1] / 4
