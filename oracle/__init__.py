@@ -34,6 +34,8 @@ What it computes, and where the paper defines it:
 * ``forces``      -- Hellmann-Feynman forces on the nuclei, Eq. (force:NewForm)
                      (Sec. 3; Eq. (ON:forces) in Sec. 2): the pseudocharge
                      term and the nonlocal term in the paper's form.
+* ``qmd``         -- velocity-Verlet dynamics of the nuclei on those forces,
+                     with the isokinetic option of the paper's QMD (Sec. 5).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, library routines or brute force; none is marked "parity
