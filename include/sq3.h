@@ -310,6 +310,21 @@ int sq3_profile_read(sq3_ctx* ctx, double* ms, long long* launches,
 int sq3_lanczos_bounds_noalloc(const double* Hs, int Ns, double* bounds,
                                void* cuda_stream);
 
+/* Degree of the Chebyshev expansion of the Fermi function (Sec. 4,
+ * Eq. (ChebyshevExpansion); Sec. 5 notes that the degree needed falls as the
+ * temperature rises).  Host-only arithmetic, no GPU work: the Fermi function
+ * of width sigma (Ha) is analytic except at its poles mu +- i pi sigma (2k + 1),
+ * so on [chi - xi, chi + xi] its Chebyshev coefficients decay at least like
+ * rho^-j, rho = a + sqrt(1 + a^2), a = pi sigma / xi (the Bernstein ellipse
+ * through the nearest pole, for mu anywhere in the interval).  Returns
+ * ceil(ln(1 / tol) / ln rho), at least 1: the degree at which the expansion
+ * error of the occupations is below tol for every mu in the interval.
+ * xi: half-width of the spectrum of Hs (the xi sq3_kernel_from_hs reports);
+ * tol in (0, 1).  Degrees above 1000 exceed what sq3_kernel_from_hs accepts.
+ * Errors: SQ3_EINVAL (sigma <= 0, xi <= 0, tol outside (0, 1), or a degree
+ * beyond 2^31). */
+int sq3_fermi_degree(double sigma, double xi, double tol);
+
 /* Human-readable name of a status code (static string). */
 const char* sq3_status_string(int status);
 

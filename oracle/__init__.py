@@ -34,6 +34,10 @@ What it computes, and where the paper defines it:
 * ``forces``      -- Hellmann-Feynman forces on the nuclei, Eq. (force:NewForm)
                      (Sec. 3; Eq. (ON:forces) in Sec. 2): the pseudocharge
                      term and the nonlocal term in the paper's form.
+* ``degree``      -- the minimal Chebyshev degree of the Fermi-operator
+                     expansion for a tolerance on the occupations, by brute
+                     force over the Fermi level (Sec. 4; the trend with
+                     temperature in Sec. 5).
 * ``qmd``         -- velocity-Verlet dynamics of the nuclei on those forces,
                      with the isokinetic option of the paper's QMD (Sec. 5).
 

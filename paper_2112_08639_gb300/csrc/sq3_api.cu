@@ -339,6 +339,17 @@ const char* sq3_version(void) { return "sq3-gb300 0.1 (sm_103a)"; }
 
 const char* sq3_last_cuda_error(void) { return g_last_cuda_error; }
 
+int sq3_fermi_degree(double sigma, double xi, double tol) {
+  if (!(sigma > 0) || !(xi > 0) || !(tol > 0) || !(tol < 1) || !isfinite(sigma) ||
+      !isfinite(xi))
+    return SQ3_EINVAL;
+  const double a = M_PI * sigma / xi;
+  const double lr = log(a + sqrt(1.0 + a * a));   // ln rho > 0
+  const double n = ceil(log(1.0 / tol) / lr);
+  if (!(n < 2147483647.0)) return SQ3_EINVAL;
+  return n < 1.0 ? 1 : (int)n;
+}
+
 const char* sq3_status_string(int s) {
   switch (s) {
     case SQ3_OK: return "ok";

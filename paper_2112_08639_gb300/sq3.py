@@ -58,6 +58,7 @@ _sigs = {
     "sq3_kerker": (_i, [_p, _p, _p, _d]),
     "sq3_mixer_setup": (_i, [_p, _i, _i, _d, _d]),
     "sq3_mixer_step": (_i, [_p, _p, _p, _p]),
+    "sq3_fermi_degree": (_i, [_d, _d, _d]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -93,6 +94,15 @@ def _prec_dtype(prec: int):
 
 def version() -> str:
     return lib.sq3_version().decode()
+
+
+def fermi_degree(sigma: float, xi: float, tol: float) -> int:
+    """Chebyshev degree for the Fermi function of width sigma on a spectrum of
+    half-width xi with occupation error below tol (host arithmetic only)."""
+    n = lib.sq3_fermi_degree(sigma, xi, tol)
+    if n < 0:
+        raise SQ3Error(n, "sq3_fermi_degree")
+    return n
 
 
 NOALLOC_MAX_NS = 8192
