@@ -343,7 +343,7 @@ int sq3_fermi_degree(double sigma, double xi, double tol) {
   if (!(sigma > 0) || !(xi > 0) || !(tol > 0) || !(tol < 1) || !isfinite(sigma) ||
       !isfinite(xi))
     return SQ3_EINVAL;
-  const double a = M_PI * sigma / xi;
+  const double a = 3.14159265358979323846 * sigma / xi;
   const double lr = log(a + sqrt(1.0 + a * a));   // ln rho > 0
   const double n = ceil(log(1.0 / tol) / lr);
   if (!(n < 2147483647.0)) return SQ3_EINVAL;
