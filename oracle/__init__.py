@@ -38,6 +38,9 @@ What it computes, and where the paper defines it:
                      expansion for a tolerance on the occupations, by brute
                      force over the Fermi level (Sec. 4; the trend with
                      temperature in Sec. 5).
+* ``guess``       -- starting densities for the SCF: uniform, atomic
+                     superposition, and a small learned model (not in the
+                     paper; the comparison the learned guess is built for).
 * ``qmd``         -- velocity-Verlet dynamics of the nuclei on those forces,
                      with the isokinetic option of the paper's QMD (Sec. 5).
 

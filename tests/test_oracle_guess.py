@@ -1,0 +1,87 @@
+"""Pins of the initial-density oracle (``oracle.guess``): the descriptors are
+periodic and move with the atoms, the training gradient equals central
+differences of the loss, the prediction carries exactly N_e electrons, and on
+held-out cells the learned density is far closer to the self-consistent one
+than the uniform and the best-width atomic-superposition starts, and the
+SCF started from it needs fewer iterations."""
+import functools
+
+import numpy as np
+
+from oracle import guess, scf
+from paper_2112_08639_gb300 import inputs
+
+N_GRID, NS = 12, 40
+L = inputs.A0_FCC
+DV = (L / N_GRID) ** 3
+NE = 12.0
+SIGMA = inputs.ev_to_ha(10.0)
+Z, RC = inputs.Z_VALENCE, inputs.RC_LOCAL
+
+
+def _pos(seed):
+    return inputs.fcc_positions(1, disp_sigma=0.25, seed=seed)
+
+
+@functools.lru_cache(maxsize=None)
+def _scf(seed, start="uniform"):
+    pos = _pos(seed)
+    rho0 = None
+    if start == "superposition":
+        rho0 = guess.superposition(N_GRID, L, pos, NE, _model()[1])
+    elif start == "learned":
+        rho0 = guess.predict(_model()[0], guess.descriptors(N_GRID, L, pos), NE, DV)
+    return scf.scf(N_GRID, L, pos, Ns=NS, sigma=SIGMA, Z=Z, rc=RC, rho0=rho0, tol=1e-8)
+
+
+@functools.lru_cache(maxsize=None)
+def _model():
+    seeds = (1, 2, 3, 4)
+    data = [(guess.descriptors(N_GRID, L, _pos(s)), _scf(s)["rho"]) for s in seeds]
+    p = guess.train(data, NE, DV)
+    w = guess.fit_superposition_width([(_pos(s), _scf(s)["rho"]) for s in seeds], N_GRID, L, NE)
+    return p, w
+
+
+def test_descriptors_are_periodic_and_move_with_the_atoms():
+    pos = _pos(5)
+    D = guess.descriptors(N_GRID, L, pos)
+    shifted = pos.copy()
+    shifted[2] += np.array([L, -L, 2 * L])             # an image of atom 2
+    np.testing.assert_allclose(guess.descriptors(N_GRID, L, shifted), D, rtol=1e-12, atol=1e-14)
+    h = L / N_GRID
+    Dx = guess.descriptors(N_GRID, L, pos + np.array([h, 0.0, 0.0]))
+    rolled = np.roll(D.reshape(N_GRID, N_GRID, N_GRID, -1), 1, axis=2).reshape(D.shape)
+    np.testing.assert_allclose(Dx, rolled, rtol=1e-12, atol=1e-14)
+
+
+def test_training_gradient_and_normalisation():
+    rng = np.random.default_rng(0)
+    data = [(guess.descriptors(N_GRID, L, _pos(s)), rng.uniform(0.01, 0.2, N_GRID ** 3))
+            for s in (6, 7)]
+    p = rng.normal(size=guess.n_params()) * 0.3
+    _, g = guess.loss_and_grad(p, data, NE, DV)
+    for k in (0, 17, guess.n_params() - 5, guess.n_params() - 1):
+        e = np.zeros_like(p)
+        e[k] = 1e-6
+        fd = (guess.loss_and_grad(p + e, data, NE, DV)[0]
+              - guess.loss_and_grad(p - e, data, NE, DV)[0]) / 2e-6
+        assert abs(fd - g[k]) < 1e-6 * max(1.0, abs(g[k])), k
+    r = guess.predict(p, data[0][0], NE, DV)
+    assert abs(r.sum() * DV - NE) < 1e-12 and np.all(r > 0)
+
+
+def test_learned_density_beats_uniform_and_superposition_on_held_out_cells():
+    p, w = _model()
+    assert 1.0 < w < 3.5
+    for seed in (11, 12):
+        ref = _scf(seed)["rho"]
+        pos = _pos(seed)
+        l1 = lambda r: np.abs(r - ref).sum() * DV / NE
+        e_u = l1(guess.uniform(N_GRID, L, NE))
+        e_s = l1(guess.superposition(N_GRID, L, pos, NE, w))
+        e_l = l1(guess.predict(p, guess.descriptors(N_GRID, L, pos), NE, DV))
+        assert e_l < 0.1 * min(e_u, e_s), (e_l, e_s, e_u)
+    it = {s: _scf(11, s)["iterations"] for s in ("uniform", "superposition", "learned")}
+    assert it["learned"] < min(it["uniform"], it["superposition"]), it
+    np.testing.assert_allclose(_scf(11, "learned")["rho"], _scf(11)["rho"], atol=1e-6)
