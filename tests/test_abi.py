@@ -55,3 +55,55 @@ def test_status_strings_and_version(libpath):
 def test_built_for_sm_103a():
     from paper_2112_08639_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_argument_errors_before_any_device_work(libpath):
+    """Every entry point checks its context and arguments before touching
+    the device: with a NULL context, NULL arrays or out-of-range sizes each
+    returns its documented status, here on a host without a GPU."""
+    lib = ctypes.CDLL(libpath)
+    p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    EINVAL, ENOTSETUP, ECUDA = -1, -2, -3
+    h = ctypes.c_void_p(1)
+    lib.sq3_create.argtypes = [ctypes.POINTER(p), i, p]
+    assert lib.sq3_create(None, 0, None) == EINVAL
+    assert lib.sq3_create(ctypes.byref(h), -1, None) == EINVAL and h.value is None
+    assert lib.sq3_create(ctypes.byref(h), 0, None) == ECUDA and h.value is None   # no GPU here
+    lib.sq3_destroy.argtypes = [p]
+    lib.sq3_destroy(None)
+    calls = {
+        "sq3_setup_grid": ([p, i, i, i, d, d, d, i], (None, 8, 8, 8, 1.0, 1.0, 1.0, 12), EINVAL),
+        "sq3_set_potential": ([p, p], (None, None), ENOTSETUP),
+        "sq3_set_projectors": ([p, i, p, p, p, p], (None, 0, None, None, None, None), ENOTSETUP),
+        "sq3_hamiltonian_apply": ([p, p, p, i, i], (None, None, None, 4, 0), ENOTSETUP),
+        "sq3_cheb_filter": ([p, p, i, i, d, d, d, i], (None, None, 4, 3, 1.0, 2.0, 0.0, 0),
+                            ENOTSETUP),
+        "sq3_cheb_filter_from_host": ([p, p, p, i, i, d, d, d, i],
+                                      (None, None, None, 4, 3, 1.0, 2.0, 0.0, 0), ENOTSETUP),
+        "sq3_orthonormalise": ([p, p, i, i], (None, None, 4, 0), ENOTSETUP),
+        "sq3_project": ([p, p, i, i, p], (None, None, 4, 0, None), ENOTSETUP),
+        "sq3_kernel_from_hs": ([p, p, i, i, d, d, i, p, p, p],
+                               (None, None, 4, 10, 0.3, 2.0, 0, None, None, None), EINVAL),
+        "sq3_density_kernel": ([p, p, i, i, d, d, i, p, p, p, p],
+                               (None, None, 4, 10, 0.3, 2.0, 0, None, None, None, None), ENOTSETUP),
+        "sq3_density": ([p, p, p, i, i, p], (None, None, None, 4, 0, None), ENOTSETUP),
+        "sq3_selftest_timeout": ([p], (None,), EINVAL),
+        "sq3_profile_enable": ([p, i], (None, 1), EINVAL),
+        "sq3_profile_read": ([p, p, p, i], (None, None, None, 0), EINVAL),
+        "sq3_lanczos_bounds_noalloc": ([p, i, p, p], (None, 4, None, None), EINVAL),
+        "sq3_poisson": ([p, p, p, p], (None, None, None, None), EINVAL),
+        "sq3_effective_potential": ([p, p, p, p, p, p], (None,) * 6, EINVAL),
+        "sq3_free_energy": ([p, p, p, d, d, d, p], (None, None, None, 0.0, 0.0, 0.0, None), EINVAL),
+        "sq3_kerker": ([p, p, p, d], (None, None, None, 0.8), EINVAL),
+        "sq3_mixer_setup": ([p, i, i, d, d], (None, 7, 2, 0.3, 0.8), EINVAL),
+        "sq3_mixer_step": ([p, p, p, p], (None, None, None, None), EINVAL),
+    }
+    for name, (argtypes, args, want) in calls.items():
+        f = getattr(lib, name)
+        f.argtypes = argtypes
+        f.restype = i
+        assert f(*args) == want, name
+    missing = set(declared_symbols()) - set(calls) - {
+        "sq3_create", "sq3_destroy", "sq3_status_string", "sq3_version", "sq3_last_cuda_error",
+        "sq3_fermi_degree"}
+    assert not missing, missing
