@@ -192,3 +192,25 @@ def test_nonlocal_paper_form_against_the_exact_derivative():
 
     e = [both(w) for w in (1.6, 2.0, 2.4)]
     assert e[0] < 5e-3 and e[1] < e[0] / 4 and e[2] < e[1] / 4
+
+
+def test_nonlocal_force_through_the_projector_gradient():
+    """The discrete identity a device kernel can use: because grad_h is
+    antisymmetric and X Ds X^T symmetric, the paper's form equals
+    +4 sum_p gamma_p (c_p^T X) Ds (X^T grad_h c_p) to rounding, for any
+    projectors (here the inputs' own, with their cutoff) and any X, Ds."""
+    rng = np.random.default_rng(2)
+    table = inputs.projectors(N_GRID, L, POS, seed=4, rcut=3.0)
+    X, _ = np.linalg.qr(rng.normal(size=(N_GRID ** 3, 16)))
+    A = rng.normal(size=(16, 16))
+    Ds = (A + A.T) / 32
+    paper = forces.nonlocal_forces(X, Ds, table, N_GRID, L, len(POS))
+    alt = np.zeros_like(paper)
+    for p in range(len(table.gamma)):
+        c = np.zeros(N_GRID ** 3)
+        c[table.idx[table.ptr[p]:table.ptr[p + 1]]] = table.val[table.ptr[p]:table.ptr[p + 1]] * np.sqrt(DV)
+        gc = forces.gradient_fd(c, N_GRID, L)
+        for a in range(3):
+            alt[p // 4, a] += 4 * table.gamma[p] * float((c @ X) @ Ds @ (X.T @ gc[a]))
+    np.testing.assert_allclose(alt, paper, rtol=1e-11, atol=1e-13 * np.abs(paper).max())
+    assert np.abs(paper).max() > 1e-4
