@@ -141,3 +141,37 @@ def test_scf_small_cell_converges_and_f_matches_the_direct_route():
     e_h = 0.5 * float(np.sum((res["rho"] + res["b"]) * phi) * dV)
     F_direct = (t_s + float(np.sum(exc * res["rho"]) * dV) + e_h - res["e_self"] + res["e_ent"])
     assert abs(res["F"] - F_direct) < 1e-9 * abs(res["F"])      # 2.6e-11 seen
+
+
+def test_kerker_preconditioned_pulay_reaches_the_fixed_point():
+    """A mean-preserving linear contraction on a grid, x -> x0_mean + S (x -
+    mean) + c with c of zero mean, S a smoothing operator diagonal in Fourier
+    space (eigenvalues in (-0.6, 0.9)): Kerker kills the mean of the
+    residual, which is zero here, so the preconditioned Pulay iteration must
+    reach the exact fixed point (period 2, history 7, beta 0.3)."""
+    n, L, k0 = 8, 6.0, 0.8
+    rng = np.random.default_rng(4)
+    lam = rng.uniform(-0.6, 0.9, size=(n, n, n))
+    lam = 0.5 * (lam + np.roll(np.flip(lam), 1, axis=(0, 1, 2)))   # lam(k) = lam(-k): S real
+    lam[0, 0, 0] = 0.0
+    c = rng.normal(size=n ** 3)
+    c -= c.mean()
+
+    def S(x):
+        return np.fft.ifftn(lam * np.fft.fftn(x.reshape(n, n, n))).real.ravel()
+
+    def G(x):
+        return x.mean() + S(x - x.mean()) + c
+
+    x0 = np.full(n ** 3, 0.7)
+    chat = np.fft.fftn(c.reshape(n, n, n))
+    den = 1.0 - lam
+    den[0, 0, 0] = 1.0
+    xstar = 0.7 + np.fft.ifftn(chat / den).real.ravel()
+    np.testing.assert_allclose(G(xstar), xstar, atol=1e-12)
+    mix = scf.PulayMixer(beta=0.3, history=7, period=2, precond=lambda f: scf.kerker(f, n, L, k0))
+    x = x0
+    for _ in range(60):
+        x = mix.step(x, G(x))
+    assert np.max(np.abs(x - xstar)) < 1e-9
+    assert abs(x.mean() - 0.7) < 1e-12
