@@ -60,3 +60,28 @@ def test_library_degree_rule_errors(sq3_host):
         with pytest.raises(sq3_host.SQ3Error):
             sq3_host.fermi_degree(*bad)
     assert sq3_host.fermi_degree(100.0, 1.0, 0.5) == 1
+
+
+def test_npl_sweep_reproduces_the_accuracy_study():
+    """Sec. 5's accuracy study on a synthetic 4-atom cell (12^3 grid,
+    Ns = 80, fixed potential, exact subspace): the free-energy and force
+    errors against diagonalisation fall exponentially with n_pl, fall with
+    temperature at fixed n_pl, and the degree that reaches chemical accuracy
+    (1e-3 Ha/atom and 1e-3 Ha/bohr) falls with temperature (24, 12, 8, 8
+    here for 10,000, 50,000, 100,000 and 250,000 K; the paper used 33, 12,
+    10 and 8 on its own cells)."""
+    from paper_2112_08639_gb300 import inputs
+    temps = (10_000, 50_000, 100_000, 250_000)
+    npls = (8, 12, 16, 24, 32, 48, 64)
+    pos = inputs.fcc_positions(1, disp_sigma=0.05, seed=0)
+    sw = degree.npl_sweep(12, inputs.A0_FCC, pos, 80, temps, npls, 3.0, 1.0)
+    for T in temps:
+        eF = [r[1] for r in sw[T]]
+        assert eF[-1] < 1e-3 * eF[0] or eF[-1] < 1e-12
+    for col in (1, 2):                                  # F per atom, forces
+        at12 = [sw[T][1][col] for T in temps]
+        assert all(a > b for a, b in zip(at12, at12[1:])), at12
+    for T in temps[1:]:
+        assert max(r[1] for r in sw[T] if r[0] == 64) < 1e-12
+    need = [min(r[0] for r in sw[T] if r[1] < 1e-3 and r[2] < 1e-3) for T in temps]
+    assert need == sorted(need, reverse=True) and need[0] > need[-1], need
