@@ -175,3 +175,17 @@ def test_kerker_preconditioned_pulay_reaches_the_fixed_point():
         x = mix.step(x, G(x))
     assert np.max(np.abs(x - xstar)) < 1e-9
     assert abs(x.mean() - 0.7) < 1e-12
+
+
+def test_self_energy_is_the_gaussians_own_coulomb_energy():
+    """E_self per atom = 1/2 int rho(r) phi(r) d^3r for the Gaussian charge
+    rho = Z exp(-r^2/rc^2) / (pi^(3/2) rc^3), whose potential is
+    Z erf(r/rc) / r: radial quadrature against the closed form used in F."""
+    from scipy.integrate import quad
+    from scipy.special import erf
+    for Z, rc in ((3.0, 1.0), (1.0, 0.6), (4.0, 1.7)):
+        rho = lambda r: Z * np.exp(-r * r / (rc * rc)) / (np.pi ** 1.5 * rc ** 3)
+        e, _ = quad(lambda r: 0.5 * 4 * np.pi * r * rho(r) * Z * erf(r / rc), 0, 30 * rc,
+                    epsabs=1e-14, epsrel=1e-13)
+        assert abs(scf.self_energy(1, Z, rc) - e) < 1e-11 * e
+        assert abs(scf.self_energy(5, Z, rc) - 5 * e) < 1e-10 * e
