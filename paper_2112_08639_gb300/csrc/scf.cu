@@ -493,6 +493,17 @@ int mixer_step(sq3_ctx* ctx, const double* x_in, const double* x_out, double* x_
   double* cbuf = part + (size_t)MIX_BLOCKS * MIX_NQ;
   cudaStream_t st = ctx->stream;
   const unsigned blocks = (unsigned)std::min<long long>((N + 255) / 256, 152LL * 8);
+  const bool precond = M.k0 > 0.0;
+  double *A = nullptr, *B = nullptr;
+  if (precond) {
+    // workspace first (sq3_mixer_setup already holds it): a failure here
+    // leaves the mixer's state untouched
+    int rc = ensure_tables(ctx);
+    if (rc) return rc;
+    double *p2, *res;
+    rc = scf_scratch(ctx, &A, &B, &p2, &res);
+    if (rc) return rc;
+  }
   // ring slot of the new difference (the oldest is overwritten when full)
   int slot = -1;
   if (M.have_prev) {
@@ -522,20 +533,15 @@ int mixer_step(sq3_ctx* ctx, const double* x_in, const double* x_out, double* x_
   } else {
     mp.m = 0;
   }
-  const bool precond = M.k0 > 0.0;
   mix_combine_kernel<<<blocks, 256, 0, st>>>(mp, pulay ? cbuf : nullptr, x_in, fp, x_next,
                                              precond ? fbar : nullptr, M.beta, N);
   if (precond) {
-    int rc = ensure_tables(ctx);
-    if (rc) return rc;
-    double *A, *B, *p2, *res;
-    rc = scf_scratch(ctx, &A, &B, &p2, &res);
-    if (rc) return rc;
     spectral_apply(ctx, fbar, nullptr, fbar, SCALE_KERKER, M.k0 * M.k0, A, B);
     axpy_kernel<<<blocks, 256, 0, st>>>(x_next, fbar, M.beta, N);
   }
   return cuda_err(cudaGetLastError());
 }
+
 }  // namespace
 
 }  // namespace sq3
@@ -576,6 +582,13 @@ int sq3_mixer_setup(sq3_ctx* c, int history, int period, double beta, double k0)
   c->mix.k0 = k0 > 0 ? k0 : 0.0;
   rc = mixer_buffers(c);
   if (rc) return rc;
+  if (c->mix.k0 > 0.0) {          // the Kerker step's tables and scratch
+    rc = ensure_tables(c);
+    if (rc) return rc;
+    double *A, *B, *part, *res;
+    rc = scf_scratch(c, &A, &B, &part, &res);
+    if (rc) return rc;
+  }
   c->mix.ready = true;
   return SQ3_OK;
 }
