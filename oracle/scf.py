@@ -36,6 +36,9 @@ TEST INFRASTRUCTURE ONLY, like the rest of this package: only ``tests/``
                        occupied subspace by exact diagonalisation
                        (``fermi``), mixing, until the L1 change of rho per
                        electron falls below a tolerance.
+* ``scf_sq3``       -- the same loop in the paper's algorithm order, the
+                       fixed-potential SQ3 iteration (``subspace``) in
+                       place of the diagonalisation.
 """
 from __future__ import annotations
 
@@ -257,5 +260,47 @@ def scf(n: int, L: float, positions: np.ndarray, Ns: int, sigma: float, Z: float
                                 Z, rc)
             return {"rho": out["rho"], "mu": out["mu"], "lam": lam, "U": U, "veff": veff,
                     "phi": phi, "b": b, "iterations": it + 1, "errors": hist, **terms}
+        rho = mixer.step(rho, out["rho"])
+    raise RuntimeError(f"SCF did not converge in {max_iter} iterations (last {hist[-1]:.3e})")
+
+
+def scf_sq3(n: int, L: float, positions: np.ndarray, X0: np.ndarray, sigma: float, Z: float,
+            rc: float, filt: tuple, npl: int, degree: int = 16, passes: tuple = (12, 3),
+            proj=None, tol: float = 1e-10, max_iter: int = 200, order: int = 12,
+            k0: float = 0.8) -> dict:
+    """The SCF in the paper's algorithm order: each iteration builds V_eff
+    from the mixed density, then runs the fixed-potential SQ3 iteration
+    (``subspace.sq3_iteration``: Chebyshev filter, Cholesky QR, Hs, the
+    Chebyshev density kernel with exact spectral bounds, rho) `passes[0]`
+    times in the first iteration and `passes[1]` times after, from the
+    starting block X0 (N x Ns, e.g. seeded random); filt = (a, b, a0) are the
+    filter's cutoff, upper bound and lower estimate.  Stops when the L1 change of rho per electron is below
+    `tol`; F by Eq. (FreeEnergy:NewForm) from the last output density."""
+    from . import subspace
+    natoms = len(positions)
+    Ne = Z * natoms
+    dV = (L / n) ** 3
+    a, b_up, a0 = filt
+    b, _ = pseudocharge(n, L, positions, Z, rc, Ne=Ne)
+    rho = np.full(n ** 3, Ne / (n ** 3 * dV))
+    mixer = PulayMixer(precond=lambda f: kerker(f, n, L, k0))
+    X = np.array(X0, dtype=float)
+    hist = []
+    for it in range(max_iter):
+        phi = poisson_fd(rho + b, n, L, order)
+        _, vxc = lda_xc(rho)
+        parts = hamiltonian.hamiltonian_sparse(n, L, phi + vxc, proj, order)
+        apply_H = lambda Y: hamiltonian.apply(parts, Y)
+        for _ in range(passes[0] if it == 0 else passes[1]):
+            out = subspace.sq3_iteration(apply_H, X, degree, a, b_up, a0, npl, sigma, Ne, dV)
+            X = out["X"]
+        err = float(np.sum(np.abs(out["rho"] - rho)) * dV / Ne)
+        hist.append(err)
+        if err < tol:
+            phi_out = poisson_fd(out["rho"] + b, n, L, order)
+            terms = free_energy(out["e_band"], out["e_ent"], out["rho"], b, phi_out, dV, natoms,
+                                Z, rc)
+            return {"rho": out["rho"], "mu": out["mu"], "X": X, "D": out["D"], "b": b,
+                    "iterations": it + 1, "errors": hist, **terms}
         rho = mixer.step(rho, out["rho"])
     raise RuntimeError(f"SCF did not converge in {max_iter} iterations (last {hist[-1]:.3e})")
