@@ -85,3 +85,25 @@ def test_npl_sweep_reproduces_the_accuracy_study():
         assert max(r[1] for r in sw[T] if r[0] == 64) < 1e-12
     need = [min(r[0] for r in sw[T] if r[1] < 1e-3 and r[2] < 1e-3) for T in temps]
     assert need == sorted(need, reverse=True) and need[0] > need[-1], need
+
+
+def test_chemical_accuracy_degrees_follow_the_papers_choices():
+    """The degrees the paper selects for chemical accuracy at 10,000 to
+    250,000 K (tests/golden/npl_chemical_accuracy.txt, Sec. 5) against the
+    synthetic study's: the same non-increasing order with temperature, and
+    each within a factor 0.5..1.5 of the paper's (the cells and spectral
+    widths differ, so only the scale is comparable)."""
+    import os
+    from paper_2112_08639_gb300 import inputs
+    path = os.path.join(os.path.dirname(__file__), "golden", "npl_chemical_accuracy.txt")
+    rows = [tuple(int(v) for v in line.split()) for line in open(path)
+            if line.strip() and not line.startswith("#")]
+    temps = tuple(r[0] for r in rows)
+    paper = [r[2] for r in rows]
+    npls = (6, 8, 10, 12, 16, 20, 24, 32, 40, 48)
+    pos = inputs.fcc_positions(1, disp_sigma=0.05, seed=0)
+    sw = degree.npl_sweep(12, inputs.A0_FCC, pos, 80, temps, npls, 3.0, 1.0)
+    ours = [min(r[0] for r in sw[T] if r[1] < 1e-3 and r[2] < 1e-3) for T in temps]
+    assert ours == sorted(ours, reverse=True) and paper == sorted(paper, reverse=True)
+    for o, p in zip(ours, paper):
+        assert 0.5 * p <= o <= 1.5 * p, (ours, paper)
