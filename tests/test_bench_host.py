@@ -1,0 +1,57 @@
+"""CPU checks of the bench's roofline arithmetic: the algorithmic work per
+launch of each dominant kernel class equals its closed form (three words
+per point and vector for the FP32 stencil, a read and a write of the
+covered points for the nonlocal pass, the useful flops of each GEMM with
+six BF16 piece products issued per useful product, about 80 flop per point
+and vector for the FP64 stencil), and the fraction is achieved / peak."""
+import pytest
+
+import bench
+from paper_2112_08639_gb300 import inputs
+
+PK = {"hbm_gbs": 6679.8, "bf16_tflops": 1899.4, "bf16_tflops_sustained": 1722.8}
+
+
+def _entry(kind, ms=2.0, n=2, fp64=False, n_covered=None):
+    cfg = inputs.C3
+    prof = {kind: (ms, n)}
+    esize = 8 if fp64 else 4
+    return bench.roofline(kind, prof, cfg, esize, fp64, PK, "test",
+                          1, cfg.N if n_covered is None else n_covered), cfg
+
+
+def test_stencil_fp32_is_three_words_per_point_and_vector():
+    r, cfg = _entry("stencil")                         # 1 ms per launch
+    algo = 3 * cfg.N * cfg.Ns * 4
+    assert r["bound"] == "hbm" and r["algorithmic"] == pytest.approx(algo / 1e9, abs=1e-3)
+    assert abs(algo / 1e9 - 9.853) < 1e-3                 # 72^3 points x 2200 vectors
+    assert r["achieved"] == pytest.approx(algo / 1e-3 / 1e9, abs=0.1)
+    assert r["frac"] == pytest.approx(r["achieved"] / PK["hbm_gbs"], abs=1e-4)
+    traffic = bench.MEASURED_TRAFFIC["stencil"][0] * cfg.N * cfg.Ns / 1e9
+    assert r["traffic"] == pytest.approx(traffic, abs=1e-3)
+
+
+def test_nonlocal_pass_reads_and_writes_the_covered_points():
+    r, cfg = _entry("nl_pass", n_covered=300_000)
+    algo = 2 * 300_000 * cfg.Ns * 4
+    assert r["algorithmic"] == pytest.approx(algo / 1e9, abs=1e-3)
+    assert r["achieved"] == pytest.approx(algo / 1e-3 / 1e9, abs=0.1)
+
+
+@pytest.mark.parametrize("kind,flops", [("gram", "NNs2"), ("hs_gemm", "NNs2"),
+                                        ("x_rinv", "NNs2"), ("rho", "NNs2"),
+                                        ("cheb_gemm", "Ns3")])
+def test_gemm_useful_flops_and_piece_products(kind, flops):
+    r, cfg = _entry(kind)
+    useful = cfg.N * cfg.Ns ** 2 if flops == "NNs2" else cfg.Ns ** 3
+    assert r["bound"] == "tensor"
+    assert r["useful"] == pytest.approx(useful / 1e-3 / 1e12, abs=0.01)
+    assert r["achieved"] == pytest.approx(6 * r["useful"], abs=0.05)
+    assert r["frac"] == pytest.approx(r["achieved"] / PK["bf16_tflops_sustained"], abs=1e-4)
+
+
+def test_fp64_paths_report_against_the_derived_fp64_peak():
+    r, cfg = _entry("stencil", fp64=True)
+    assert r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(80 * cfg.N * cfg.Ns / 1e-3 / 1e12, abs=1e-3)
+    assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12, abs=1e-4)
