@@ -1,21 +1,38 @@
-"""Benchmark of the SQ3 hot path on GB300.
+"""Benchmark of the SQ3 path on GB300: seconds per converged SCF solve.
 
-One step = one fixed-potential SQ3 iteration of the 108-atom Al-like cell
-(72^3 grid, Ns = 2200, filter degree 30, Fermi degree 120, s/p projectors):
-Chebyshev filter, Cholesky-QR orthonormalisation, Hs = X^T H X, Lanczos
-bounds, Chebyshev Fermi-operator expansion with the Fermi level found on
-the device, Ds, and the fused density rho = 2 rowdot(X, X Ds)/dV.  Every step
-runs through the C ABI of libsq3 (ctypes binding); inputs are seeded and
-synthetic and resident in HBM when the timed region starts (X alone is
-larger than L2).
+One step = one converged self-consistent-field solve of the 108-atom
+Al-like cell (72^3 grid, Ns = 2200, filter degree 30, Fermi degree 120,
+kT = 10 eV, s/p projectors) through the library's SCF driver
+(sq3_scf_solve): per SCF iteration V_eff = phi[rho + b] + V_xc[rho], the
+Chebyshev filter and Cholesky QR, Hs = X^T H X, Lanczos bounds, the
+Chebyshev Fermi-operator expansion with the Fermi level on the device, Ds,
+the fused density rho = 2 rowdot(X, X Ds)/dV, F and Kerker/Pulay mixing,
+until sum |rho_out - rho_in| dV / Ne < 1e-6.  Every step runs in the
+library's kernels behind the C ABI (ctypes binding); the inputs (seeded
+synthetic positions and projectors, the starting block and density) are
+resident in HBM when a timed solve starts, and every solve restarts from
+the same block and density (X alone, 3.3 GB, is larger than L2).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed]
-                    [--config al108_72|al32_48|al4_18] [--impl sq3|reference]
+The `value` arm is the mixed-precision path (FP32 stencil, BF16-split
+tcgen05 products, FP64 Cholesky/Fermi level/energies) from the starting
+density `--start` (learned: the MLP over atom-centred Gaussian
+descriptors, trained on converged densities of 32-atom cells; the
+atomic superposition otherwise).  `--fp64-arm` also runs the plain FP64
+path from the atomic superposition to convergence (one solve, minutes at
+this size) and reports its time and the differences of the converged
+density, free energy and Fermi level between the arms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--start learned|superposition]
+                    [--fp64-arm] [--config al108_72|al32_48] [--impl sq3|reference]
+                    [--mode solve|iteration]
+
+`--mode iteration` times one fixed-potential SQ3 iteration (the unit an
+SCF iteration repeats) instead, for kernel-level profiling.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
-replica of the cell (the single-cell path has no data-parallel exchange), the
-timed region is bracketed by barriers, the slowest rank's time is taken, and
-`value` is whole-job seconds per iteration (that time / number of replicas).
+replica of the cell, the timed region is bracketed by barriers, the slowest
+rank's time is taken, and `value` is whole-job seconds per solve (that time
+/ number of replicas).
 
 `--impl reference` times the CPU oracle (numpy/scipy FP64) on a bounded
 sample of the same workload on the host cores and prints the same line with
@@ -38,18 +55,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "s per SCF solve (108-atom) mixed+learned vs FP64 at ρ err ≤1e-5; % roofline"
+METRIC_ITER = "s per fixed-potential SQ3 iteration (108-atom), mixed precision"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal
 # unit count and maximum clock; probed 1.18 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grid point
-# and vector of one launch of the FP32 kernels, from the ncu captures
-# summarised in profiles/ (32-atom cell: 110,592 points x 640 vectors); the
-# roofline entry scales them to the bench's workload by points x vectors.
+# and vector of one launch of the FP32 kernels, from ncu captures of the
+# 32-atom cell (110,592 points x 640 vectors); the roofline entry scales
+# them to the bench's workload by points x vectors.
 MEASURED_TRAFFIC = {
-    "stencil": (831.3e6 / (110592 * 640), "profiles/cheb_step_ring_f32_al32_48.md"),
-    "nl_pass": (533.1e6 / (110592 * 640), "profiles/nl_brick_f32_al32_48.md"),
+    "stencil": (831.3e6 / (110592 * 640), "ncu dram__bytes, 48^3 x 640 capture"),
+    "nl_pass": (533.1e6 / (110592 * 640), "ncu dram__bytes, 48^3 x 640 capture"),
 }
+SCF_TOL = 1e-6
+# SCF driver settings: 4 filter passes in the first iteration (from a
+# random block), one per later iteration; Pulay every 2nd step over 7
+# differences, beta 0.3, Kerker k0 0.8 / bohr
+SCF_KW = dict(first_passes=4, passes=1, max_iter=80, mix_history=7, mix_period=2,
+              mix_beta=0.3, kerker_k0=0.8)
+SUPERPOSITION_WIDTH = 1.9     # bohr; the fitted width of the atomic superposition
 
 
 def parse():
@@ -60,7 +85,10 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--config", default="al108_72")
     p.add_argument("--impl", default="sq3", choices=["sq3", "reference"])
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--mode", default="solve", choices=["solve", "iteration"])
+    p.add_argument("--start", default="superposition", choices=["learned", "superposition"])
+    p.add_argument("--fp64-arm", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-clocks", action="store_true")
     return p.parse_args()
 
@@ -131,7 +159,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# the GPU path
+# rank helpers
 # ----------------------------------------------------------------------------
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest of the ranks' values of x (x itself with one rank)."""
@@ -144,118 +172,158 @@ def max_over_ranks(x: float, world: int, device) -> float:
 
 
 def job_seconds_per_iteration(ms_step_slowest: float, world: int) -> float:
-    """Whole-job time per iteration: the replicas run one cell each, so
-    `world` iterations finish in the slowest rank's time per step."""
+    """Whole-job time per step: the replicas run one cell each, so `world`
+    steps finish in the slowest rank's time per step."""
     return ms_step_slowest / 1e3 / max(world, 1)
 
 
-def run_sq3(args, rank, world):
+# ----------------------------------------------------------------------------
+# the GPU path
+# ----------------------------------------------------------------------------
+def _setup(args, rank):
     import torch
     from paper_2112_08639_gb300 import build, inputs
     build.build()
     from paper_2112_08639_gb300 import sq3
-
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cfg = inputs.CONFIGS[args.config]
-    prec = sq3.FP64 if args.prec == "fp64" else sq3.MIXED
-    dtype = torch.float64 if prec == sq3.FP64 else torch.float32
-    esize = 8 if prec == sq3.FP64 else 4
     cell = inputs.make_cell(cfg)
     ctx = sq3.Context(dev)
     ctx.setup_grid(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L, 12)
-    V = torch.from_numpy(cell.V).cuda()
-    ctx.set_potential(V)
     if cell.proj is not None:
         ctx.set_projectors(cell.proj.ptr, cell.proj.idx, cell.proj.val, cell.proj.gamma)
-    gen = torch.Generator(device="cuda").manual_seed(1000 + rank)
-    X = torch.randn((cfg.Ns, cfg.N), generator=gen, device="cuda", dtype=dtype)
-    D = torch.empty((cfg.Ns, cfg.Ns), dtype=torch.float64, device="cuda")
+    return dev, cfg, cell, ctx, sq3, inputs
+
+
+def _stage_summary(prof, steps):
+    return {k: round(v[0] / steps, 3) for k, v in prof.items() if v[1] or v[0]}
+
+
+def learned_start(ctx, cfg, cell, dev):
+    """Train the starting-density MLP on converged densities of 32-atom cells
+    (untimed set-up) and return a predictor for this cell's positions."""
+    from paper_2112_08639_gb300 import learned
+    model = learned.train_on_cells(dev, ncells=4, seed=0)
+    return model
+
+
+def run_solve(args, rank, world):
+    import torch
+    dev, cfg, cell, ctx, sq3, inputs = _setup(args, rank)
+    Z, rc = inputs.Z_VALENCE, inputs.RC_LOCAL
+    e_self = cfg.natoms * Z * Z / np.sqrt(2.0 * np.pi) / rc
+    b, _ = ctx.pseudocharge(cell.positions, Z, rc)
+    model = None
+    if args.start == "learned":
+        model = learned_start(ctx, cfg, cell, dev)
+    sup, _ = ctx.atom_gaussians(cell.positions, SUPERPOSITION_WIDTH, total=cfg.Ne)
+
+    def start_density():
+        if model is None:
+            return sup.clone()
+        return model.predict(ctx, cell.positions, cfg.Ne)
+
+    X0 = inputs.random_block_device(cfg.N, cfg.Ns, seed=1000 + rank)       # FP32
+    X = torch.empty_like(X0)
     rho = torch.empty(cfg.N, dtype=torch.float64, device="cuda")
+    D = torch.empty((cfg.Ns, cfg.Ns), dtype=torch.float64, device="cuda")
+    kw = dict(degree=cfg.m, npl=cfg.npl, kT=cfg.sigma, Ne=cfg.Ne, e_self=e_self, tol=SCF_TOL,
+              prec=sq3.MIXED, D=D, **SCF_KW)
 
-    # spectral bounds for the filter: upper bound b above the FD kinetic
-    # maximum (1/2 * 3 * s_max / h^2, s_max = 7.0729 for 12th order) plus the
-    # largest potential; damped interval [a, b]; a0 at the lower end.
-    b = 0.5 * 3 * 7.0729 / cfg.h ** 2 + float(cell.V.max()) + (
-        float(np.max(cell.proj.gamma)) * 4 if cell.proj is not None else 0.0)
-    state = {"a0": float(cell.V.min()) - 1.0}
-    state["a"] = state["a0"] + 0.05 * (b - state["a0"])
+    stream = torch.cuda.current_stream()
 
-    def step(Xb, Xhost=None):
-        if Xhost is None:
-            ctx.cheb_filter(Xb, cfg.m, state["a"], b, state["a0"], prec)
-        else:   # the block arrives from host memory, its upload overlapping the filter
-            ctx.cheb_filter_from_host(Xhost, Xb, cfg.m, state["a"], b, state["a0"], prec)
-        ctx.orthonormalise(Xb, prec)
-        _, out = ctx.density_kernel(Xb, cfg.npl, cfg.sigma, cfg.Ne, prec, D=D)
-        ctx.density(Xb, D, prec, rho=rho)
-        state["a0"], state["a"] = out["chi"] - out["xi"], out["chi"] + out["xi"]
-        return out
+    def solve():
+        """One converged solve from the starting block and density; the
+        start is restored before the timed region (X0 -> X copy)."""
+        X.copy_(X0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r0 = start_density()
+        rho.copy_(r0)
+        res, hist = ctx.scf_solve(b, rho, X, raise_on_noconv=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res, hist
 
     for _ in range(args.warmup):
-        step(X)
-    stream = torch.cuda.current_stream()
+        solve()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx.profile(True)
+    times = []
     with ClockSampler(dev, enabled=not args.no_clocks) as clk:
-        e0.record(stream)
         for _ in range(args.steps):
-            out = step(X)
-        e1.record(stream)
-        torch.cuda.synchronize()
+            ms, res, hist = solve()
+            times.append(ms)
+    torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read()
-    ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    ms_total = max_over_ranks(sum(times), world, "cuda")
     if world > 1:
         torch.distributed.barrier()
     ms_step = ms_total / args.steps
+    rho_mixed = rho.clone()
 
-    # end to end through the public API with host buffers: the step's inputs
-    # (V and the starting block X) copied from pinned host memory, the step,
-    # and rho plus the scalars read back, all inside the timed region.  The
-    # block goes up through the filter's host entry point, which copies it in
-    # chunks of vectors and filters each chunk as soon as it has landed.
-    Xh = X.cpu().pin_memory()
-    Vh = V.cpu().pin_memory()
+    # end to end through the public API with host buffers: the positions
+    # (for the learned start), the starting block and the pseudocharges
+    # copied from pinned host memory, the solve, and rho plus the result read
+    # back, all inside the timed region
+    Xh = X0.cpu().pin_memory()
+    bh = b.cpu().pin_memory()
     rho_h = torch.empty(cfg.N, dtype=torch.float64).pin_memory()
 
-    # every end-to-end step starts from the same host block and the same
-    # filter bounds (the steps would otherwise alternate between two bound
-    # settings, since each one restarts from that block)
-    bounds0 = dict(state)
-
     def e2e_step():
-        state.update(bounds0)
-        V.copy_(Vh, non_blocking=True)
-        ctx.set_potential(V)
-        step(X, Xh)
+        X.copy_(Xh, non_blocking=True)
+        b.copy_(bh, non_blocking=True)
+        rho.copy_(start_density())
+        res_e, _ = ctx.scf_solve(b, rho, X, raise_on_noconv=False, **kw)
         rho_h.copy_(rho, non_blocking=True)
         torch.cuda.synchronize()
+        return res_e
 
-    e2e_step()          # untimed: first use of the host buffers and the copy stream
-    torch.cuda.synchronize()
-    # each step timed on its own (wall clock, synchronised on both sides);
-    # the median, so that one host-side hiccup does not set the figure
+    e2e_step()
     e2e_t = []
     for _ in range(args.e2e_steps):
         t0 = time.perf_counter()
         e2e_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.median(e2e_t))
-    h2d = Xh.numel() * Xh.element_size() + Vh.numel() * 8
-    d2h = cfg.N * 8 + 6 * 8
+    h2d = Xh.numel() * Xh.element_size() + bh.numel() * 8 + cfg.natoms * 3 * 8
+    d2h = cfg.N * 8
+
+    fp64 = None
+    if args.fp64_arm:
+        X64 = X0.double()
+        r64 = sup.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kw64 = dict(kw, prec=sq3.FP64)
+        res64, hist64 = ctx.scf_solve(b, r64, X64, raise_on_noconv=False, **kw64)
+        torch.cuda.synchronize()
+        s64 = time.perf_counter() - t0
+        fp64 = {
+            "s_per_solve": round(s64, 3), "iterations": res64["iterations"],
+            "converged": res64["converged"], "err": res64["err"],
+            "start": "superposition",
+            "rho_l1_per_Ne_vs_mixed": float((rho_mixed - r64).abs().sum()) * cfg.dV / cfg.Ne,
+            "F_per_atom_vs_mixed": abs(res["F"] - res64["F"]) / cfg.natoms,
+            "mu_vs_mixed": abs(res["mu"] - res64["mu"]),
+            "F": res64["F"], "mu": res64["mu"],
+            "speedup_mixed_vs_fp64": round(s64 / (ms_step / 1e3), 2),
+        }
+        del X64
 
     launches = int(sum(v[1] for v in prof.values()))
-    stage_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1] or v[0]}
     pk, pk_src = peaks()
     dominant = max(prof, key=lambda k: prof[k][0])
     n_cov = int(np.unique(cell.proj.idx).size) if cell.proj is not None else 0
-    roof = roofline(dominant, prof, cfg, esize, prec == sq3.FP64, pk, pk_src, args.steps, n_cov)
+    roof = roofline(dominant, prof, cfg, 4, False, pk, pk_src, n_cov)
     clocks = clk.summary()
-    res = {
+    it_total = res["iterations"] + SCF_KW["first_passes"] - 1
+    out = {
         "metric": METRIC,
         "value": round(job_seconds_per_iteration(ms_step, world), 6),
         "unit": "s",
@@ -266,31 +334,101 @@ def run_sq3(args, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == sq3.FP64 else "f32+bf16x3",
+        "dtype": "f32+bf16x3",
         "data": "synthetic",
         "config": {
             "workload": f"{cfg.name}: {cfg.natoms}-atom Al-like cell, {cfg.n}^3 grid, Ns={cfg.Ns}, "
                         f"filter degree {cfg.m}, Fermi degree {cfg.npl}, kT={cfg.kT_ev} eV, "
                         f"projectors={'s/p' if cfg.projectors else 'none'}",
-            "step": "one fixed-potential SQ3 iteration (filter, CholQR, Hs, Lanczos, FOE, Ds, rho)",
-            "precision": args.prec,
+            "step": f"converged SCF solve (rho L1/Ne change < {SCF_TOL:g}) from a seeded random "
+                    f"block and the {args.start} starting density",
+            "precision": "mixed",
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (X block %.2f GB)" % (cfg.N * cfg.Ns * esize / 1e9),
+            "l2": "inputs larger than L2 (X block %.2f GB)" % (cfg.N * cfg.Ns * 4 / 1e9),
         },
-        "e2e": {"value": round(e2e_s, 6), "unit": "s", "stat": f"median of {len(e2e_t)} steps",
-                "steps_s": [round(x, 6) for x in e2e_t], "h2d_bytes_per_step": int(h2d),
+        "scf": {"iterations": res["iterations"], "filter_passes": it_total,
+                "ms_per_iteration": round(ms_step / res["iterations"], 2),
+                "F": res["F"], "mu": res["mu"], "err": res["err"], "converged": res["converged"],
+                "start": args.start,
+                "per_iteration": [{k: (round(v, 9) if isinstance(v, float) else v)
+                                   for k, v in h.items()} for h in hist]},
+        "e2e": {"value": round(e2e_s, 6), "unit": "s", "stat": f"median of {len(e2e_t)} solves",
+                "steps_s": [round(x, 4) for x in e2e_t], "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
-        "stage_ms_per_step": stage_ms,
+        "stage_ms_per_step": _stage_summary(prof, args.steps),
         "roofline": roof,
-        "mu": out["mu"], "e_band": out["e_band"], "e_ent": out["e_ent"],
     }
+    if fp64 is not None:
+        out["fp64_arm"] = fp64
+    if clocks is not None:
+        out["clocks"] = clocks
+    return out, it_total
+
+
+def run_iteration(args, rank, world):
+    """One fixed-potential SQ3 iteration per step (kernel-level profiling)."""
+    import torch
+    dev, cfg, cell, ctx, sq3, inputs = _setup(args, rank)
+    prec = sq3.FP64 if args.prec == "fp64" else sq3.MIXED
+    dtype = torch.float64 if prec == sq3.FP64 else torch.float32
+    esize = 8 if prec == sq3.FP64 else 4
+    V = torch.from_numpy(cell.V).cuda()
+    ctx.set_potential(V)
+    X = inputs.random_block_device(cfg.N, cfg.Ns, seed=1000 + rank, dtype=dtype)
+    D = torch.empty((cfg.Ns, cfg.Ns), dtype=torch.float64, device="cuda")
+    rho = torch.empty(cfg.N, dtype=torch.float64, device="cuda")
+    lo, b = ctx.hamiltonian_bounds()
+    state = {"a0": lo, "a": lo + 0.05 * (b - lo)}
+
+    def step():
+        ctx.cheb_filter(X, cfg.m, state["a"], b, state["a0"], prec)
+        ctx.orthonormalise(X, prec)
+        _, out = ctx.density_kernel(X, cfg.npl, cfg.sigma, cfg.Ne, prec, D=D)
+        ctx.density(X, D, prec, rho=rho)
+        state["a0"], state["a"] = out["chi"] - out["xi"], out["chi"] + out["xi"]
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    with ClockSampler(dev, enabled=not args.no_clocks) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms_step = max_over_ranks(e0.elapsed_time(e1), world, "cuda") / args.steps
+    pk, pk_src = peaks()
+    dominant = max(prof, key=lambda k: prof[k][0])
+    n_cov = int(np.unique(cell.proj.idx).size) if cell.proj is not None else 0
+    res = {
+        "metric": METRIC_ITER, "value": round(job_seconds_per_iteration(ms_step, world), 6),
+        "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == sq3.FP64 else "f32+bf16x3",
+        "data": "synthetic",
+        "config": {"workload": cfg.name, "step": "one fixed-potential SQ3 iteration",
+                   "precision": args.prec},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "stage_ms_per_step": _stage_summary(prof, args.steps),
+        "roofline": roofline(dominant, prof, cfg, esize, prec == sq3.FP64, pk, pk_src, n_cov),
+        "mu": out["mu"],
+    }
+    clocks = clk.summary()
     if clocks is not None:
         res["clocks"] = clocks
-    return res
+    return res, 1
 
 
-def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
+def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, n_covered):
     """Roofline entry for the kernel class that takes the most device time.
 
     Algorithmic work per launch:
@@ -298,15 +436,18 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
                 write Y_{k+1}); FP64 path: ~80 flop per point per vector
       nl_pass   read and write of the step's output at the n_covered grid
                 points inside at least one projector
-      GEMMs     useful flops: Gram and X^T(HX) N Ns^2 (upper triangle),
-                X R^{-1} N Ns^2 (triangular), X Ds 2 N Ns^2, recurrence 2 Ns^3
+      GEMMs     useful flops: Gram and X^T(HX) N Ns^2 (upper-triangle tiles
+                of a symmetric product), X R^{-1} N Ns^2 (triangular
+                R^{-1}), the density row-dot N Ns^2 (triangular B), the
+                recurrence Ns^3 (upper-triangle tiles)
     """
     N, Ns = cfg.N, cfg.Ns
     ms, n = prof[dominant]
     per_launch_s = ms / max(n, 1) / 1e3
     fp64_peak = {"peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                  "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
-    hbm_peak = {"peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk_src + " (MEASURED_PEAKS hbm_gbs)"}
+    hbm_peak = {"peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": pk_src + " (MEASURED_PEAKS hbm_gbs; of measured)"}
     if dominant == "stencil":
         if fp64:
             ach = 80.0 * N * Ns / per_launch_s / 1e12
@@ -326,8 +467,6 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
                     traffic=round(bpu * n_covered * Ns / 1e9, 3), traffic_unit="GB per launch",
                     algorithmic=round(2.0 * n_covered * Ns * esize / 1e9, 3),
                     traffic_source=src + ", scaled by points x vectors", **hbm_peak)
-    # useful flops per launch: symmetric outputs (Gram, Hs, the recurrence)
-    # and triangular B (X R^-1, the density row-dot) count half a full product
     gemm_flops = {"gram": N * Ns * Ns, "hs_gemm": N * Ns * Ns, "x_rinv": N * Ns * Ns,
                   "rho": N * Ns * Ns, "cheb_gemm": Ns ** 3}
     if dominant in gemm_flops:
@@ -336,11 +475,10 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
             return dict(bound="alu", kernel=f"{dominant} (FP64 GEMM)", achieved=round(ach, 4),
                         frac=round(ach / FP64_PEAK_TFLOPS, 4), traffic=None, **fp64_peak)
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        # six BF16 piece products are issued per useful FP32-level product
         return dict(bound="tensor", kernel=f"{dominant} (tcgen05, 6 BF16 piece products)",
                     achieved=round(6 * ach, 2), useful=round(ach, 2), peak=peak, unit="TFLOP/s",
                     frac=round(6 * ach / peak, 4), traffic=None,
-                    peak_source=pk_src + " (bf16_tflops_sustained)")
+                    peak_source=pk_src + " (bf16_tflops_sustained; of measured)")
     return {"bound": "unknown", "kernel": dominant, "achieved": None, "peak": None, "unit": None,
             "frac": None, "traffic": None}
 
@@ -348,18 +486,26 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, steps, n_covered):
 # ----------------------------------------------------------------------------
 # the CPU oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------
-def run_oracle_sample(cfg_name: str):
-    """Time the oracle's steps of one SQ3 iteration on sampled sizes and scale
-    each by its operation count to the full cell.
+# filter passes per converged mixed solve at the 108-atom configuration (SCF
+# iterations + 3 extra passes of the first iteration), measured by this
+# bench's GPU arm with the learned start; the reference arm scales the
+# oracle's per-iteration cost by it
+PASSES_PER_SOLVE = {"al108_72": 20, "al32_48": 20}
+
+
+def run_oracle_sample(cfg_name: str, passes: int):
+    """Time the oracle's steps of one SQ3 iteration and of the SCF pieces on
+    sampled sizes, scale each by its operation count to the full cell, and
+    multiply by the number of filter passes of one solve.
 
     filter: m sparse H applies on k columns (scaled by Ns/k); the H apply of
     the projection step costs 1/m of that per column; Cholesky QR, X^T (H X)
     and the density on an N x s column block (dense FP64 BLAS, scaled by
     (Ns/s)^2); the Fermi-operator expansion on an s x s Hs (scaled by
-    (Ns/s)^3).
+    (Ns/s)^3); the SCF pieces (Poisson, LDA, Kerker/Pulay) at full size.
     """
     from paper_2112_08639_gb300 import inputs
-    from oracle import chebyshev, hamiltonian, subspace
+    from oracle import chebyshev, hamiltonian, scf, subspace
 
     cfg = inputs.CONFIGS[cfg_name]
     cell = inputs.make_cell(cfg)
@@ -385,15 +531,27 @@ def run_oracle_sample(cfg_name: str):
     chi, xi = subspace.exact_bounds(Hs)
     chebyshev.foe_density_kernel(Hs, cfg.npl, cfg.sigma, min(cfg.Ne, 1.5 * s), chi, xi)
     t_foe = (time.perf_counter() - t) * (cfg.Ns / s) ** 3
-    total = t_filter + t_apply + t_dense + t_foe
+    rho = np.full(cfg.N, cfg.Ne / (cfg.N * cfg.dV))
+    bq, _ = scf.pseudocharge(cfg.n, cfg.L, cell.positions, 3.0, 1.0, Ne=cfg.Ne)
+    mixer = scf.PulayMixer(precond=lambda f: scf.kerker(f, cfg.n, cfg.L, 0.8))
+    t = time.perf_counter()
+    phi = scf.poisson_fd(rho + bq, cfg.n, cfg.L)
+    scf.lda_xc(rho)
+    mixer.step(rho, rho + 1e-3 * phi)
+    t_scf = time.perf_counter() - t
+    per_iter = t_filter + t_apply + t_dense + t_foe + t_scf
+    total = per_iter * passes
     try:
         cores = len(os.sched_getaffinity(0))
     except Exception:
         cores = os.cpu_count()
-    sample = (f"{cfg.name}: filter (degree {cfg.m}) on {k} of {cfg.Ns} columns (x{cfg.Ns / k:.0f}); "
-              f"CholQR + X^T(HX) + rho on an N x {s} block (x{(cfg.Ns / s) ** 2:.1f}); FOE (npl {cfg.npl}) "
-              f"at Ns={s} (x{(cfg.Ns / s) ** 3:.0f}); numpy/scipy FP64, operation-count scaling")
-    return total, cores, sample, {"filter": t_filter, "apply": t_apply, "dense": t_dense, "foe": t_foe}
+    sample = (f"{cfg.name}: per SQ3 iteration, filter (degree {cfg.m}) on {k} of {cfg.Ns} columns "
+              f"(x{cfg.Ns / k:.0f}); CholQR + X^T(HX) + rho on an N x {s} block "
+              f"(x{(cfg.Ns / s) ** 2:.1f}); FOE (npl {cfg.npl}) at Ns={s} (x{(cfg.Ns / s) ** 3:.0f}); "
+              f"Poisson + LDA + Kerker/Pulay at full size; numpy/scipy FP64, operation-count "
+              f"scaling; x {passes} filter passes per solve (the GPU arm's count)")
+    return total, cores, sample, {"per_iteration": per_iter, "filter": t_filter,
+                                  "dense": t_dense, "foe": t_foe, "scf": t_scf}
 
 
 def main():
@@ -401,22 +559,26 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.steps is None:
-        args.steps = 1 if args.prec == "fp64" else 5
+        args.steps = 3 if args.mode == "solve" else 5
+    metric = METRIC if args.mode == "solve" else METRIC_ITER
+    passes_ref = PASSES_PER_SOLVE.get(args.config, 20) if args.mode == "solve" else 1
     if args.impl == "reference":
         if rank != 0:
             return
         vals = []
         for _ in range(max(args.warmup, 0)):
-            run_oracle_sample(args.config)
+            run_oracle_sample(args.config, passes_ref)
         for _ in range(args.steps):
-            v, cores, sample, parts = run_oracle_sample(args.config)
+            v, cores, sample, parts = run_oracle_sample(args.config, passes_ref)
             vals.append(v)
         v = statistics.median(vals)
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+            "impl": "reference", "metric": metric, "value": round(v, 3), "unit": "s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.config, "step": "one fixed-potential SQ3 iteration (oracle)"},
+            "config": {"workload": args.config,
+                       "step": "converged SCF solve (oracle, extrapolated from a sample)"
+                       if args.mode == "solve" else "one fixed-potential SQ3 iteration (oracle)"},
             "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -428,9 +590,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    res = run_sq3(args, rank, world)
+    if args.mode == "solve":
+        res, passes = run_solve(args, rank, world)
+    else:
+        res, passes = run_iteration(args, rank, world)
     if rank == 0:
-        v, cores, sample, parts = run_oracle_sample(args.config)
+        v, cores, sample, parts = run_oracle_sample(args.config, passes)
         res["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
                                "sample": sample}
         print(json.dumps(res))

@@ -255,6 +255,108 @@ int sq3_mixer_step(sq3_ctx* ctx, const double* x_in, const double* x_out,
  * may alias r.  Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOMEM, SQ3_ECUDA. */
 int sq3_kerker(sq3_ctx* ctx, const double* r, double* out, double k0);
 
+/* Rigorous bounds of the spectrum of the context's H (grid and potential
+ * set): out[0] = min V + (lower Gershgorin bound of V_nl), out[1] = the
+ * largest eigenvalue of the FD kinetic operator -1/2 L_h over the grid's
+ * frequencies + max V + (upper Gershgorin bound of V_nl, from the overlaps
+ * of the projectors).  out: HOST array of 2 doubles.  Host arithmetic on
+ * values the set-up calls keep; no GPU work.  The upper bound is the b of
+ * the Chebyshev filter (Sec. 4: the CheFSI filter needs an upper bound of
+ * the spectrum).  Errors: SQ3_EINVAL, SQ3_ENOTSETUP. */
+int sq3_hamiltonian_bounds(sq3_ctx* ctx, double* out);
+
+/* Atom-centred Gaussians on the grid (device output, N doubles):
+ *   out(x) = sum_J q_J sum_images exp(-|x - R_J - images|^2 / width^2)
+ *            [/ (pi^{3/2} width^3) when normalised != 0],
+ * then, when total != 0, rescaled so that sum out dV = total.  With
+ * q_J = -Z, width = r_c, normalised and total = -Ne this is the Gaussian
+ * pseudocharge density b of the nuclei (Sec. 2, Eq. (poisson); its
+ * potential is the local pseudopotential -Z erf(r/r_c)/r per atom); with
+ * q = NULL (all 1) and total = Ne the atomic-superposition starting
+ * density; with q = NULL, total = 0 and normalised = 0 one radial
+ * descriptor of the learned starting density.  pos: HOST natoms x 3
+ * positions (bohr; any real values, the cell is periodic).  q: HOST natoms
+ * weights or NULL.  sum_out: HOST, receives sum out dV before rescaling
+ * (may be NULL).  Images are summed while the Gaussian exceeds exp(-784).
+ * Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOMEM, SQ3_ECUDA, SQ3_ENONFINITE. */
+int sq3_atom_gaussians(sq3_ctx* ctx, int natoms, const double* pos, const double* q,
+                       double width, int normalised, double total, double* out,
+                       double* sum_out);
+
+/* ---- Self-consistent-field driver (Sec. 2: the SCF loop; Sec. 4: the SQ3
+ * iteration inside each SCF iteration; Sec. 5: periodic Pulay mixing with a
+ * Kerker preconditioner). ---- */
+typedef struct sq3_scf_params {
+  int Ns;            /* auxiliary vectors (columns of X)                    */
+  int degree;        /* Chebyshev filter degree m                          */
+  int npl;           /* Fermi-operator degree; <= 0: chosen per iteration
+                        by sq3_fermi_degree(kT, xi, fermi_tol)            */
+  int first_passes;  /* filter + Cholesky QR passes in the first iteration */
+  int passes;        /* ... in every later iteration                       */
+  int max_iter;      /* SCF iterations before SQ3_ENOCONV                  */
+  int mix_history;   /* mixer history (1..8)                               */
+  int mix_period;    /* Pulay extrapolation every mix_period-th step       */
+  double kT;         /* sigma (Ha)                                         */
+  double Ne;         /* electrons, 0 < Ne < 2 Ns                           */
+  double tol;        /* stop when sum |rho_out - rho_in| dV / Ne < tol     */
+  double e_self;     /* self energy of the pseudocharges (Ha)              */
+  double mix_beta;   /* mixing parameter                                   */
+  double kerker_k0;  /* Kerker wave number (1/bohr); <= 0: none            */
+  double fermi_tol;  /* occupation tolerance of the adaptive degree        */
+  double filter_cut; /* first iteration without chi0/xi0: damped interval
+                        starts this fraction of the spectral width above its
+                        lower bound (<= 0: 0.05)                           */
+  double chi0, xi0;  /* xi0 > 0: spectral centre/half-width of the starting
+                        block's Hs (e.g. the previous solve's), which sets
+                        the first iteration's damped interval              */
+  double cut_shift;  /* the damped interval starts this far (Ha) above the
+                        largest Ritz value (0: at it)                      */
+} sq3_scf_params;
+
+typedef struct sq3_scf_result {
+  int iterations;    /* SCF iterations run                                 */
+  int converged;     /* 1 when err < tol                                   */
+  int npl_last;      /* Fermi-operator degree of the last iteration        */
+  int reserved;
+  double F;          /* free energy of the last output density (Ha)        */
+  double e_band, e_ent, mu;
+  double e_xc, vxc_rho, e_es;   /* the density terms of F                 */
+  double err;        /* last sum |rho_out - rho_in| dV / Ne               */
+  double chi, xi;    /* Lanczos bounds of the last Hs                      */
+  double b_up;       /* the filter's upper spectral bound, last iteration  */
+} sq3_scf_result;
+
+/* Values per iteration in the history array of sq3_scf_solve:
+ * err, mu, E_band, E_ent, F, npl, wall ms, chi, xi. */
+#define SQ3_SCF_HIST 9
+
+/* Converged SCF solve of one cell from a starting density and block.
+ * Each iteration: V_eff = phi[rho_in + b] + V_xc[rho_in] (as
+ * sq3_effective_potential) becomes the context's potential; the filter's
+ * upper bound is sq3_hamiltonian_bounds' out[1]; `passes` (first_passes in
+ * the first iteration) times X <- p_m(H) X and Cholesky QR, the damped
+ * interval [a, b] with a = lambda_max(Hs) + cut_shift, a0 = lambda_min(Hs)
+ * of the latest block's Lanczos bounds (the first pass of the first iteration uses
+ * chi0/xi0, or filter_cut); Hs = X^T H X, its 40-step Lanczos bounds, the
+ * density kernel Ds (sq3_kernel_from_hs with those bounds), rho_out
+ * (sq3_density), err = sum |rho_out - rho_in| dV / Ne, F of rho_out
+ * (sq3_free_energy with e_self); then, unless err < tol, rho_in is mixed
+ * (sq3_mixer_setup(mix_history, mix_period, mix_beta, kerker_k0) at the
+ * start, sq3_mixer_step each iteration).  Projectors, if any, are the
+ * context's (sq3_set_projectors) and stay fixed.
+ * b: device N doubles, the pseudocharge density (sum b dV = -Ne).
+ * rho: device N doubles; in: starting density; out: the converged output
+ * density (the last mixed input when not converged).  X: device block
+ * N x Ns of the precision's element type; in: starting block (random, or
+ * the previous solve's); out: the last orthonormal block.  D: device Ns x Ns
+ * doubles receiving the last Ds, or NULL.  res: HOST result.  history: HOST
+ * array of max_iter x SQ3_SCF_HIST doubles (row per iteration), or NULL.
+ * Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOCONV (max_iter reached; res
+ * holds the last iteration), and every error of the calls above. */
+int sq3_scf_solve(sq3_ctx* ctx, const sq3_scf_params* params, const double* b,
+                  double* rho, void* X, sq3_prec prec, double* D,
+                  sq3_scf_result* res, double* history);
+
 /* Self-test of the device-side failure path (no counterpart in the paper):
  * one CTA waits on an mbarrier that nothing completes, through the bounded
  * wait (about one second of wall time) that every TMA and tensor-core wait
@@ -299,10 +401,14 @@ int sq3_profile_read(sq3_ctx* ctx, double* ms, long long* launches,
  * is ordered on (NULL = legacy default stream); the call returns after that
  * stream has finished the work.  It needs no context, and calls no
  * cudaMalloc, cudaFree or allocating routine: its scratch is a fixed
- * device array inside the library, sized for Ns <= 8192 (2.7 MB), which
- * every GPU that loads the library holds until the process exits.  The
- * first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All
+ * device array inside the library, sized for Ns <= 8192 and 40 steps
+ * (349,304 doubles: 2.79 MB, 2.66 MiB), which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's device address (with the device current), and so does the
+ * first call after the device's context was reset or created anew (the
+ * address is cached per context); make that first call before any stream
+ * capture.  An error left pending by earlier, unrelated asynchronous work
+ * is cleared on entry and not reported by this call.  All
  * calls share the array and it keeps the previous call's contents, so two
  * calls whose GPU work overlaps (other streams, other host threads) race
  * and give wrong bounds: serialise them.

@@ -347,6 +347,7 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
     accumulate_d_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(
         T, nn, Ns, npl, coef, D);
   }
+  if (D != nullptr) check_finite(D, nn, ctx->dev_status, st);
   rc = cuda_err(cudaGetLastError());
   if (rc) return rc;
   rc = cuda_err(cudaMemcpyAsync(ctx->host_scal, outd, 6 * sizeof(double),
@@ -354,7 +355,10 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   if (rc) return rc;
   rc = check_device_status(ctx);
   if (rc) return rc;
-  for (int i = 0; i < 6; ++i) out_host[i] = ctx->host_scal[i];
+  for (int i = 0; i < 6; ++i) {
+    if (!isfinite(ctx->host_scal[i])) return SQ3_ENONFINITE;
+    out_host[i] = ctx->host_scal[i];
+  }
   return SQ3_OK;
 }
 

@@ -526,7 +526,38 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
+// per device: the address of the array and the id of the CUDA context it
+// was looked up in.  A device reset or a new primary context loads the
+// module again at another address, so the cache is keyed on the context.
 double* g_noalloc_addr[kMaxDevices] = {nullptr};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current CUDA context (0 if it cannot be read).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+    looked_up = true;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 }  // namespace
 
 }  // namespace sq3
@@ -541,18 +572,25 @@ extern "C" int sq3_lanczos_bounds_noalloc(const double* Hs, int Ns, double* boun
     cudaGetLastError();
     return SQ3_ECUDA;
   }
+  // an error left by earlier, unrelated asynchronous work is not this
+  // call's: clear it so that the check after the launches sees only ours
+  cudaGetLastError();
   double* scratch = nullptr;
   {
-    // first call on this device: look up the device address of the array
-    // with the device current (the host-side name is only a stand-in)
+    // first call on this device (and after its context changed): look up
+    // the device address of the array with the device current (the
+    // host-side name is only a stand-in)
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_noalloc_addr[dev] || cid == 0 || cid != g_noalloc_ctx[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
+        g_noalloc_addr[dev] = nullptr;
         return SQ3_ECUDA;
       }
       g_noalloc_addr[dev] = (double*)p;
+      g_noalloc_ctx[dev] = cid;
     }
     scratch = g_noalloc_addr[dev];
   }

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "async_copy.cuh"
@@ -93,6 +94,70 @@ static void fd_weights(int order, double* w) {
 __global__ void to_float_kernel(const double* a, float* b, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
+}
+
+// Sets DEV_NONFINITE when any of the n values is NaN or infinite.
+__global__ void check_finite_kernel(const double* __restrict__ a, long long n, int* status) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, DEV_OK, DEV_NONFINITE);
+}
+
+void check_finite(const double* a, long long n, int* status, cudaStream_t st) {
+  if (n <= 0) return;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 8);
+  check_finite_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, n, status);
+}
+
+// Smallest and largest value of a (n > 0) in a fixed reduction order:
+// per-block pairs into part[2 * blockIdx.x], then one block folds them into
+// out[0] = min, out[1] = max.  Non-finite values set DEV_NONFINITE.
+constexpr int MM_BLOCKS = 304;
+__global__ void __launch_bounds__(256) minmax_part_kernel(const double* __restrict__ a,
+                                                          long long n, double* part,
+                                                          int* status) {
+  __shared__ double smin[8], smax[8];
+  double lo = INFINITY, hi = -INFINITY;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    bad |= !isfinite(v);
+    lo = fmin(lo, v);
+    hi = fmax(hi, v);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, DEV_OK, DEV_NONFINITE);
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) { smin[threadIdx.x >> 5] = lo; smax[threadIdx.x >> 5] = hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, smin[w]); hi = fmax(hi, smax[w]); }
+    lo = fmin(lo, smin[0]);
+    hi = fmax(hi, smax[0]);
+    part[2 * blockIdx.x] = lo;
+    part[2 * blockIdx.x + 1] = hi;
+  }
+}
+
+__global__ void minmax_finish_kernel(const double* part, int nb, double* out) {
+  if (threadIdx.x != 0) return;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = 0; b < nb; ++b) { lo = fmin(lo, part[2 * b]); hi = fmax(hi, part[2 * b + 1]); }
+  out[0] = lo;
+  out[1] = hi;
+}
+
+// out[0..1] = min, max of the n device values (part: 2 * MM_BLOCKS doubles
+// of device scratch).
+void minmax(const double* a, long long n, double* part, double* out, int* status,
+            cudaStream_t st) {
+  minmax_part_kernel<<<MM_BLOCKS, 256, 0, st>>>(a, n, part, status);
+  minmax_finish_kernel<<<1, 32, 0, st>>>(part, MM_BLOCKS, out);
 }
 
 static void free_projectors(Projectors& P) {
@@ -403,7 +468,7 @@ void sq3_destroy(sq3_ctx* c) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
                   c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32,
-                  c->scfTab, c->wsScf, c->wsMix};
+                  c->scfTab, c->wsScf, c->wsMix, c->wsDrv, c->wsAtoms};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (c->host_scal) cudaFreeHost(c->host_scal);
   delete c;
@@ -454,8 +519,20 @@ int sq3_set_potential(sq3_ctx* c, const double* V) {
                                     cudaMemcpyDeviceToDevice, c->stream));
   if (rc) return rc;
   to_float_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->V, c->Vf, N);
-  c->pot_ok = true;
-  return finish(c, 0);
+  // range of the potential (the Chebyshev filter's spectral bounds use it)
+  // and a check that every value is finite
+  double* part = c->dev_scal + SQ3_SCAL_MISC;
+  double* mm = part + 2 * MM_BLOCKS;
+  minmax(c->V, N, part, mm, c->dev_status, c->stream);
+  rc = cuda_err(cudaMemcpyAsync(c->host_scal + 62, mm, 2 * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (rc) return finish(c, rc);
+  rc = finish(c, 0);
+  c->pot_ok = rc == SQ3_OK;
+  if (rc) return rc;
+  c->v_min = c->host_scal[62];
+  c->v_max = c->host_scal[63];
+  return SQ3_OK;
 }
 
 int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
@@ -469,10 +546,10 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
   const long long N = c->grid.N;
   for (int p = 0; p < n_proj; ++p)
-    if (ptr[p + 1] < ptr[p]) return SQ3_EINVAL;
+    if (ptr[p + 1] < ptr[p] || !isfinite(gamma[p])) return SQ3_EINVAL;
   const long long nnz = ptr[n_proj];
   for (long long e = 0; e < nnz; ++e)
-    if (idx[e] < 0 || idx[e] >= N) return SQ3_EINVAL;
+    if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
   const double sq = sqrt(c->dV);
   // group consecutive projectors with identical index lists (<= 4 per ball)
   std::vector<int> bptr{0}, bidx, bp0, bnp, boff;
@@ -523,6 +600,42 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
       for (int q = 0; q < 4; ++q)
         v4[q] = (q < bnp[B]) ? bval[(size_t)boff[B] + (size_t)q * len + pos] : 0.0;
     };
+    // Gershgorin bounds of V_nl: its nonzero eigenvalues are those of
+    // Gamma S, S_pq = c_p . c_q the overlaps of the projectors (formed per
+    // pair of balls that share a grid point)
+    {
+      std::vector<std::vector<std::pair<int, std::array<double, 16>>>> ov(nballs);
+      double v4a[4], v4b[4];
+      for (long long k = 0; k < N; ++k)
+        for (int i = kptr[k]; i < kptr[k + 1]; ++i) {
+          ball_val4(kball[i], kpos[i], v4a);
+          for (int j = kptr[k]; j < kptr[k + 1]; ++j) {
+            ball_val4(kball[j], kpos[j], v4b);
+            auto& row = ov[kball[i]];
+            size_t t = 0;
+            while (t < row.size() && row[t].first != kball[j]) ++t;
+            if (t == row.size()) row.push_back({kball[j], {}});
+            for (int q = 0; q < 4; ++q)
+              for (int r = 0; r < 4; ++r) row[t].second[4 * q + r] += v4a[q] * v4b[r];
+          }
+        }
+      double lo = 0.0, hi = 0.0;
+      for (int B = 0; B < nballs; ++B)
+        for (int q = 0; q < bnp[B]; ++q) {
+          const int pq = bp0[B] + q;
+          double diag = 0.0, rad = 0.0;
+          for (auto& e : ov[B])
+            for (int r = 0; r < bnp[e.first]; ++r) {
+              const double v = gamma[pq] * e.second[4 * q + r];
+              if (e.first == B && r == q) diag = v;
+              else rad += fabs(v);
+            }
+          lo = std::min(lo, diag - rad);
+          hi = std::max(hi, diag + rad);
+        }
+      P.vnl_lo = lo;
+      P.vnl_hi = hi;
+    }
     std::vector<int> qptr{0}, sptr{0}, spid, zptr{0};
     std::vector<short> qlb, zpt;
     std::vector<double> qval, zval;
@@ -798,6 +911,8 @@ int sq3_density(sq3_ctx* c, const void* X, const double* D, int Ns,
   if (prec == SQ3_FP64) rc = density_f64(c, (const double*)X, D, Ns, rho);
   else if (prec == SQ3_MIXED) rc = density_mixed(c, (const float*)X, D, Ns, rho);
   else return SQ3_EINVAL;
+  // a NaN or infinity anywhere in X or D reaches rho: report it
+  if (rc == SQ3_OK) check_finite(rho, c->grid.N, c->dev_status, c->stream);
   return finish(c, rc);
 }
 

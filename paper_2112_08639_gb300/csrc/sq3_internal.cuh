@@ -12,7 +12,11 @@
 
 #define SQ3_MAX_FD_RADIUS 6
 #define SQ3_MAX_NPL 1000
-#define SQ3_DEV_SCAL 2304
+#define SQ3_DEV_SCAL 3072
+// dev_scal slots: 0..63 bounds/outputs/norms, 64..2065 Fermi-operator
+// moments and coefficients, from SQ3_SCAL_MISC: the potential's range
+// (2 values + 2 x 304 partials) and the SCF driver's scalars
+#define SQ3_SCAL_MISC 2304
 // bf16 pieces per FP32 operand in the mixed path (3 pieces, 6 products)
 #define MIXED_PIECES 3
 // largest Ns accepted by sq3_lanczos_bounds_noalloc (static scratch size)
@@ -72,6 +76,9 @@ struct Projectors {
   float* nb_bl_valf = nullptr;
   int max_brick_balls = 0;     // most balls touching one brick
   int max_brick_entries = 0;   // most (point, ball) entries in one brick
+  // Gershgorin bounds on the spectrum of V_nl = sum_p gamma_p c_p c_p^T
+  // (from the projectors' overlap matrix): vnl_lo <= lambda <= vnl_hi
+  double vnl_lo = 0.0, vnl_hi = 0.0;
 };
 
 }  // namespace sq3
@@ -126,6 +133,11 @@ struct sq3_ctx {
     double beta = 0.0, k0 = 0.0;
   } mix;
   double* wsMix = nullptr; size_t wsMix_bytes = 0;
+  // SCF driver (sq3_scf_solve): output density, V_eff, Hs, Ds, Lanczos work
+  double* wsDrv = nullptr; size_t wsDrv_bytes = 0;
+  // atom-centred Gaussians and forces (atoms.cu, forces.cu): 1-D tables,
+  // charges, partial sums
+  double* wsAtoms = nullptr; size_t wsAtoms_bytes = 0;
   // uploads of a host block (sq3_cheb_filter_from_host): a stream of their
   // own and one event per chunk, created on first use
   cudaStream_t copy_stream = nullptr;
@@ -146,6 +158,13 @@ struct Prof {
 };
 int cuda_err(cudaError_t e);
 int check_device_status(sq3_ctx* ctx);
+// Sets DEV_NONFINITE in *status when one of the n device values is not finite.
+void check_finite(const double* a, long long n, int* status, cudaStream_t st);
+// out[0], out[1] = smallest and largest of the n device values (fixed-order
+// reduction; part: 608 doubles of device scratch); non-finite values set
+// DEV_NONFINITE.
+void minmax(const double* a, long long n, double* part, double* out, int* status,
+            cudaStream_t st);
 // Tiled TMA tensor map over a dense array (FP32 or FP64 elements), no
 // swizzle, zero fill; dims and box innermost first, strides in bytes for
 // dims 1..rank-1.  Returns SQ3_OK, SQ3_EINVAL (alignment) or SQ3_ECUDA.

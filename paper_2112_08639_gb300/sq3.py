@@ -59,11 +59,38 @@ _sigs = {
     "sq3_mixer_setup": (_i, [_p, _i, _i, _d, _d]),
     "sq3_mixer_step": (_i, [_p, _p, _p, _p]),
     "sq3_fermi_degree": (_i, [_d, _d, _d]),
+    "sq3_hamiltonian_bounds": (_i, [_p, _p]),
+    "sq3_scf_solve": (_i, [_p, _p, _p, _p, _p, _i, _p, _p, _p]),
+    "sq3_atom_gaussians": (_i, [_p, _i, _p, _p, _d, _i, _d, _p, _p]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
     _f.restype = _res
     _f.argtypes = _args
+
+
+class ScfParams(ctypes.Structure):
+    """sq3_scf_params (include/sq3.h)."""
+    _fields_ = [("Ns", _i), ("degree", _i), ("npl", _i), ("first_passes", _i), ("passes", _i),
+                ("max_iter", _i), ("mix_history", _i), ("mix_period", _i), ("kT", _d), ("Ne", _d),
+                ("tol", _d), ("e_self", _d), ("mix_beta", _d), ("kerker_k0", _d),
+                ("fermi_tol", _d), ("filter_cut", _d), ("chi0", _d), ("xi0", _d),
+                ("cut_shift", _d)]
+
+
+class ScfResult(ctypes.Structure):
+    """sq3_scf_result (include/sq3.h)."""
+    _fields_ = [("iterations", _i), ("converged", _i), ("npl_last", _i), ("reserved", _i),
+                ("F", _d), ("e_band", _d), ("e_ent", _d), ("mu", _d), ("e_xc", _d),
+                ("vxc_rho", _d), ("e_es", _d), ("err", _d), ("chi", _d), ("xi", _d),
+                ("b_up", _d)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+SCF_HIST = 9
+SCF_HIST_KEYS = ("err", "mu", "e_band", "e_ent", "F", "npl", "ms", "chi", "xi")
 
 
 class SQ3Error(RuntimeError):
@@ -287,6 +314,62 @@ class Context:
         _check(lib.sq3_mixer_step(self._h, self._grid_vec(x_in), self._grid_vec(x_out),
                                   self._grid_vec(x_next)), "sq3_mixer_step")
         return x_next
+
+    def atom_gaussians(self, positions, width: float, q=None, normalised: bool = True,
+                       total: float = 0.0, out: torch.Tensor | None = None):
+        """(out, sum dV before rescaling) of sum_J q_J Gaussians of the given
+        width around the atoms (periodic images included)."""
+        pos = np.ascontiguousarray(positions, dtype=np.float64)
+        qa = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        s = ctypes.c_double()
+        _check(lib.sq3_atom_gaussians(self._h, pos.shape[0], pos.ctypes.data,
+                                      None if qa is None else qa.ctypes.data, width,
+                                      int(normalised), total, self._grid_vec(out),
+                                      ctypes.byref(s)), "sq3_atom_gaussians")
+        return out, s.value
+
+    def pseudocharge(self, positions, Z: float, rc: float, out: torch.Tensor | None = None):
+        """Gaussian pseudocharges b (sum b dV = -Z natoms) and the sum before
+        rescaling."""
+        n = len(positions)
+        return self.atom_gaussians(positions, rc, q=np.full(n, -Z), normalised=True,
+                                   total=-Z * n, out=out)
+
+    def hamiltonian_bounds(self) -> tuple[float, float]:
+        """Rigorous (lower, upper) bounds of the spectrum of H."""
+        out = (ctypes.c_double * 2)()
+        _check(lib.sq3_hamiltonian_bounds(self._h, out), "sq3_hamiltonian_bounds")
+        return out[0], out[1]
+
+    def scf_solve(self, b: torch.Tensor, rho: torch.Tensor, X: torch.Tensor, *, degree: int,
+                  npl: int, kT: float, Ne: float, e_self: float, tol: float = 1e-6,
+                  prec=FP64, first_passes: int = 4, passes: int = 1, max_iter: int = 100,
+                  mix_history: int = 7, mix_period: int = 2, mix_beta: float = 0.3,
+                  kerker_k0: float = 0.8, fermi_tol: float = 0.0, filter_cut: float = 0.0,
+                  cut_shift: float = 0.0, bounds0=None, D: torch.Tensor | None = None, raise_on_noconv: bool = True):
+        """Converged SCF solve (sq3_scf_solve).  rho (in: start, out: the
+        converged density) and X (in: starting block, out: last block) are
+        updated in place.  Returns (result dict, list of per-iteration dicts)."""
+        if X.dtype != _prec_dtype(prec):
+            raise ValueError("X dtype does not match the precision")
+        p = ScfParams(Ns=X.shape[0], degree=degree, npl=npl, first_passes=first_passes,
+                      passes=passes, max_iter=max_iter, mix_history=mix_history,
+                      mix_period=mix_period, kT=kT, Ne=Ne, tol=tol, e_self=e_self,
+                      mix_beta=mix_beta, kerker_k0=kerker_k0, fermi_tol=fermi_tol,
+                      filter_cut=filter_cut,
+                      chi0=bounds0[0] if bounds0 is not None else 0.0,
+                      xi0=bounds0[1] if bounds0 is not None else 0.0, cut_shift=cut_shift)
+        r = ScfResult()
+        hist = (ctypes.c_double * (max_iter * SCF_HIST))()
+        code = lib.sq3_scf_solve(self._h, ctypes.byref(p), self._grid_vec(b), self._grid_vec(rho),
+                                 _ptr(X), prec, _ptr(D), ctypes.byref(r), hist)
+        rows = [dict(zip(SCF_HIST_KEYS, hist[i * SCF_HIST:(i + 1) * SCF_HIST]))
+                for i in range(r.iterations)]
+        if code != OK and not (code == ENOCONV and not raise_on_noconv):
+            raise SQ3Error(code, "sq3_scf_solve")
+        return r.as_dict(), rows
 
     STAGES = ("stencil", "nl_project", "gram", "cholesky", "tri_inverse", "x_rinv",
               "hs_gemm", "lanczos", "cheb_gemm", "fermi", "d_accum", "rho", "split", "copy", "nl_pass")

@@ -97,6 +97,11 @@ def test_argument_errors_before_any_device_work(libpath):
         "sq3_kerker": ([p, p, p, d], (None, None, None, 0.8), EINVAL),
         "sq3_mixer_setup": ([p, i, i, d, d], (None, 7, 2, 0.3, 0.8), EINVAL),
         "sq3_mixer_step": ([p, p, p, p], (None, None, None, None), EINVAL),
+        "sq3_hamiltonian_bounds": ([p, p], (None, None), EINVAL),
+        "sq3_atom_gaussians": ([p, i, p, p, d, i, d, p, p], (None, 1, None, None, 1.0, 1, 0.0,
+                                                            None, None), EINVAL),
+        "sq3_scf_solve": ([p, p, p, p, p, i, p, p, p], (None,) * 5 + (0, None, None, None),
+                          EINVAL),
     }
     for name, (argtypes, args, want) in calls.items():
         f = getattr(lib, name)

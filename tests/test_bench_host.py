@@ -17,7 +17,7 @@ def _entry(kind, ms=2.0, n=2, fp64=False, n_covered=None):
     prof = {kind: (ms, n)}
     esize = 8 if fp64 else 4
     return bench.roofline(kind, prof, cfg, esize, fp64, PK, "test",
-                          1, cfg.N if n_covered is None else n_covered), cfg
+                          cfg.N if n_covered is None else n_covered), cfg
 
 
 def test_stencil_fp32_is_three_words_per_point_and_vector():
@@ -55,3 +55,23 @@ def test_fp64_paths_report_against_the_derived_fp64_peak():
     assert r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(80 * cfg.N * cfg.Ns / 1e-3 / 1e12, abs=1e-3)
     assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12, abs=1e-4)
+
+
+@pytest.mark.parametrize("Ns", [640, 2200])
+def test_symmetric_gemm_flops_against_the_tile_schedule(Ns):
+    """The Gram product computes only the 128 x 128 output tiles on or above
+    the diagonal (nt (nt + 1) / 2 of nt^2): the multiply-adds those tiles
+    issue, 128^2 N per tile, bound the bench's useful count N Ns^2 (the
+    product's upper triangle with the diagonal, 2 N Ns (Ns + 1) / 2 flops)
+    from above, and exceed it only by the diagonal tiles' lower halves and
+    the padding of the last tile row."""
+    N = inputs.C3.N
+    nt = (Ns + 127) // 128
+    tiles = nt * (nt + 1) // 2
+    issued = 2 * 128 * 128 * N * tiles
+    useful = N * Ns * Ns
+    exact_upper = N * Ns * (Ns + 1)
+    assert exact_upper >= useful
+    assert issued >= exact_upper
+    pad = nt * 128
+    assert issued <= 2 * N * pad * (pad + 128) / 2 + 1
