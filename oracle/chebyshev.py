@@ -94,6 +94,29 @@ def filter_plain(apply_H, X: np.ndarray, m: int, a: float, b: float, a0: float):
     return z / cheb_T(m, np.array([(a0 - c) / e]))[0]
 
 
+def fermi_level_series(moments, sigma: float, Ne: float, chi: float, xi: float,
+                       M: int | None = None, max_halvings: int = 200) -> float:
+    """mu of Eq. (FermiLevelCalc): 2 sum'_j c_j(mu) m_j = Ne, by bisection on
+    [chi - xi - 40 sigma, chi + xi + 40 sigma] with c_j(mu) re-evaluated by
+    quadrature at every trial mu, until the bracket cannot shrink."""
+    npl = len(moments) - 1
+
+    def count(mu):
+        c, _, _ = fermi_coeffs(mu, sigma, chi, xi, npl, M)
+        return 2.0 * primed_sum(c, moments)
+
+    lo, hi = chi - xi - 40.0 * sigma, chi + xi + 40.0 * sigma
+    for _ in range(max_halvings):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if count(mid) < Ne:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
 def foe_density_kernel(Hs: np.ndarray, npl: int, sigma: float, Ne: float,
                        chi: float, xi: float, M: int | None = None,
                        max_halvings: int = 200) -> dict:
@@ -117,20 +140,7 @@ def foe_density_kernel(Hs: np.ndarray, npl: int, sigma: float, Ne: float,
         T_prev, T = T, 2.0 * Hhat @ T - T_prev
         moments[j + 1] = np.trace(T)
 
-    def count(mu):
-        c, _, _ = fermi_coeffs(mu, sigma, chi, xi, npl, M)
-        return 2.0 * primed_sum(c, moments)
-
-    lo, hi = chi - xi - 40.0 * sigma, chi + xi + 40.0 * sigma
-    for _ in range(max_halvings):
-        mid = 0.5 * (lo + hi)
-        if mid <= lo or mid >= hi:
-            break
-        if count(mid) < Ne:
-            lo = mid
-        else:
-            hi = mid
-    mu = 0.5 * (lo + hi)
+    mu = fermi_level_series(moments, sigma, Ne, chi, xi, M, max_halvings)
     c, d, e = fermi_coeffs(mu, sigma, chi, xi, npl, M)
 
     D = 0.5 * c[0] * np.eye(Ns)

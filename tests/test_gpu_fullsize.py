@@ -116,9 +116,10 @@ def test_density_fullsize_sampled_points(orthonormal):
 
 
 def test_kernel_fullsize_known_spectrum():
-    """Ns = 2200, n_pl = 120: D against sum'_j c_j(mu) T_j evaluated on the
-    known eigenvalues (the exact value of the same expansion), mu against
-    the electron count of that expansion, 2 tr D = Ne."""
+    """Ns = 2200, n_pl = 120: mu against the oracle's Fermi level of the
+    same expansion on the known eigenvalues (1e-6 Ha), D against
+    sum'_j c_j(mu) T_j evaluated there (the exact value of the expansion),
+    2 tr D = Ne."""
     cell, _ = c3()
     cfg = cell.cfg
     Ns = cfg.Ns
@@ -132,9 +133,16 @@ def test_kernel_fullsize_known_spectrum():
     ctx = context_for(inputs.make_cell(inputs.C1))
     D, out = ctx.kernel_from_hs(torch.from_numpy(Hs).cuda(), cfg.npl, cfg.sigma, Ne,
                                 bounds=(chi, xi), prec=sq3().MIXED)
-    c, _, _ = chebyshev.fermi_coeffs(out["mu"], cfg.sigma, chi, xi, cfg.npl)
-    g = chebyshev.series_scalar(c, (lam - chi) / xi)
+    # the Fermi level of the same expansion, independent of the GPU: the
+    # moments m_j = sum_n T_j(x_n) of the known spectrum and the oracle's
+    # bisection on Eq. (FermiLevelCalc)
+    x = (lam - chi) / xi
+    moments = np.array([np.sum(chebyshev.cheb_T(j, x)) for j in range(cfg.npl + 1)])
+    mu_ref = chebyshev.fermi_level_series(moments, cfg.sigma, Ne, chi, xi)
+    assert abs(out["mu"] - mu_ref) < 1e-6
+    c, _, _ = chebyshev.fermi_coeffs(mu_ref, cfg.sigma, chi, xi, cfg.npl)
+    g = chebyshev.series_scalar(c, x)
     Dref = (Q * g) @ Q.T
     assert np.max(np.abs(D.cpu().numpy() - Dref)) < 2e-5
-    assert abs(2.0 * np.sum(g) - Ne) < 1e-3 * Ne
+    assert abs(2.0 * np.sum(g) - Ne) < 1e-9 * Ne
     assert abs(out["two_tr_D"] - Ne) < 1e-6 * Ne
