@@ -165,6 +165,27 @@ int sq3_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                        double kT, double Ne, sq3_prec prec,
                        const double* bounds_in, double* D, double* out);
 
+/* The density kernel of sq3_kernel_from_hs with two options (Sec. 4 picks
+ * n_pl by hand; Sec. 5 notes that the degree needed falls as T rises):
+ * - npl < 1: the degree is chosen after the spectral bounds are known, as
+ *   sq3_fermi_degree(kT, xi, fermi_tol) (capped at 1000); *npl_used (HOST,
+ *   may be NULL) receives the degree used.
+ * - eval_mode SQ3_EVAL_PATERSON_STOCKMEYER (FP64 only): the same polynomial
+ *   sum'_j c_j T_j(Hhat) evaluated with O(sqrt(npl)) matrix products: s =
+ *   ceil(sqrt(2 npl)) baby steps T_0..T_s, giant steps T_{qs} = T_q(T_s)
+ *   (the Chebyshev composition identity) for the moments m_{qs+r} =
+ *   2 tr(T_{qs} T_r) - m_{qs-r}, and Ds = sum_q A_q T_q(T_s) by Clenshaw's
+ *   recurrence in T_s with A_q = sum_{r<s} alpha_{qr} T_r
+ *   ((s - 1) + 2 floor(npl/s) - 1 products instead of npl - 1); equal to
+ *   the recurrence up to rounding.
+ * Other arguments and errors as sq3_kernel_from_hs (SQ3_EINVAL for the
+ * Paterson-Stockmeyer mode with SQ3_MIXED). */
+#define SQ3_EVAL_RECURRENCE 0
+#define SQ3_EVAL_PATERSON_STOCKMEYER 1
+int sq3_kernel_from_hs_ex(sq3_ctx* ctx, const double* Hs, int Ns, int npl, double fermi_tol,
+                          int eval_mode, double kT, double Ne, sq3_prec prec,
+                          const double* bounds_in, double* D, double* out, int* npl_used);
+
 /* sq3_project followed by sq3_kernel_from_hs: the density-kernel step of one
  * SQ3 iteration.  Hs_out (device, may be NULL) receives Hs. */
 int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
@@ -283,6 +304,88 @@ int sq3_atom_gaussians(sq3_ctx* ctx, int natoms, const double* pos, const double
                        double width, int normalised, double total, double* out,
                        double* sum_out);
 
+/* Hellmann-Feynman forces on the nuclei (Sec. 3, Eq. (force:NewForm); Sec. 2,
+ * Eq. (ON:forces)) for the Gaussian pseudocharges of sq3_atom_gaussians
+ * (charge -Z, width rc, rescaled to sum b dV = -Ne) and the context's
+ * projectors:
+ *   f_I = sum_x grad b_I(x) phi(x) dV
+ *         + 4 sum_{p of I} gamma_p (X^T c_p)^T D (X^T grad_h c_p),
+ * the second line being the nonlocal term -4 sum gamma (c . u_i)
+ * (c . grad_h u~_i) of Eq. (force:NewForm) with u~ = X D, rewritten by the
+ * antisymmetry of the periodic FD first derivative grad_h (of the
+ * Laplacian's order); f_sc = 0 (E_self is constant, E_c = 0).
+ * phi: device N doubles, the electrostatic potential of rho + b
+ * (sq3_effective_potential's phi).  X: device N x Ns block (precision's
+ * type), D: device Ns x Ns density kernel (both ignored, may be NULL,
+ * without projectors).  atom_of: HOST array of n_proj atom indices (NULL
+ * without projectors).  forces: HOST natoms x 3 (Ha/bohr).  parts: HOST
+ * natoms x 3 x 2 {local, nonlocal} or NULL.  The first call after
+ * sq3_set_projectors tabulates grad_h c on the host.
+ * Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENOMEM, SQ3_ECUDA, SQ3_ENONFINITE. */
+int sq3_forces(sq3_ctx* ctx, int natoms, const double* pos, double Z, double rc, double Ne,
+               const double* phi, const void* X, const double* D, int Ns, sq3_prec prec,
+               const int* atom_of, double* forces, double* parts);
+
+/* Velocity Verlet for the QMD of the nuclei (Sec. 5 runs QMD on the forces
+ * of Eq. (force:NewForm)); host arithmetic on HOST arrays, no GPU work.
+ * A step from (R, V, F(R)) is: phase 0, V += dt F / (2 m), R += dt V; the
+ * caller then computes F at the new R (SCF and sq3_forces); phase 1,
+ * V += dt F / (2 m), and when ke_target > 0 the velocities are rescaled
+ * to that kinetic energy (the isokinetic ensemble the paper's QMD uses,
+ * held by rescaling after every step).  R, V, F: natoms x 3 (bohr,
+ * bohr per atomic time unit, Ha/bohr); masses: natoms electron masses;
+ * dt in atomic time units.  Errors: SQ3_EINVAL. */
+int sq3_verlet(int natoms, const double* masses, double dt, double* R, double* V,
+               const double* F, int phase, double ke_target);
+
+/* ---- Learned starting density (the paper has no counterpart: it does
+ * not say how each SCF starts).  A multilayer perceptron over atom-centred
+ * Gaussian descriptors predicts the density of a cell from its atom
+ * positions; it is trained on self-consistent densities the method itself
+ * produced.  Per grid point x of the context's grid:
+ *   d_k(x) = sum_J sum_images exp(-|x - R_J|^2 / w_k^2) / m_k,
+ *            m_k = natoms pi^{3/2} w_k^3 / Omega (mean 1 over the cell)
+ *   h1 = tanh(W1 d + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3)
+ *        (128 units each), y = softplus(w4 . h3 + b4),
+ *   rho(x) = Ne y(x) / (sum_x y dV);
+ * loss L = sum_x (rho(x) - rho_ref(x))^2 dV.  The three matrix products of
+ * each pass and the weight gradients run on the tensor cores with BF16
+ * operands and FP32 accumulation; activations, the output layer and the
+ * reductions in FP32/FP64; Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32
+ * master weights.  Parameters, as one FP32 array: W1 [128][F] row-major,
+ * b1 [128], W2 [128][128], b2, W3 [128][128], b3, w4 [128], b4 [1]. ---- */
+typedef struct sq3_mlp sq3_mlp;
+
+/* A model for the context's grid with n_features (1..16) descriptor widths
+ * (HOST array, bohr), weights initialised from `seed` (N(0, 1/fan_in),
+ * biases 0).  Errors: SQ3_EINVAL, SQ3_ENOTSETUP (no grid), SQ3_ENOMEM. */
+int sq3_mlp_create(sq3_ctx* ctx, int n_features, const double* widths, int seed,
+                   sq3_mlp** out);
+/* Release a model; it may be released after its context (it does not
+ * touch the context), but no other call may use it once the context is
+ * destroyed. */
+void sq3_mlp_destroy(sq3_mlp* mlp);
+/* Number of parameters (128 F + 33,281). */
+int sq3_mlp_num_params(const sq3_mlp* mlp);
+/* HOST arrays of sq3_mlp_num_params floats.  Setting resets Adam. */
+int sq3_mlp_set_params(sq3_mlp* mlp, const float* params);
+int sq3_mlp_get_params(sq3_mlp* mlp, float* params);
+/* Descriptors of the grid for natoms positions (HOST natoms x 3, bohr);
+ * the features every later predict/gradient/train call uses. */
+int sq3_mlp_features(sq3_mlp* mlp, int natoms, const double* pos);
+/* rho (device, N doubles) = the model's density with Ne electrons. */
+int sq3_mlp_predict(sq3_mlp* mlp, double Ne, double* rho);
+/* Loss against rho_ref (device, N doubles) and its gradient (HOST array of
+ * num_params doubles, or NULL); rho_scratch: device N doubles receiving
+ * the prediction.  Errors: SQ3_EINVAL, SQ3_ENOTSETUP (no features),
+ * SQ3_ENONFINITE. */
+int sq3_mlp_gradient(sq3_mlp* mlp, const double* rho_ref, double Ne, double* rho_scratch,
+                     double* loss, double* grad);
+/* One Adam step of size lr on the gradient of sq3_mlp_gradient; loss:
+ * HOST, the loss before the step. */
+int sq3_mlp_train_step(sq3_mlp* mlp, const double* rho_ref, double Ne, double lr,
+                       double* rho_scratch, double* loss);
+
 /* ---- Self-consistent-field driver (Sec. 2: the SCF loop; Sec. 4: the SQ3
  * iteration inside each SCF iteration; Sec. 5: periodic Pulay mixing with a
  * Kerker preconditioner). ---- */
@@ -311,6 +414,9 @@ typedef struct sq3_scf_params {
                         the first iteration's damped interval              */
   double cut_shift;  /* the damped interval starts this far (Ha) above the
                         largest Ritz value (0: at it)                      */
+  int kernel_eval;   /* SQ3_EVAL_RECURRENCE or SQ3_EVAL_PATERSON_STOCKMEYER
+                        (FP64 only), as sq3_kernel_from_hs_ex             */
+  int reserved;
 } sq3_scf_params;
 
 typedef struct sq3_scf_result {

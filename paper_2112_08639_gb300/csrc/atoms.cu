@@ -166,3 +166,29 @@ extern "C" int sq3_atom_gaussians(sq3_ctx* c, int natoms, const double* pos, con
   if (sum_out) *sum_out = c->host_scal[60];
   return SQ3_OK;
 }
+
+// Velocity-Verlet halves on host arrays (the QMD of Sec. 5 moves the nuclei
+// on the forces of Eq. (force:NewForm)); see sq3.h.
+extern "C" int sq3_verlet(int natoms, const double* masses, double dt, double* R, double* V,
+                          const double* F, int phase, double ke_target) {
+  if (natoms < 1 || !masses || !V || !F || !(dt > 0) || !isfinite(dt) || (phase != 0 && phase != 1) ||
+      (phase == 0 && !R) || !isfinite(ke_target))
+    return SQ3_EINVAL;
+  for (int I = 0; I < natoms; ++I)
+    if (!(masses[I] > 0)) return SQ3_EINVAL;
+  for (int I = 0; I < natoms; ++I)
+    for (int a = 0; a < 3; ++a) {
+      V[3 * I + a] += 0.5 * dt * F[3 * I + a] / masses[I];
+      if (phase == 0) R[3 * I + a] += dt * V[3 * I + a];
+    }
+  if (phase == 1 && ke_target > 0) {
+    double ke = 0.0;
+    for (int I = 0; I < natoms; ++I)
+      for (int a = 0; a < 3; ++a) ke += 0.5 * masses[I] * V[3 * I + a] * V[3 * I + a];
+    if (ke > 0) {
+      const double f = sqrt(ke_target / ke);
+      for (int k = 0; k < 3 * natoms; ++k) V[k] *= f;
+    }
+  }
+  return SQ3_OK;
+}

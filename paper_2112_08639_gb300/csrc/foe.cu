@@ -18,6 +18,9 @@
 // Ds is a weighted sum of stored matrices instead of a second recurrence.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "sq3_internal.cuh"
 
 namespace sq3 {
@@ -248,9 +251,228 @@ __global__ void accumulate_d_kernel(const double* __restrict__ T, long long nn,
   D[e] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Paterson-Stockmeyer evaluation (FP64): the same polynomial of Hhat,
+// reordered so that it takes O(sqrt(npl)) matrix products instead of npl.
+// With s baby steps T_0 .. T_s and Y = T_s, every T_{qs} = T_q(Y) (the
+// Chebyshev composition identity T_q(T_s(x)) = T_{qs}(x)):
+//   giant steps   G_{q+1} = 2 Y G_q - G_{q-1}, G_0 = I, G_1 = Y
+//   moments       m_{qs+r} = 2 tr(G_q T_r) - m_{qs-r}   (T_a T_b =
+//                 (T_{a+b} + T_{|a-b|}) / 2; tr(G_q T_r) is a Frobenius
+//                 product of symmetric matrices, no further product)
+//   kernel        sum'_j c_j T_j = sum_{q=0}^{Q} A_q T_q(Y),
+//                 A_q = sum_{r<s} alpha_{q,r} T_r, the alpha found top-down
+//                 (T_r T_{qs} = (T_{qs+r} + T_{qs-r}) / 2), and the outer
+//                 sum by Clenshaw's recurrence in Y:
+//                 b_q = A_q + 2 Y b_{q+1} - b_{q+2},  Ds = A_0 + Y b_1 - b_2.
+// Products: (s - 1) + (Q - 1) + Q with Q = floor(npl / s), s = ceil(sqrt(2 npl)).
+// ---------------------------------------------------------------------------
+constexpr int PS_FROB_BLOCKS = 16;   // blocks per Frobenius product
+
+// part[(pair) * PS_FROB_BLOCKS + b]: block sums of <G_q, T_r>, pair =
+// (q - 1) (s - 1) + (r - 1); G_q at gq[q], T_r at T + r nn.
+__global__ void __launch_bounds__(256) ps_frob_kernel(const double* const* __restrict__ gq,
+                                                      const double* __restrict__ T, long long nn,
+                                                      int s, double* part) {
+  __shared__ double sh[8];
+  const int pair = blockIdx.x / PS_FROB_BLOCKS, blk = blockIdx.x % PS_FROB_BLOCKS;
+  const int q = pair / (s - 1) + 1, r = pair % (s - 1) + 1;
+  const double* A = gq[q];
+  const double* B = T + (long long)r * nn;
+  double acc = 0.0;
+  for (long long e = (long long)blk * blockDim.x + threadIdx.x; e < nn;
+       e += (long long)PS_FROB_BLOCKS * blockDim.x)
+    acc += A[e] * B[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// m_{qs + r} = 2 <G_q, T_r> - m_{qs - r}, in increasing q (one thread).
+__global__ void ps_moments_kernel(const double* __restrict__ part, int s, int Q, int npl,
+                                  double* mom) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 1; q <= Q; ++q)
+    for (int r = 1; r < s; ++r) {
+      const int j = q * s + r;
+      if (j > npl) continue;
+      const int pair = (q - 1) * (s - 1) + (r - 1);
+      double f = 0.0;
+      for (int b = 0; b < PS_FROB_BLOCKS; ++b) f += part[pair * PS_FROB_BLOCKS + b];
+      mom[j] = 2.0 * f - mom[q * s - r];
+    }
+}
+
+// alpha[q s + r] from the coefficients c_j (c_0 halved), top-down; w: work
+// of (Q + 1) s doubles (one thread).
+__global__ void ps_alpha_kernel(const double* __restrict__ coef, int npl, int s, int Q,
+                                double* w, double* alpha) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int top = (Q + 1) * s;
+  for (int j = 0; j < top; ++j) w[j] = j <= npl ? (j == 0 ? 0.5 * coef[0] : coef[j]) : 0.0;
+  for (int q = Q; q >= 1; --q) {
+    alpha[q * s] = w[q * s];
+    for (int r = 1; r < s; ++r) {
+      alpha[q * s + r] = 2.0 * w[q * s + r];
+      w[q * s - r] -= w[q * s + r];
+    }
+  }
+  for (int r = 0; r < s; ++r) alpha[r] = w[r];
+}
+
+// out = ea E + eb Bm + sum_{r<s} alpha[r] T_r (E, Bm may be null; out may
+// alias E).
+__global__ void __launch_bounds__(256) ps_combine_kernel(double* out, const double* E, double ea,
+                                                         const double* __restrict__ Bm, double eb,
+                                                         const double* __restrict__ T, long long nn,
+                                                         int s, const double* __restrict__ alpha) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int r = 0; r < s; ++r) v += alpha[r] * T[(long long)r * nn + e];
+    if (E) v += ea * E[e];
+    if (Bm) v += eb * Bm[e];
+    out[e] = v;
+  }
+}
+
+// Pointers into the Paterson-Stockmeyer workspace (T = ctx->wsT).
+struct PsWs {
+  double* baby;        // T_0 .. T_s
+  double* giant;       // G_2 .. G_Q
+  double* b[3];        // Clenshaw buffers
+  double* part;        // Frobenius partials
+  double* alpha;       // (Q + 1) s
+  double* work;        // (Q + 1) s
+  double** gptr;       // device pointers G_0 .. G_Q (Q + 2 slots)
+};
+static PsWs ps_ws(double* T, long long nn, int s, int Q) {
+  PsWs w;
+  w.baby = T;
+  w.giant = T + (long long)(s + 1) * nn;
+  double* p = w.giant + (long long)std::max(Q - 1, 0) * nn;
+  for (int k = 0; k < 3; ++k) { w.b[k] = p; p += nn; }
+  w.part = p; p += (size_t)Q * s * PS_FROB_BLOCKS;
+  w.alpha = p; p += (size_t)(Q + 1) * s;
+  w.work = p; p += (size_t)(Q + 1) * s;
+  w.gptr = reinterpret_cast<double**>(p);
+  return w;
+}
+// C = 2 A B - P (FP64 GEMM with the Chebyshev epilogue), trace of C into tr
+static void cheb_product(const double* A, const double* B, const double* P, double* C, int Ns,
+                         double* tr, cudaStream_t st) {
+  GemmArgs g{};
+  g.M = Ns; g.N = Ns; g.K = Ns;
+  g.A = A; g.lda = Ns; g.a_kcontig = false;
+  g.B = B; g.ldb = Ns; g.b_kcontig = true;
+  g.C = C; g.ldc = Ns;
+  g.P = P; g.ldp = Ns;
+  g.trace = tr;
+  g.alpha = 1.0; g.splits = 1;
+  gemm_f64(g, EPI_CHEB, st);
+}
+
+// Moments m_0 .. m_npl by baby steps, giant steps and Frobenius products.
+int ps_moments_f64(sq3_ctx* ctx, const double* Hs, int Ns, int npl, int s, int Q,
+                   const double* bounds, double* mom, double* T) {
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)Ns * Ns;
+  const PsWs w = ps_ws(T, nn, s, Q);
+  const int sb = std::min(s, npl);            // baby steps actually needed
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    hhat_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Hs, w.baby, w.baby + nn, Ns,
+                                                              bounds, mom, npl);
+    trace_kernel<<<1, 1024, 0, st>>>(w.baby + nn, Ns, mom + 1);
+  }
+  {
+    Prof p(ctx, ST_CHEB_GEMM, std::max(sb - 1, 0));
+    for (int j = 1; j < sb; ++j)
+      cheb_product(w.baby + nn, w.baby + (long long)j * nn, w.baby + (long long)(j - 1) * nn,
+                   w.baby + (long long)(j + 1) * nn, Ns, mom + j + 1, st);
+  }
+  if (Q < 1) return cuda_err(cudaGetLastError());
+  // giant steps G_q = T_{qs}: G_{q+1} = 2 Y G_q - G_{q-1}, Y = T_s
+  const double* Y = w.baby + (long long)s * nn;
+  std::vector<double*> g(Q + 1);
+  g[0] = w.baby;
+  g[1] = const_cast<double*>(Y);
+  for (int q = 2; q <= Q; ++q) g[q] = w.giant + (long long)(q - 2) * nn;
+  {
+    Prof p(ctx, ST_CHEB_GEMM, std::max(Q - 1, 0));
+    for (int q = 1; q < Q; ++q)
+      cheb_product(Y, g[q], g[q - 1], g[q + 1], Ns, mom + (q + 1) * s, st);
+  }
+  int rc = cuda_err(cudaMemcpyAsync(w.gptr, g.data(), (Q + 1) * sizeof(double*),
+                                    cudaMemcpyHostToDevice, st));
+  if (rc) return rc;
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    ps_frob_kernel<<<Q * (s - 1) * PS_FROB_BLOCKS, 256, 0, st>>>(
+        const_cast<const double* const*>(w.gptr), w.baby, nn, s, w.part);
+    ps_moments_kernel<<<1, 32, 0, st>>>(w.part, s, Q, npl, mom);
+  }
+  // the host vector g is only read by the copy above, which the stream
+  // orders before any later use; wait for it before g goes out of scope
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+// Ds = sum'_j c_j T_j by the Clenshaw recurrence in Y = T_s.
+int ps_kernel_f64(sq3_ctx* ctx, int Ns, int npl, int s, int Q, const double* coef, double* T,
+                  double* D) {
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)Ns * Ns;
+  const PsWs w = ps_ws(T, nn, s, Q);
+  const int sb = std::min(s, npl + 1);       // baby steps T_0 .. T_{sb-1} hold A_q
+  const unsigned blocks = (unsigned)std::min<long long>((nn + 255) / 256, 152LL * 8);
+  Prof pd(ctx, ST_D_ACCUM, 2 + 2 * Q);
+  ps_alpha_kernel<<<1, 32, 0, st>>>(coef, npl, s, Q, w.work, w.alpha);
+  if (Q == 0) {
+    ps_combine_kernel<<<blocks, 256, 0, st>>>(D, nullptr, 0.0, nullptr, 0.0, w.baby, nn, sb,
+                                              w.alpha);
+    return cuda_err(cudaGetLastError());
+  }
+  const double* Y = w.baby + (long long)s * nn;
+  double* bq1 = w.b[0];     // b_{q+1}
+  double* bq2 = w.b[1];     // b_{q+2}
+  double* bq = w.b[2];
+  cudaMemsetAsync(bq2, 0, nn * sizeof(double), st);
+  // b_Q = A_Q
+  ps_combine_kernel<<<blocks, 256, 0, st>>>(bq1, nullptr, 0.0, nullptr, 0.0, w.baby, nn, s,
+                                            w.alpha + (size_t)Q * s);
+  for (int q = Q - 1; q >= 1; --q) {
+    // b_q = A_q + 2 Y b_{q+1} - b_{q+2}
+    cheb_product(Y, bq1, bq2, bq, Ns, nullptr, st);
+    ps_combine_kernel<<<blocks, 256, 0, st>>>(bq, bq, 1.0, nullptr, 0.0, w.baby, nn, s,
+                                              w.alpha + (size_t)q * s);
+    double* t = bq2;
+    bq2 = bq1;
+    bq1 = bq;
+    bq = t;
+  }
+  // Ds = A_0 + Y b_1 - b_2 = (2 Y b_1 - b_2) / 2 - b_2 / 2 + A_0
+  cheb_product(Y, bq1, bq2, bq, Ns, nullptr, st);
+  ps_combine_kernel<<<blocks, 256, 0, st>>>(D, bq, 0.5, bq2, -0.5, w.baby, nn, s, w.alpha);
+  return cuda_err(cudaGetLastError());
+}
+
+int ps_layout(int npl, int* s_out, int* Q_out) {
+  int s = (int)ceil(sqrt(2.0 * npl));
+  if (s < 2) s = 2;
+  *s_out = s;
+  *Q_out = npl / s;
+  return 0;
+}
+
 int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                            double sigma, double Ne, const double* bounds_in,
-                           double* D, double* out_host, bool mixed) {
+                           double* D, double* out_host, bool mixed, double fermi_tol,
+                           int eval_mode, int* npl_used) {
   cudaStream_t st = ctx->stream;
   const long long nn = (long long)Ns * Ns;
   // workspace: T_0..T_npl (FP64), or in the mixed path T_0..T_h (FP32) and
@@ -258,25 +480,14 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   // The mixed path runs the recurrence to h = ceil(npl / 2) only: the
   // moments and the terms of Ds above h follow from the product identity
   // T_h T_k = (T_{h+k} + T_{h-k}) / 2 (one more tensor-core product).
-  const int h = mixed ? (npl + 1) / 2 : npl;
-  // (mixed: then the block sums of the moment tail, 8-byte aligned)
-  const size_t tail_off = (((size_t)(h + 2) * nn * sizeof(float) + 7) / 8) * 8;
-  size_t need_T = mixed ? tail_off + moments_tail_part_words(npl, h) * sizeof(double)
-                        : (size_t)(npl + 1) * nn * sizeof(double);
-  int rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
-  if (rc) return rc;
   const int lsteps = Ns < 40 ? Ns : 40;
   size_t need_m = lanczos_work_words((size_t)Ns, (size_t)lsteps) * sizeof(double);
-  rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes, need_m);
+  int rc = ensure((void**)&ctx->wsMat, &ctx->wsMat_bytes, need_m);
   if (rc) return rc;
-  if (npl > SQ3_MAX_NPL) return SQ3_EINVAL;
   double* bounds = ctx->dev_scal;                  // chi, xi
   double* outd = ctx->dev_scal + 8;                // 6 outputs
   double* mom = ctx->dev_scal + 64;                // moments m_0..m_npl
   double* coef = ctx->dev_scal + 64 + SQ3_MAX_NPL + 1;  // c_0..c_npl
-  rc = cuda_err(cudaMemsetAsync(mom, 0, (size_t)(npl + 1) * sizeof(double), st));
-  if (rc) return rc;
-
   if (bounds_in) {
     rc = cuda_err(cudaMemcpyAsync(bounds, bounds_in, 2 * sizeof(double),
                                   cudaMemcpyHostToDevice, st));
@@ -285,6 +496,43 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
     Prof p(ctx, ST_LANCZOS, 5 * lsteps + 2);
     lanczos_bounds_f64(ctx, Hs, Ns, lsteps, bounds, ctx->wsMat, st);
   }
+  if (npl < 1) {
+    // degree from the tolerance and the spectral half-width (the Bernstein
+    // ellipse rule of sq3_fermi_degree)
+    double xi = 0.0;
+    if (bounds_in) {
+      xi = bounds_in[1];
+    } else {
+      rc = cuda_err(cudaMemcpyAsync(ctx->host_scal + 40, bounds + 1, sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+      if (rc == SQ3_OK) rc = cuda_err(cudaStreamSynchronize(st));
+      if (rc) return rc;
+      xi = ctx->host_scal[40];
+    }
+    if (!(xi > 0) || !isfinite(xi)) return SQ3_ENONFINITE;
+    npl = sq3_fermi_degree(sigma, xi, fermi_tol);
+    if (npl < 1) return SQ3_EINVAL;
+    if (npl > SQ3_MAX_NPL) npl = SQ3_MAX_NPL;
+  }
+  if (npl > SQ3_MAX_NPL) return SQ3_EINVAL;
+  if (npl_used) *npl_used = npl;
+  const bool ps = eval_mode == 1 && !mixed;
+  int ps_s = 0, ps_Q = 0;
+  ps_layout(npl, &ps_s, &ps_Q);
+  const int h = mixed ? (npl + 1) / 2 : npl;
+  // (mixed: then the block sums of the moment tail, 8-byte aligned)
+  const size_t tail_off = (((size_t)(h + 2) * nn * sizeof(float) + 7) / 8) * 8;
+  // Paterson-Stockmeyer: T_0..T_s, G_2..G_Q, three Clenshaw buffers, the
+  // Frobenius partials, alpha and its work, and the giant-step pointers
+  const size_t ps_mats = (size_t)(ps_s + 1) + (size_t)std::max(ps_Q - 1, 0) + 3;
+  const size_t ps_words = ps_mats * nn + (size_t)ps_Q * ps_s * PS_FROB_BLOCKS +
+                          2 * (size_t)(ps_Q + 1) * ps_s + (size_t)(ps_Q + 2);
+  size_t need_T = mixed ? tail_off + moments_tail_part_words(npl, h) * sizeof(double)
+                        : (ps ? ps_words : (size_t)(npl + 1) * nn) * sizeof(double);
+  rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
+  if (rc) return rc;
+  rc = cuda_err(cudaMemsetAsync(mom, 0, (size_t)(npl + 1) * sizeof(double), st));
+  if (rc) return rc;
   double* T = ctx->wsT;
   if (mixed) {
     rc = cheb_recurrence_mixed(ctx, Hs, Ns, h, bounds, mom, (float*)ctx->wsT);
@@ -294,6 +542,9 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
       rc = moments_tail_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, mom,
                               (double*)((char*)ctx->wsT + tail_off));
     }
+    if (rc) return rc;
+  } else if (ps) {
+    rc = ps_moments_f64(ctx, Hs, Ns, npl, ps_s, ps_Q, bounds, mom, T);
     if (rc) return rc;
   } else {
   {
@@ -341,6 +592,9 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   if (D != nullptr && mixed) {
     rc = accumulate_d_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, coef, D,
                             (float*)ctx->wsT + (size_t)(h + 1) * nn);
+    if (rc) return rc;
+  } else if (D != nullptr && ps) {
+    rc = ps_kernel_f64(ctx, Ns, npl, ps_s, ps_Q, coef, T, D);
     if (rc) return rc;
   } else if (D != nullptr) {
     Prof pd(ctx, ST_D_ACCUM);

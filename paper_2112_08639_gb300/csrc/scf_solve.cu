@@ -109,7 +109,9 @@ int sq3_scf_solve(sq3_ctx* c, const sq3_scf_params* p, const double* b, double* 
   if (Ns <= 0 || Ns > 65535 || p->degree < 1 || p->max_iter < 1 || p->first_passes < 1 ||
       p->passes < 1 || !(p->kT > 0) || !(p->Ne > 0) || !(p->Ne < 2.0 * Ns) || !(p->tol > 0) ||
       p->npl > SQ3_MAX_NPL || (p->npl < 1 && !(p->fermi_tol > 0 && p->fermi_tol < 1)) ||
-      !isfinite(p->e_self) || !isfinite(p->cut_shift) || p->cut_shift < 0)
+      !isfinite(p->e_self) || !isfinite(p->cut_shift) || p->cut_shift < 0 ||
+      (p->kernel_eval != SQ3_EVAL_RECURRENCE && p->kernel_eval != SQ3_EVAL_PATERSON_STOCKMEYER) ||
+      (p->kernel_eval == SQ3_EVAL_PATERSON_STOCKMEYER && prec != SQ3_FP64))
     return SQ3_EINVAL;
   cudaSetDevice(c->device);
   *res = sq3_scf_result{};
@@ -189,12 +191,8 @@ int sq3_scf_solve(sq3_ctx* c, const sq3_scf_params* p, const double* b, double* 
     if (rc) return rc;
     const double bnd[2] = {c->host_scal[56], c->host_scal[57]};
     if (!isfinite(bnd[0]) || !(bnd[1] > 0)) return SQ3_ENONFINITE;
-    if (p->npl < 1) {
-      npl_it = sq3_fermi_degree(p->kT, bnd[1], p->fermi_tol);
-      if (npl_it < 1) return SQ3_EINVAL;
-      if (npl_it > SQ3_MAX_NPL) npl_it = SQ3_MAX_NPL;
-    }
-    rc = sq3_kernel_from_hs(c, Hs, Ns, npl_it, p->kT, p->Ne, prec, bnd, D, out);
+    rc = sq3_kernel_from_hs_ex(c, Hs, Ns, p->npl, p->fermi_tol, p->kernel_eval, p->kT, p->Ne,
+                               prec, bnd, D, out, &npl_it);
     if (rc) return rc;
     rc = sq3_density(c, X, D, Ns, prec, rho_out);
     if (rc) return rc;

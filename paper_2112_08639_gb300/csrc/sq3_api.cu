@@ -163,7 +163,8 @@ void minmax(const double* a, long long n, double* part, double* out, int* status
 static void free_projectors(Projectors& P) {
   void* ptrs[] = {P.gamma,       P.nb_ball_ptr, P.nb_slot_pid, P.nb_pt_ptr, P.nb_pt_lb,
                   P.nb_pt_val,   P.nb_pt_valf, P.nb_bl_ptr,  P.nb_bl_pt,
-                  P.nb_bl_val,   P.nb_bl_valf};
+                  P.nb_bl_val,   P.nb_bl_valf, P.fq_ptr,     P.fq_idx,
+                  P.fq_val,      P.fq_valf};
   for (void* p : ptrs) if (p) cudaFree(p);
   P = Projectors{};
 }
@@ -708,7 +709,14 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
     rc = rc ? rc : upload(&P.nb_bl_val, zval.data(), zval.size());
     rc = rc ? rc : upload(&P.nb_bl_valf, zvalf.data(), zvalf.size());
   }
-  c->proj = P;
+  P.h_bptr = std::move(bptr);
+  P.h_bidx = std::move(bidx);
+  P.h_bp0 = std::move(bp0);
+  P.h_bnp = std::move(bnp);
+  P.h_boff = std::move(boff);
+  P.h_bval = std::move(bval);
+  P.h_gamma.assign(gamma, gamma + n_proj);
+  c->proj = std::move(P);
   if (rc) { free_projectors(c->proj); return rc; }
   return SQ3_OK;
 }
@@ -844,15 +852,29 @@ int sq3_project(sq3_ctx* c, const void* X, int Ns, sq3_prec prec, double* Hs) {
 int sq3_kernel_from_hs(sq3_ctx* c, const double* Hs, int Ns, int npl,
                        double kT, double Ne, sq3_prec prec,
                        const double* bounds_in, double* D, double* out) {
+  if (npl < 1) return SQ3_EINVAL;
+  return sq3_kernel_from_hs_ex(c, Hs, Ns, npl, 0.0, SQ3_EVAL_RECURRENCE, kT, Ne, prec,
+                               bounds_in, D, out, nullptr);
+}
+
+int sq3_kernel_from_hs_ex(sq3_ctx* c, const double* Hs, int Ns, int npl, double fermi_tol,
+                          int eval_mode, double kT, double Ne, sq3_prec prec,
+                          const double* bounds_in, double* D, double* out, int* npl_used) {
   if (!c) return SQ3_EINVAL;
-  if (!Hs || !out || Ns <= 0 || npl < 1 || npl > SQ3_MAX_NPL || !(kT > 0) ||
+  if (!Hs || !out || Ns <= 0 || npl > SQ3_MAX_NPL || !(kT > 0) ||
       !(Ne > 0) || !(Ne < 2.0 * Ns))
     return SQ3_EINVAL;
+  if (npl < 1 && !(fermi_tol > 0 && fermi_tol < 1)) return SQ3_EINVAL;
+  if (eval_mode != SQ3_EVAL_RECURRENCE && eval_mode != SQ3_EVAL_PATERSON_STOCKMEYER)
+    return SQ3_EINVAL;
+  if (eval_mode == SQ3_EVAL_PATERSON_STOCKMEYER && prec != SQ3_FP64) return SQ3_EINVAL;
   if (bounds_in && !(bounds_in[1] > 0)) return SQ3_EINVAL;
   if (prec != SQ3_FP64 && prec != SQ3_MIXED) return SQ3_EINVAL;
   cudaSetDevice(c->device);
+  int used = 0;
   int rc = density_kernel_from_hs(c, Hs, Ns, npl, kT, Ne, bounds_in, D, out,
-                                  prec == SQ3_MIXED);
+                                  prec == SQ3_MIXED, fermi_tol, eval_mode, &used);
+  if (npl_used) *npl_used = used;
   return finish(c, rc);
 }
 

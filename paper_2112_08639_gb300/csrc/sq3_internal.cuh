@@ -79,6 +79,21 @@ struct Projectors {
   // Gershgorin bounds on the spectrum of V_nl = sum_p gamma_p c_p c_p^T
   // (from the projectors' overlap matrix): vnl_lo <= lambda <= vnl_hi
   double vnl_lo = 0.0, vnl_hi = 0.0;
+  // host copy of the balls (for the force tables): ball B covers grid
+  // indices h_bidx[h_bptr[B] .. h_bptr[B+1]-1]; its h_bnp[B] projectors are
+  // h_bp0[B] + q with values h_bval[h_boff[B] + q * len + e] (c = chi sqrt(dV))
+  std::vector<int> h_bptr, h_bidx, h_bp0, h_bnp, h_boff;
+  std::vector<double> h_bval;
+  std::vector<double> h_gamma;
+  // force tables (forces.cu), built on the first force call: per ball the
+  // rows fq_ptr[B] .. fq_ptr[B+1]-1, each a grid index fq_idx and 16 values
+  // (4 projectors x {c, d/dx c, d/dy c, d/dz c}, FD first derivative)
+  bool fq_ok = false;
+  int* fq_ptr = nullptr;
+  int* fq_idx = nullptr;
+  double* fq_val = nullptr;
+  float* fq_valf = nullptr;
+  int fq_max_rows = 0;
 };
 
 }  // namespace sq3
@@ -193,6 +208,12 @@ template <typename T>
 int launch_nl_pass(const sq3_ctx* ctx, T* out, const T* gC, T* gC_next, int Ns,
                    double s1, cudaStream_t st);
 
+// ---- atom-centred Gaussians (atoms.cu) ----
+// Host tables of the 1-D periodic image sums of exp(-(x - R)^2 / w^2) (or
+// their x-derivatives) for every atom: gx | gy | gz, natoms x n each.
+void atom_tables(const sq3_ctx* c, int natoms, const double* pos, double w, bool deriv,
+                 std::vector<double>& tab);
+
 // ---- FP64 GEMM (gemm_f64.cu) ----
 enum Epi { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_CHEB = 2, EPI_RHO = 3 };
 struct GemmArgs {
@@ -254,9 +275,12 @@ void lanczos_bounds_f64(sq3_ctx* ctx, const double* Hs, int n, int steps,
                         double* d_bounds, double* work, cudaStream_t st);
 
 // ---- Chebyshev Fermi-operator expansion (foe.cu) ----
+// npl < 1: degree from sq3_fermi_degree(sigma, xi, fermi_tol); eval_mode 1:
+// Paterson-Stockmeyer (FP64 path); *npl_used (may be null) = the degree.
 int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                            double sigma, double Ne, const double* bounds_in,
-                           double* D, double* out_host, bool mixed);
+                           double* D, double* out_host, bool mixed, double fermi_tol = 0.0,
+                           int eval_mode = 0, int* npl_used = nullptr);
 
 // ---- mixed-precision path (mixed.cu) ----
 int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns);

@@ -598,6 +598,8 @@ static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& 
 template <int EPI>
 static int launch_e(int PA, int PB, const CUtensorMap& a, const CUtensorMap& b,
                     const TcParams& p, dim3 grid, cudaStream_t st) {
+  if constexpr (EPI == EPI_TC_STORE || EPI == EPI_TC_ATOMIC)
+    if (PA == 1 && PB == 1) return launch_t<1, 1, EPI>(a, b, p, grid, st);
   if (PA == 2 && PB == 2) return launch_t<2, 2, EPI>(a, b, p, grid, st);
   if (PA == 3 && PB == 3) return launch_t<3, 3, EPI>(a, b, p, grid, st);
   return SQ3_EINVAL;

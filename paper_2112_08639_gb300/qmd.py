@@ -1,0 +1,131 @@
+"""Quantum molecular dynamics of the nuclei on the library's forces (the QMD
+of Sec. 5: velocity Verlet, isokinetic ensemble), one converged SCF solve
+per step through the SCF driver, with a choice of starting density per
+step: the atomic superposition, the previous step's density, or the
+learned model (``learned.LearnedStart``).
+
+This module orders library calls: the projector table of each step comes
+from the inputs module (the synthetic pseudopotential's projectors at the
+new positions), and the pseudocharges, the SCF solve, the forces and the
+Verlet halves run in the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import inputs, sq3
+
+AMU_IN_ME = 1822.888486209             # atomic mass unit / electron mass
+FS_IN_AU = 1.0 / 0.02418884326585747    # femtoseconds in hbar / Ha
+MASS_AL = 26.9815385 * AMU_IN_ME
+SUPERPOSITION_WIDTH = 1.9
+
+
+def maxwell_boltzmann(natoms: int, kT: float, seed: int = 0, mass: float = MASS_AL) -> np.ndarray:
+    """Seeded velocities with zero total momentum and kinetic energy
+    (3 natoms - 3) kT / 2 (the equipartition value of the free degrees)."""
+    rng = np.random.default_rng(seed + 15485863)
+    V = rng.normal(size=(natoms, 3)) * np.sqrt(kT / mass)
+    V -= V.mean(axis=0)
+    ke = 0.5 * mass * float(np.sum(V * V))
+    return np.ascontiguousarray(V * np.sqrt(0.5 * (3 * natoms - 3) * kT / ke))
+
+
+class Cell:
+    """One periodic cell on a context: grid, pseudopotential parameters and
+    the per-step state (block X, density, last spectral bounds)."""
+
+    def __init__(self, cfg: inputs.CellConfig, device: int = 0, prec=sq3.MIXED,
+                 proj_seed: int | None = None):
+        self.cfg = cfg
+        self.prec = prec
+        self.ctx = sq3.Context(device)
+        self.ctx.setup_grid(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L, 12)
+        self.proj_seed = cfg.seed if proj_seed is None else proj_seed
+        dtype = torch.float64 if prec == sq3.FP64 else torch.float32
+        self.X = inputs.random_block_device(cfg.N, cfg.Ns, seed=cfg.seed, dtype=dtype)
+        self.rho = torch.empty(cfg.N, dtype=torch.float64, device=self.ctx.device)
+        self.b = torch.empty_like(self.rho)
+        self.phi = torch.empty_like(self.rho)
+        self.D = torch.empty((cfg.Ns, cfg.Ns), dtype=torch.float64, device=self.ctx.device)
+        self.bounds = None
+        self.rho_prev = None
+        self.e_self = cfg.natoms * inputs.Z_VALENCE ** 2 / np.sqrt(2 * np.pi) / inputs.RC_LOCAL
+
+    def set_positions(self, pos):
+        cfg = self.cfg
+        self.pos = np.ascontiguousarray(pos, dtype=np.float64)
+        self.proj = None
+        self.atom_of = None
+        if cfg.projectors:
+            pr = inputs.projectors(cfg.n, cfg.L, self.pos, seed=self.proj_seed)
+            self.ctx.set_projectors(pr.ptr, pr.idx, pr.val, pr.gamma)
+            self.proj = pr
+            self.atom_of = np.arange(pr.n_proj) // 4
+        self.ctx.pseudocharge(self.pos, inputs.Z_VALENCE, inputs.RC_LOCAL, out=self.b)
+
+    def start_density(self, start: str, learned=None):
+        cfg = self.cfg
+        if start == "previous" and self.rho_prev is not None:
+            self.rho.copy_(self.rho_prev)
+        elif start == "learned":
+            learned.predict(self.ctx, self.pos, cfg.Ne, out=self.rho)
+        else:
+            self.ctx.atom_gaussians(self.pos, SUPERPOSITION_WIDTH, total=cfg.Ne, out=self.rho)
+
+    def solve(self, tol: float = 1e-6, **kw):
+        cfg = self.cfg
+        first = self.bounds is None
+        args = dict(degree=cfg.m, npl=cfg.npl, kT=cfg.sigma, Ne=cfg.Ne, e_self=self.e_self,
+                    tol=tol, prec=self.prec, first_passes=4 if first else 1, passes=1,
+                    max_iter=100, bounds0=self.bounds, D=self.D)
+        args.update(kw)
+        res, hist = self.ctx.scf_solve(self.b, self.rho, self.X, **args)
+        self.bounds = (res["chi"], res["xi"])
+        self.rho_prev = self.rho.clone()
+        return res, hist
+
+    def forces(self):
+        cfg = self.cfg
+        self.ctx.effective_potential(self.rho, self.b, phi=self.phi)
+        f, _, _ = self.ctx.forces(self.pos, inputs.Z_VALENCE, inputs.RC_LOCAL, cfg.Ne, self.phi,
+                                  self.X if cfg.projectors else None,
+                                  self.D if cfg.projectors else None, self.prec, self.atom_of)
+        return np.ascontiguousarray(f)
+
+
+def run(cell: Cell, R0, V0, dt_fs: float, nsteps: int, start: str = "previous",
+        learned=None, isokinetic: bool = True, tol: float = 1e-6, on_step=None) -> dict:
+    """nsteps of velocity Verlet from (R0, V0) with dt_fs femtoseconds per
+    step; returns per-step positions, SCF iterations, F and kinetic energy.
+    on_step(step, cell, result) is called after each converged solve (for
+    example to collect training densities)."""
+    masses = np.full(len(R0), MASS_AL)
+    dt = dt_fs * FS_IN_AU
+    R = np.array(R0, dtype=np.float64)
+    V = np.array(V0, dtype=np.float64)
+    ke0 = 0.5 * float(np.sum(masses[:, None] * V * V))
+    cell.set_positions(R)
+    cell.start_density(start, learned)
+    res, _ = cell.solve(tol)
+    if on_step:
+        on_step(0, cell, res)
+    F = cell.forces()
+    traj = {"R": [R.copy()], "iterations": [res["iterations"]], "F": [res["F"]],
+            "E_kin": [ke0], "converged": [res["converged"]]}
+    for step in range(1, nsteps + 1):
+        sq3.verlet(masses, dt, R, V, F, 0)
+        cell.set_positions(R)
+        cell.start_density(start, learned)
+        res, _ = cell.solve(tol)
+        if on_step:
+            on_step(step, cell, res)
+        F = cell.forces()
+        sq3.verlet(masses, dt, R, V, F, 1, ke0 if isokinetic else 0.0)
+        traj["R"].append(R.copy())
+        traj["iterations"].append(res["iterations"])
+        traj["F"].append(res["F"])
+        traj["E_kin"].append(0.5 * float(np.sum(masses[:, None] * V * V)))
+        traj["converged"].append(res["converged"])
+    return {k: np.asarray(v) for k, v in traj.items()}

@@ -19,6 +19,8 @@ from . import build as _build
 
 FP64 = 0
 MIXED = 1
+EVAL_RECURRENCE = 0
+EVAL_PATERSON_STOCKMEYER = 1
 
 OK, EINVAL, ENOTSETUP, ECUDA, ENOTPD, ENOCONV, ETIMEOUT, ENONFINITE, ENOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
@@ -43,6 +45,7 @@ _sigs = {
     "sq3_orthonormalise": (_i, [_p, _p, _i, _i]),
     "sq3_project": (_i, [_p, _p, _i, _i, _p]),
     "sq3_kernel_from_hs": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p]),
+    "sq3_kernel_from_hs_ex": (_i, [_p, _p, _i, _i, _d, _i, _d, _d, _i, _p, _p, _p, _p]),
     "sq3_density_kernel": (_i, [_p, _p, _i, _i, _d, _d, _i, _p, _p, _p, _p]),
     "sq3_density": (_i, [_p, _p, _p, _i, _i, _p]),
     "sq3_status_string": (ctypes.c_char_p, [_i]),
@@ -62,6 +65,17 @@ _sigs = {
     "sq3_hamiltonian_bounds": (_i, [_p, _p]),
     "sq3_scf_solve": (_i, [_p, _p, _p, _p, _p, _i, _p, _p, _p]),
     "sq3_atom_gaussians": (_i, [_p, _i, _p, _p, _d, _i, _d, _p, _p]),
+    "sq3_verlet": (_i, [_i, _p, _d, _p, _p, _p, _i, _d]),
+    "sq3_forces": (_i, [_p, _i, _p, _d, _d, _d, _p, _p, _p, _i, _i, _p, _p, _p]),
+    "sq3_mlp_create": (_i, [_p, _i, _p, _i, ctypes.POINTER(_p)]),
+    "sq3_mlp_destroy": (None, [_p]),
+    "sq3_mlp_num_params": (_i, [_p]),
+    "sq3_mlp_set_params": (_i, [_p, _p]),
+    "sq3_mlp_get_params": (_i, [_p, _p]),
+    "sq3_mlp_features": (_i, [_p, _i, _p]),
+    "sq3_mlp_predict": (_i, [_p, _d, _p]),
+    "sq3_mlp_gradient": (_i, [_p, _p, _d, _p, _p, _p]),
+    "sq3_mlp_train_step": (_i, [_p, _p, _d, _d, _p, _p]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -75,7 +89,7 @@ class ScfParams(ctypes.Structure):
                 ("max_iter", _i), ("mix_history", _i), ("mix_period", _i), ("kT", _d), ("Ne", _d),
                 ("tol", _d), ("e_self", _d), ("mix_beta", _d), ("kerker_k0", _d),
                 ("fermi_tol", _d), ("filter_cut", _d), ("chi0", _d), ("xi0", _d),
-                ("cut_shift", _d)]
+                ("cut_shift", _d), ("kernel_eval", _i), ("reserved", _i)]
 
 
 class ScfResult(ctypes.Structure):
@@ -130,6 +144,18 @@ def fermi_degree(sigma: float, xi: float, tol: float) -> int:
     if n < 0:
         raise SQ3Error(n, "sq3_fermi_degree")
     return n
+
+
+def verlet(masses, dt: float, R: np.ndarray, V: np.ndarray, F: np.ndarray, phase: int,
+           ke_target: float = 0.0):
+    """One velocity-Verlet half step in place on float64 (natoms, 3) arrays
+    (sq3_verlet): phase 0 kicks V by F/2 and drifts R, phase 1 kicks V."""
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    for a in (R, V, F):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("float64 C-contiguous arrays expected")
+    _check(lib.sq3_verlet(len(m), m.ctypes.data, dt, R.ctypes.data, V.ctypes.data,
+                          F.ctypes.data, phase, ke_target), "sq3_verlet")
 
 
 NOALLOC_MAX_NS = 8192
@@ -244,6 +270,22 @@ class Context:
                "sq3_kernel_from_hs")
         return D, self._unpack(out)
 
+    def kernel_from_hs_ex(self, Hs: torch.Tensor, npl: int, kT: float, Ne: float, prec=FP64,
+                          fermi_tol: float = 0.0, eval_mode: int = EVAL_RECURRENCE, bounds=None,
+                          D: torch.Tensor | None = None):
+        """(D, outputs, degree used): the density kernel with the adaptive
+        degree (npl < 1) and/or the Paterson-Stockmeyer evaluation."""
+        Ns = Hs.shape[0]
+        if D is None:
+            D = torch.empty((Ns, Ns), dtype=torch.float64, device=self.device)
+        out = (ctypes.c_double * 6)()
+        used = ctypes.c_int()
+        b = (ctypes.c_double * 2)(*bounds) if bounds is not None else None
+        _check(lib.sq3_kernel_from_hs_ex(self._h, _ptr(Hs), Ns, npl, fermi_tol, eval_mode, kT, Ne,
+                                         prec, b, _ptr(D), out, ctypes.byref(used)),
+               "sq3_kernel_from_hs_ex")
+        return D, self._unpack(out), used.value
+
     def density_kernel(self, X: torch.Tensor, npl: int, kT: float, Ne: float, prec=FP64,
                        bounds=None, Hs: torch.Tensor | None = None,
                        D: torch.Tensor | None = None):
@@ -337,6 +379,21 @@ class Context:
         return self.atom_gaussians(positions, rc, q=np.full(n, -Z), normalised=True,
                                    total=-Z * n, out=out)
 
+    def forces(self, positions, Z: float, rc: float, Ne: float, phi: torch.Tensor,
+               X: torch.Tensor | None = None, D: torch.Tensor | None = None, prec=FP64,
+               atom_of=None):
+        """(forces (natoms, 3), local part, nonlocal part) in Ha/bohr."""
+        pos = np.ascontiguousarray(positions, dtype=np.float64)
+        n = pos.shape[0]
+        f = np.empty((n, 3))
+        parts = np.empty((n, 3, 2))
+        ao = None if atom_of is None else np.ascontiguousarray(atom_of, dtype=np.int32)
+        Ns = 0 if X is None else X.shape[0]
+        _check(lib.sq3_forces(self._h, n, pos.ctypes.data, Z, rc, Ne, self._grid_vec(phi),
+                              _ptr(X), _ptr(D), Ns, prec, None if ao is None else ao.ctypes.data,
+                              f.ctypes.data, parts.ctypes.data), "sq3_forces")
+        return f, parts[..., 0], parts[..., 1]
+
     def hamiltonian_bounds(self) -> tuple[float, float]:
         """Rigorous (lower, upper) bounds of the spectrum of H."""
         out = (ctypes.c_double * 2)()
@@ -348,7 +405,7 @@ class Context:
                   prec=FP64, first_passes: int = 4, passes: int = 1, max_iter: int = 100,
                   mix_history: int = 7, mix_period: int = 2, mix_beta: float = 0.3,
                   kerker_k0: float = 0.8, fermi_tol: float = 0.0, filter_cut: float = 0.0,
-                  cut_shift: float = 0.0, bounds0=None, D: torch.Tensor | None = None, raise_on_noconv: bool = True):
+                  cut_shift: float = 0.0, kernel_eval: int = 0, bounds0=None, D: torch.Tensor | None = None, raise_on_noconv: bool = True):
         """Converged SCF solve (sq3_scf_solve).  rho (in: start, out: the
         converged density) and X (in: starting block, out: last block) are
         updated in place.  Returns (result dict, list of per-iteration dicts)."""
@@ -360,7 +417,8 @@ class Context:
                       mix_beta=mix_beta, kerker_k0=kerker_k0, fermi_tol=fermi_tol,
                       filter_cut=filter_cut,
                       chi0=bounds0[0] if bounds0 is not None else 0.0,
-                      xi0=bounds0[1] if bounds0 is not None else 0.0, cut_shift=cut_shift)
+                      xi0=bounds0[1] if bounds0 is not None else 0.0, cut_shift=cut_shift,
+                      kernel_eval=kernel_eval)
         r = ScfResult()
         hist = (ctypes.c_double * (max_iter * SCF_HIST))()
         code = lib.sq3_scf_solve(self._h, ctypes.byref(p), self._grid_vec(b), self._grid_vec(rho),
@@ -390,3 +448,73 @@ class Context:
         if r < 0:
             raise SQ3Error(r, "sq3_profile_read")
         return {s: (ms[i], la[i]) for i, s in enumerate(self.STAGES)}
+
+
+class MLP:
+    """Learned starting density (sq3_mlp_*): a 3 x 128 tanh perceptron over
+    atom-centred Gaussian descriptors of the given widths, bound to a
+    context's grid.  Parameters are one float32 array (W1 [128][F], b1, W2,
+    b2, W3, b3, w4, b4)."""
+
+    def __init__(self, ctx: Context, widths, seed: int = 0):
+        self.ctx = ctx
+        self.widths = np.ascontiguousarray(widths, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.sq3_mlp_create(ctx._h, len(self.widths), self.widths.ctypes.data, seed,
+                                  ctypes.byref(h)), "sq3_mlp_create")
+        self._h = h
+        self.n_params = lib.sq3_mlp_num_params(h)
+        self._scratch = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sq3_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(lib.sq3_mlp_set_params(self._h, a.ctypes.data), "sq3_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(lib.sq3_mlp_get_params(self._h, a.ctypes.data), "sq3_mlp_get_params")
+        return a
+
+    def features(self, positions):
+        pos = np.ascontiguousarray(positions, dtype=np.float64)
+        _check(lib.sq3_mlp_features(self._h, pos.shape[0], pos.ctypes.data), "sq3_mlp_features")
+
+    def predict(self, Ne: float, rho: torch.Tensor | None = None) -> torch.Tensor:
+        if rho is None:
+            rho = torch.empty(self.ctx.N, dtype=torch.float64, device=self.ctx.device)
+        _check(lib.sq3_mlp_predict(self._h, Ne, self.ctx._grid_vec(rho)), "sq3_mlp_predict")
+        return rho
+
+    def _rho_scratch(self):
+        if self._scratch is None or self._scratch.numel() != self.ctx.N:
+            self._scratch = torch.empty(self.ctx.N, dtype=torch.float64, device=self.ctx.device)
+        return self._scratch
+
+    def gradient(self, rho_ref: torch.Tensor, Ne: float):
+        """(loss, gradient as a float64 array) against rho_ref."""
+        g = np.empty(self.n_params, dtype=np.float64)
+        loss = ctypes.c_double()
+        _check(lib.sq3_mlp_gradient(self._h, self.ctx._grid_vec(rho_ref), Ne,
+                                    self.ctx._grid_vec(self._rho_scratch()), ctypes.byref(loss),
+                                    g.ctypes.data), "sq3_mlp_gradient")
+        return loss.value, g
+
+    def train_step(self, rho_ref: torch.Tensor, Ne: float, lr: float) -> float:
+        loss = ctypes.c_double()
+        _check(lib.sq3_mlp_train_step(self._h, self.ctx._grid_vec(rho_ref), Ne, lr,
+                                      self.ctx._grid_vec(self._rho_scratch()),
+                                      ctypes.byref(loss)), "sq3_mlp_train_step")
+        return loss.value

@@ -100,6 +100,21 @@ def test_argument_errors_before_any_device_work(libpath):
         "sq3_hamiltonian_bounds": ([p, p], (None, None), EINVAL),
         "sq3_atom_gaussians": ([p, i, p, p, d, i, d, p, p], (None, 1, None, None, 1.0, 1, 0.0,
                                                             None, None), EINVAL),
+        "sq3_mlp_create": ([p, i, p, i, p], (None, 8, None, 0, None), EINVAL),
+        "sq3_kernel_from_hs_ex": ([p, p, i, i, d, i, d, d, i, p, p, p, p],
+                                  (None, None, 4, 10, 0.0, 0, 0.3, 2.0, 0, None, None, None, None),
+                                  EINVAL),
+        "sq3_verlet": ([i, p, d, p, p, p, i, d], (0, None, 1.0, None, None, None, 0, 0.0), EINVAL),
+        "sq3_forces": ([p, i, p, d, d, d, p, p, p, i, i, p, p, p],
+                       (None, 1, None, 3.0, 1.0, 3.0, None, None, None, 0, 0, None, None, None),
+                       EINVAL),
+        "sq3_mlp_num_params": ([p], (None,), EINVAL),
+        "sq3_mlp_set_params": ([p, p], (None, None), EINVAL),
+        "sq3_mlp_get_params": ([p, p], (None, None), EINVAL),
+        "sq3_mlp_features": ([p, i, p], (None, 1, None), EINVAL),
+        "sq3_mlp_predict": ([p, d, p], (None, 1.0, None), EINVAL),
+        "sq3_mlp_gradient": ([p, p, d, p, p, p], (None, None, 1.0, None, None, None), EINVAL),
+        "sq3_mlp_train_step": ([p, p, d, d, p, p], (None, None, 1.0, 1e-3, None, None), EINVAL),
         "sq3_scf_solve": ([p, p, p, p, p, i, p, p, p], (None,) * 5 + (0, None, None, None),
                           EINVAL),
     }
@@ -110,5 +125,5 @@ def test_argument_errors_before_any_device_work(libpath):
         assert f(*args) == want, name
     missing = set(declared_symbols()) - set(calls) - {
         "sq3_create", "sq3_destroy", "sq3_status_string", "sq3_version", "sq3_last_cuda_error",
-        "sq3_fermi_degree"}
+        "sq3_fermi_degree", "sq3_mlp_destroy"}
     assert not missing, missing
