@@ -338,13 +338,47 @@ int sq3_forces(sq3_ctx* ctx, int natoms, const double* pos, double Z, double rc,
 int sq3_verlet(int natoms, const double* masses, double dt, double* R, double* V,
                const double* F, int phase, double ke_target);
 
+/* ---- Batched filtering of many independent cells (the paper has no
+ * counterpart: throughput for many uneven cells on one GPU).  Each cell has
+ * its own periodic grid (12th-order FD Laplacian), local potential and FP32
+ * block; one Chebyshev filter (as sq3_cheb_filter with SQ3_MIXED and no
+ * projectors) of every cell runs as one persistent launch per filter step
+ * (CTAs claim (cell, vector, row tile) items from a device counter; no
+ * CTA waits on another), the launches captured once into a CUDA graph and
+ * replayed; the tile height and the resident CTAs per SM are chosen by
+ * sq3_batch_autotune. ---- */
+typedef struct sq3_batch sq3_batch;
+int sq3_batch_create(int device, void* cuda_stream, sq3_batch** out);
+/* Releases the batch's work blocks and FP32 potentials (not the cells'
+ * blocks, which stay the caller's). */
+void sq3_batch_destroy(sq3_batch* batch);
+/* Adds a cell: grid nx x ny x nz over Lx x Ly x Lz (nx a multiple of 4,
+ * 16 <= nx <= 512, ny, nz >= 6), V device N doubles (converted to FP32 and
+ * kept), X device N x Ns floats (16-byte aligned; filtered in place by
+ * sq3_batch_filter, stays the caller's), filter degree 1..256.  Returns
+ * the cell's index (>= 0) or SQ3_EINVAL / SQ3_ENOMEM / SQ3_ECUDA. */
+int sq3_batch_add_cell(sq3_batch* batch, int nx, int ny, int nz, double Lx, double Ly,
+                       double Lz, const double* V, float* X, int Ns, int degree);
+/* Filter bounds of a cell (a0 < a < b), as sq3_cheb_filter. */
+int sq3_batch_set_bounds(sq3_batch* batch, int cell, double a, double b, double a0);
+/* X_c <- p_{m_c}(H_c) X_c for every cell; returns after the work is done.
+ * The first call after cells were added captures the graph. */
+int sq3_batch_filter(sq3_batch* batch);
+/* Times each candidate launch shape (1 or 2 CTAs per SM; every cell's
+ * tile height as chosen or halved) with one graph replay each, on copies
+ * of the cells' blocks (which are put back), and keeps the fastest;
+ * *ctas_per_sm and *ty_divisor (HOST, may be NULL) receive the choice. */
+int sq3_batch_autotune(sq3_batch* batch, int* ctas_per_sm, int* ty_divisor);
+
 /* ---- Learned starting density (the paper has no counterpart: it does
  * not say how each SCF starts).  A multilayer perceptron over atom-centred
  * Gaussian descriptors predicts the density of a cell from its atom
  * positions; it is trained on self-consistent densities the method itself
  * produced.  Per grid point x of the context's grid:
- *   d_k(x) = sum_J sum_images exp(-|x - R_J|^2 / w_k^2) / m_k,
- *            m_k = natoms pi^{3/2} w_k^3 / Omega (mean 1 over the cell)
+ *   d_k(x) = log(1 + sum_J sum_images exp(-|x - R_J|^2 / w_k^2) / m_k),
+ *            m_k = natoms pi^{3/2} w_k^3 / Omega (the sum's mean over the
+ *            cell; the logarithm keeps the narrow widths, a hundred times
+ *            their mean near an atom, from saturating the first layer)
  *   h1 = tanh(W1 d + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3)
  *        (128 units each), y = softplus(w4 . h3 + b4),
  *   rho(x) = Ne y(x) / (sum_x y dV);
@@ -385,6 +419,16 @@ int sq3_mlp_gradient(sq3_mlp* mlp, const double* rho_ref, double Ne, double* rho
  * HOST, the loss before the step. */
 int sq3_mlp_train_step(sq3_mlp* mlp, const double* rho_ref, double Ne, double lr,
                        double* rho_scratch, double* loss);
+
+/* Starting density of a QMD step by extrapolation (the paper leaves the
+ * SCF's start open): out = max(prev + a - b, 0) rescaled to Ne electrons,
+ * with prev the previous step's converged density and a, b a model density
+ * (the learned one, or the atomic superposition) at the new and the
+ * previous positions, so that the model's systematic error cancels and its
+ * response to the atoms' motion remains.  All device arrays of N doubles;
+ * out may alias prev.  Errors: SQ3_EINVAL, SQ3_ENOTSETUP, SQ3_ENONFINITE. */
+int sq3_extrapolate_density(sq3_ctx* ctx, const double* prev, const double* a,
+                            const double* b, double Ne, double* out);
 
 /* ---- Self-consistent-field driver (Sec. 2: the SCF loop; Sec. 4: the SQ3
  * iteration inside each SCF iteration; Sec. 5: periodic Pulay mixing with a

@@ -10,8 +10,10 @@ perceptron over atom-centred Gaussian descriptors.
 
 * Descriptors at grid point x: d_k(x) = sum_J sum_images
   exp(-|x - R_J|^2 / w_k^2) for the widths w_k of WIDTHS, divided by their
-  mean over the cell, natoms pi^(3/2) w_k^3 / Omega (so each feature has
-  mean 1 and the same scale for any cell of the same atom density).
+  mean over the cell, natoms pi^(3/2) w_k^3 / Omega (the same scale for any
+  cell of the same atom density), and compressed as f_k = log(1 + d_k):
+  near an atom the narrow widths reach a hundred times their mean, which
+  would saturate the first tanh layer.
 * Network: three hidden layers of HIDDEN units with tanh,
   h_1 = tanh(W_1 d + b_1), h_l = tanh(W_l h_{l-1} + b_l) (l = 2, 3), and an
   output y = softplus(w_4 . h_3 + b_4) > 0.
@@ -36,12 +38,12 @@ LAYER_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")
 
 
 def descriptors(n: int, L: float, positions: np.ndarray, widths=WIDTHS) -> np.ndarray:
-    """(N, len(widths)) normalised features (mean 1 over the cell)."""
+    """(N, len(widths)) features log(1 + d_k / mean_k)."""
     natoms = len(positions)
     cols = []
     for w in widths:
         mean = natoms * np.pi ** 1.5 * w ** 3 / L ** 3
-        cols.append(radial_sum(n, L, positions, w) / mean)
+        cols.append(np.log1p(radial_sum(n, L, positions, w) / mean))
     return np.stack(cols, axis=1)
 
 

@@ -192,3 +192,51 @@ extern "C" int sq3_verlet(int natoms, const double* masses, double dt, double* R
   }
   return SQ3_OK;
 }
+
+namespace sq3 {
+namespace {
+// out = max(prev + a - b, 0), per-block sums of out in part
+__global__ void __launch_bounds__(256) extrapolate_kernel(const double* __restrict__ prev,
+                                                         const double* __restrict__ a,
+                                                         const double* __restrict__ b, long long n,
+                                                         double* out, double* part) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = fmax(prev[i] + a[i] - b[i], 0.0);
+    out[i] = v;
+    s += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+}  // namespace
+}  // namespace sq3
+
+extern "C" int sq3_extrapolate_density(sq3_ctx* c, const double* prev, const double* a,
+                                       const double* b, double Ne, double* out) {
+  if (!c) return SQ3_EINVAL;
+  if (!c->grid_ok) return SQ3_ENOTSETUP;
+  if (!prev || !a || !b || !out || !(Ne > 0) || !isfinite(Ne)) return SQ3_EINVAL;
+  cudaSetDevice(c->device);
+  const size_t words = AG_BLOCKS + 2;
+  int rc = ensure((void**)&c->wsAtoms, &c->wsAtoms_bytes, words * sizeof(double));
+  if (rc) return rc;
+  double* part = c->wsAtoms;
+  double* res = part + AG_BLOCKS;
+  const long long N = c->grid.N;
+  const unsigned blocks = (unsigned)std::min<long long>((N + 255) / 256, 152LL * 16);
+  extrapolate_kernel<<<AG_BLOCKS, 256, 0, c->stream>>>(prev, a, b, N, out, part);
+  rescale_kernel<<<blocks, 256, 0, c->stream>>>(out, N, part, AG_BLOCKS, c->dV, Ne, res);
+  rc = cuda_err(cudaGetLastError());
+  if (rc) return rc;
+  check_finite(out, N, c->dev_status, c->stream);
+  return check_device_status(c);
+}

@@ -5,8 +5,8 @@
 // work.
 //
 // Model (per grid point x, P = N points of the context's grid):
-//   d_k(x) = sum_J sum_images exp(-|x - R_J|^2 / w_k^2) / (natoms pi^{3/2}
-//            w_k^3 / Omega)                         (mean 1 over the cell)
+//   d_k(x) = log(1 + sum_J sum_images exp(-|x - R_J|^2 / w_k^2) / m_k),
+//            m_k = natoms pi^{3/2} w_k^3 / Omega   (the sum's cell mean)
 //   h1 = tanh(W1 d + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3)
 //   y = softplus(w4 . h3 + b4),  rho = Ne y / (sum_x y dV)
 // Loss against a self-consistent density rho*: L = sum_x (rho - rho*)^2 dV.
@@ -114,7 +114,8 @@ __global__ void weights_bf16_kernel(const float* __restrict__ prm, int F, __nv_b
   }
 }
 
-// Normalised descriptors -> BF16 features in both layouts (zero beyond F).
+// Compressed descriptors log(1 + d / m) -> BF16 features in both layouts
+// (zero beyond F).
 __global__ void features_kernel(const double* __restrict__ desc, int F, long long P,
                                 long long ldP, const double* __restrict__ scale,
                                 __nv_bfloat16* xp, __nv_bfloat16* xf) {
@@ -123,7 +124,7 @@ __global__ void features_kernel(const double* __restrict__ desc, int F, long lon
     __align__(16) __nv_bfloat16 row[MLP_FP];
 #pragma unroll
     for (int k = 0; k < MLP_FP; ++k) {
-      const float v = (k < F && p < P) ? (float)(desc[(size_t)k * P + p] * scale[k]) : 0.f;
+      const float v = (k < F && p < P) ? (float)log1p(desc[(size_t)k * P + p] * scale[k]) : 0.f;
       row[k] = __float2bfloat16_rn(v);
       xf[(size_t)k * ldP + p] = row[k];
     }

@@ -67,6 +67,13 @@ _sigs = {
     "sq3_atom_gaussians": (_i, [_p, _i, _p, _p, _d, _i, _d, _p, _p]),
     "sq3_verlet": (_i, [_i, _p, _d, _p, _p, _p, _i, _d]),
     "sq3_forces": (_i, [_p, _i, _p, _d, _d, _d, _p, _p, _p, _i, _i, _p, _p, _p]),
+    "sq3_extrapolate_density": (_i, [_p, _p, _p, _p, _d, _p]),
+    "sq3_batch_create": (_i, [_i, _p, ctypes.POINTER(_p)]),
+    "sq3_batch_destroy": (None, [_p]),
+    "sq3_batch_add_cell": (_i, [_p, _i, _i, _i, _d, _d, _d, _p, _p, _i, _i]),
+    "sq3_batch_set_bounds": (_i, [_p, _i, _d, _d, _d]),
+    "sq3_batch_filter": (_i, [_p]),
+    "sq3_batch_autotune": (_i, [_p, _p, _p]),
     "sq3_mlp_create": (_i, [_p, _i, _p, _i, ctypes.POINTER(_p)]),
     "sq3_mlp_destroy": (None, [_p]),
     "sq3_mlp_num_params": (_i, [_p]),
@@ -394,6 +401,16 @@ class Context:
                               f.ctypes.data, parts.ctypes.data), "sq3_forces")
         return f, parts[..., 0], parts[..., 1]
 
+    def extrapolate_density(self, prev: torch.Tensor, a: torch.Tensor, b: torch.Tensor,
+                            Ne: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        """max(prev + a - b, 0) rescaled to Ne electrons."""
+        if out is None:
+            out = torch.empty_like(prev)
+        _check(lib.sq3_extrapolate_density(self._h, self._grid_vec(prev), self._grid_vec(a),
+                                           self._grid_vec(b), Ne, self._grid_vec(out)),
+               "sq3_extrapolate_density")
+        return out
+
     def hamiltonian_bounds(self) -> tuple[float, float]:
         """Rigorous (lower, upper) bounds of the spectrum of H."""
         out = (ctypes.c_double * 2)()
@@ -518,3 +535,53 @@ class MLP:
                                       self.ctx._grid_vec(self._rho_scratch()),
                                       ctypes.byref(loss)), "sq3_mlp_train_step")
         return loss.value
+
+
+class Batch:
+    """Many independent cells filtered together (sq3_batch_*): one persistent
+    launch per filter step for all cells, replayed from a captured CUDA graph."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(lib.sq3_batch_create(device, ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h)), "sq3_batch_create")
+        self._h = h
+        self.blocks = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sq3_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_cell(self, n: tuple, L: tuple, V: torch.Tensor, X: torch.Tensor, degree: int) -> int:
+        """Adds a cell (grid n = (nx, ny, nz), lengths L); X (Ns, N) float32 is
+        filtered in place by filter()."""
+        if X.dtype != torch.float32:
+            raise ValueError("the batched filter takes float32 blocks")
+        V = V.to(device=self.device, dtype=torch.float64).contiguous()
+        idx = lib.sq3_batch_add_cell(self._h, n[0], n[1], n[2], L[0], L[1], L[2], _ptr(V),
+                                     _ptr(X), X.shape[0], degree)
+        if idx < 0:
+            raise SQ3Error(idx, "sq3_batch_add_cell")
+        self.blocks.append(X)
+        return idx
+
+    def set_bounds(self, cell: int, a: float, b: float, a0: float):
+        _check(lib.sq3_batch_set_bounds(self._h, cell, a, b, a0), "sq3_batch_set_bounds")
+
+    def filter(self):
+        _check(lib.sq3_batch_filter(self._h), "sq3_batch_filter")
+
+    def autotune(self) -> tuple[int, int]:
+        c, t = ctypes.c_int(), ctypes.c_int()
+        _check(lib.sq3_batch_autotune(self._h, ctypes.byref(c), ctypes.byref(t)),
+               "sq3_batch_autotune")
+        return c.value, t.value

@@ -101,6 +101,13 @@ def test_argument_errors_before_any_device_work(libpath):
         "sq3_atom_gaussians": ([p, i, p, p, d, i, d, p, p], (None, 1, None, None, 1.0, 1, 0.0,
                                                             None, None), EINVAL),
         "sq3_mlp_create": ([p, i, p, i, p], (None, 8, None, 0, None), EINVAL),
+        "sq3_batch_create": ([i, p, p], (-1, None, None), EINVAL),
+        "sq3_extrapolate_density": ([p, p, p, p, d, p], (None, None, None, None, 1.0, None), EINVAL),
+        "sq3_batch_add_cell": ([p, i, i, i, d, d, d, p, p, i, i],
+                               (None, 24, 24, 24, 1.0, 1.0, 1.0, None, None, 8, 10), EINVAL),
+        "sq3_batch_set_bounds": ([p, i, d, d, d], (None, 0, 1.0, 2.0, 0.0), EINVAL),
+        "sq3_batch_filter": ([p], (None,), EINVAL),
+        "sq3_batch_autotune": ([p, p, p], (None, None, None), EINVAL),
         "sq3_kernel_from_hs_ex": ([p, p, i, i, d, i, d, d, i, p, p, p, p],
                                   (None, None, 4, 10, 0.0, 0, 0.3, 2.0, 0, None, None, None, None),
                                   EINVAL),
@@ -125,5 +132,5 @@ def test_argument_errors_before_any_device_work(libpath):
         assert f(*args) == want, name
     missing = set(declared_symbols()) - set(calls) - {
         "sq3_create", "sq3_destroy", "sq3_status_string", "sq3_version", "sq3_last_cuda_error",
-        "sq3_fermi_degree", "sq3_mlp_destroy"}
+        "sq3_fermi_degree", "sq3_mlp_destroy", "sq3_batch_destroy"}
     assert not missing, missing

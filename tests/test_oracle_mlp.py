@@ -75,9 +75,11 @@ def test_descriptors_have_unit_mean_and_follow_the_atoms():
     cfg = inputs.C1
     pos = inputs.fcc_positions(1, disp_sigma=0.2, seed=1)
     d = mlp.descriptors(cfg.n, cfg.L, pos)
-    # the grid sum of a Gaussian is its integral up to aliasing, which is
-    # tiny while w is above the spacing (h = 0.43 bohr)
-    np.testing.assert_allclose(d.mean(0)[2:], 1.0, rtol=1e-6)
+    # before the compression each feature has mean 1: the grid sum of a
+    # Gaussian is its integral up to aliasing, which is tiny while w is
+    # above the spacing (h = 0.43 bohr)
+    np.testing.assert_allclose(np.expm1(d).mean(0)[2:], 1.0, rtol=1e-6)
+    assert np.all(d >= 0)
     # a lattice-vector shift of every atom leaves them unchanged
     d2 = mlp.descriptors(cfg.n, cfg.L, pos + cfg.L * np.array([1, -2, 0]))
     np.testing.assert_allclose(d2, d, rtol=1e-12, atol=1e-14)
