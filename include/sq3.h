@@ -81,8 +81,11 @@ int sq3_setup_grid(sq3_ctx* ctx, int nx, int ny, int nz,
                    double Lx, double Ly, double Lz, int fd_order);
 
 /* Effective local potential V_eff = V_xc + phi (Sec. 2, Eq. (KSeqn)) on the
- * grid: device array of N doubles.  Copied into the context.
- * Errors: SQ3_ENOTSETUP (no grid), SQ3_EINVAL. */
+ * grid: device array of N doubles.  Copied into the context, with its range
+ * (the filter's spectral bounds use it).
+ * Errors: SQ3_ENOTSETUP (no grid), SQ3_EINVAL, SQ3_ENONFINITE (a value is
+ * NaN or infinite; the context then has no potential until the next
+ * successful call). */
 int sq3_set_potential(sq3_ctx* ctx, const double* V);
 
 /* Kleinman-Bylander projectors (Sec. 2, Eq. (nonlocaloperator)) as a CSR
@@ -93,9 +96,12 @@ int sq3_set_potential(sq3_ctx* ctx, const double* V);
  * Projectors that share an index list (the lm components of one atom) are
  * grouped internally.  n_proj = 0 removes the projectors.  Copied into the
  * context.  Errors: SQ3_ENOTSETUP, SQ3_EINVAL (index out of range, ptr not
- * monotone, or projectors so dense that one 8 x 8 x 4 brick of the grid holds
+ * monotone, a value or energy not finite — checked before the context's
+ * current projectors are replaced, so a rejected table changes nothing — or
+ * projectors so dense that one 8 x 8 x 4 brick of the grid holds
  * more (point, projector) entries than the nonlocal pass can stage in shared
- * memory, about 7,700). */
+ * memory, about 7,700).  A grid index may repeat within a projector; its
+ * values add. */
 int sq3_set_projectors(sq3_ctx* ctx, int n_proj, const int* ptr,
                        const int* idx, const double* val, const double* gamma);
 
@@ -201,6 +207,9 @@ int sq3_density_kernel(sq3_ctx* ctx, const void* X, int Ns, int npl,
  * doubles (overwritten). */
 int sq3_density(sq3_ctx* ctx, const void* X, const double* D, int Ns,
                 sq3_prec prec, double* rho);
+/* (sq3_density returns SQ3_ENONFINITE when rho holds a NaN or infinity,
+ * i.e. when X or D did; sq3_kernel_from_hs likewise when D or one of its
+ * scalar outputs is not finite.) */
 
 /* ---- Self-consistent-field pieces (no Hamiltonian or potential needed;
  * the grid must be set).  All arrays are device arrays of N doubles in grid

@@ -542,15 +542,17 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   if (n_proj < 0) return SQ3_EINVAL;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  const long long N = c->grid.N;
+  if (n_proj > 0) {
+    // a rejected table leaves the context's projectors as they were
+    if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
+    for (int p = 0; p < n_proj; ++p)
+      if (ptr[p + 1] < ptr[p] || !isfinite(gamma[p])) return SQ3_EINVAL;
+    for (long long e = 0; e < (long long)ptr[n_proj]; ++e)
+      if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
+  }
   free_projectors(c->proj);
   if (n_proj == 0) return SQ3_OK;
-  if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
-  const long long N = c->grid.N;
-  for (int p = 0; p < n_proj; ++p)
-    if (ptr[p + 1] < ptr[p] || !isfinite(gamma[p])) return SQ3_EINVAL;
-  const long long nnz = ptr[n_proj];
-  for (long long e = 0; e < nnz; ++e)
-    if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
   const double sq = sqrt(c->dV);
   // group consecutive projectors with identical index lists (<= 4 per ball)
   std::vector<int> bptr{0}, bidx, bp0, bnp, boff;
