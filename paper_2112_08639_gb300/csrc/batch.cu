@@ -124,65 +124,71 @@ batch_step_kernel(const BCell* __restrict__ cells, const BStep* __restrict__ ste
       }
       ac::cp_async_commit();
     };
-    float4 q[2 * BR + 1];
+    // z-neighbour ring: plane z + j - R in q[(z + j) % BQ], the z loop
+    // unrolled BQ-fold so every index is a compile-time constant
+    constexpr int BQ = 2 * BR + 1;
+    float4 q[BQ];
     if (act) {
 #pragma unroll
-      for (int i = 1; i < 2 * BR + 1; ++i) {
-        int zz = i - 1 - BR;
+      for (int j = 0; j < 2 * BR; ++j) {
+        int zz = j - BR;
         zz += (zz < 0) ? nz : 0;
         zz -= (zz >= nz) ? nz : 0;
-        q[i] = __ldg(reinterpret_cast<const float4*>(yv + (long long)zz * plane + col));
+        q[j] = __ldg(reinterpret_cast<const float4*>(yv + (long long)zz * plane + col));
       }
     }
 #pragma unroll
     for (int e = 0; e < BA; ++e) issue(e);
-    for (int z = 0; z < nz; ++z) {
-      ac::cp_async_wait<BA - 1>();
-      __syncthreads();
-      issue(z + BA);
-      if (act) {
-        const int sl = z % (BA + 1);
-        const float* ce = cen + sl * 3 * csz;
+    for (int z0 = 0; z0 < nz; z0 += BQ) {
 #pragma unroll
-        for (int i = 0; i < 2 * BR; ++i) q[i] = q[i + 1];
-        q[2 * BR] = *reinterpret_cast<const float4*>(ce + cofs);
-        const float4 vz = *reinterpret_cast<const float4*>(ce + csz + cofs);
-        const float4 yp = pv ? *reinterpret_cast<const float4*>(ce + 2 * csz + cofs)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float* row = win + sl * wsz + (ty + BR) * Wd + BPAD + x0;
-        float xw[BVW + 2 * BPAD];
+      for (int u = 0; u < BQ; ++u) {
+        const int z = z0 + u;
+        if (z >= nz) break;
+        ac::cp_async_wait<BA - 1>();
+        __syncthreads();
+        issue(z + BA);
+        if (act) {
+          const int sl = z % (BA + 1);
+          const float* ce = cen + sl * 3 * csz;
+          q[(u + 2 * BR) % BQ] = *reinterpret_cast<const float4*>(ce + cofs);
+          const float4 vz = *reinterpret_cast<const float4*>(ce + csz + cofs);
+          const float4 yp = pv ? *reinterpret_cast<const float4*>(ce + 2 * csz + cofs)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float* row = win + sl * wsz + (ty + BR) * Wd + BPAD + x0;
+          float xw[BVW + 2 * BPAD];
 #pragma unroll
-        for (int j = 0; j < (BVW + 2 * BPAD) / BVW; ++j) {
-          const float4 t = *reinterpret_cast<const float4*>(row - BPAD + j * BVW);
-          xw[j * 4 + 0] = t.x; xw[j * 4 + 1] = t.y; xw[j * 4 + 2] = t.z; xw[j * 4 + 3] = t.w;
-        }
-        const float* vzp = reinterpret_cast<const float*>(&vz);
-        const float* qc = reinterpret_cast<const float*>(&q[BR]);
-        float acc[BVW];
-#pragma unroll
-        for (int i = 0; i < BVW; ++i) acc[i] = (C.kdiag + vzp[i] - C.c) * qc[i];
-#pragma unroll
-        for (int p = 1; p <= BR; ++p) {
-          const float4 up = *reinterpret_cast<const float4*>(row + p * Wd);
-          const float4 dn = *reinterpret_cast<const float4*>(row - p * Wd);
-          const float* upp = reinterpret_cast<const float*>(&up);
-          const float* dnp = reinterpret_cast<const float*>(&dn);
-          const float* zp = reinterpret_cast<const float*>(&q[BR + p]);
-          const float* zm = reinterpret_cast<const float*>(&q[BR - p]);
-#pragma unroll
-          for (int i = 0; i < BVW; ++i) {
-            acc[i] += C.kx[p] * (xw[BPAD + i + p] + xw[BPAD + i - p]);
-            acc[i] += C.ky[p] * (upp[i] + dnp[i]);
-            acc[i] += C.kz[p] * (zp[i] + zm[i]);
+          for (int j = 0; j < (BVW + 2 * BPAD) / BVW; ++j) {
+            const float4 t = *reinterpret_cast<const float4*>(row - BPAD + j * BVW);
+            xw[j * 4 + 0] = t.x; xw[j * 4 + 1] = t.y; xw[j * 4 + 2] = t.z; xw[j * 4 + 3] = t.w;
           }
+          const float* vzp = reinterpret_cast<const float*>(&vz);
+          const float* qc = reinterpret_cast<const float*>(&q[(u + BR) % BQ]);
+          float acc[BVW];
+#pragma unroll
+          for (int i = 0; i < BVW; ++i) acc[i] = (C.kdiag + vzp[i] - C.c) * qc[i];
+#pragma unroll
+          for (int p = 1; p <= BR; ++p) {
+            const float4 up = *reinterpret_cast<const float4*>(row + p * Wd);
+            const float4 dn = *reinterpret_cast<const float4*>(row - p * Wd);
+            const float* upp = reinterpret_cast<const float*>(&up);
+            const float* dnp = reinterpret_cast<const float*>(&dn);
+            const float* zp = reinterpret_cast<const float*>(&q[(u + BR + p) % BQ]);
+            const float* zm = reinterpret_cast<const float*>(&q[(u + BR - p) % BQ]);
+#pragma unroll
+            for (int i = 0; i < BVW; ++i) {
+              acc[i] += C.kx[p] * (xw[BPAD + i + p] + xw[BPAD + i - p]);
+              acc[i] += C.ky[p] * (upp[i] + dnp[i]);
+              acc[i] += C.kz[p] * (zp[i] + zm[i]);
+            }
+          }
+          const float* ypp = reinterpret_cast<const float*>(&yp);
+          float4 o;
+          o.x = S.s1 * acc[0] + S.s2 * ypp[0];
+          o.y = S.s1 * acc[1] + S.s2 * ypp[1];
+          o.z = S.s1 * acc[2] + S.s2 * ypp[2];
+          o.w = S.s1 * acc[3] + S.s2 * ypp[3];
+          *reinterpret_cast<float4*>(ov + (long long)z * plane + col) = o;
         }
-        const float* ypp = reinterpret_cast<const float*>(&yp);
-        float4 o;
-        o.x = S.s1 * acc[0] + S.s2 * ypp[0];
-        o.y = S.s1 * acc[1] + S.s2 * ypp[1];
-        o.z = S.s1 * acc[2] + S.s2 * ypp[2];
-        o.w = S.s1 * acc[3] + S.s2 * ypp[3];
-        *reinterpret_cast<float4*>(ov + (long long)z * plane + col) = o;
       }
     }
     ac::cp_async_wait<0>();

@@ -428,63 +428,71 @@ cheb_step_ring_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
     cp_async_commit();
   };
 
-  VT q[2 * R + 1];
+  // The 2R+1 z-neighbours live in a register ring: plane z + j - R is in
+  // q[(z + j) % Q], Q = 2R + 1.  The z loop is unrolled Q-fold so that every
+  // ring index is a compile-time constant: the new entry overwrites the
+  // slot of the plane that just left the window and no register moves.
+  constexpr int Q = 2 * R + 1;
+  VT q[Q];
 #pragma unroll
-  for (int i = 1; i < 2 * R + 1; ++i) {
-    int zz = i - 1 - R;
+  for (int j = 0; j < 2 * R; ++j) {
+    int zz = j - R;
     zz += (zz < 0) ? nz : 0;
     zz -= (zz >= nz) ? nz : 0;
-    q[i] = __ldg(reinterpret_cast<const VT*>(yv + (long long)zz * plane + col));
+    q[j] = __ldg(reinterpret_cast<const VT*>(yv + (long long)zz * plane + col));
   }
 #pragma unroll
   for (int it = 0; it < A; ++it) issue(it);
 
-  for (int z = 0; z < nz; ++z) {
-    cp_async_wait<A - 1>();
-    __syncthreads();     // entry z landed for all; entry z - 1 fully consumed
-    issue(z + A);        // reuses the slot of entry z - 1
-    const int sl = z % (A + 1);
-    const T* ce = cen + sl * 3 * csz;
+  for (int z0 = 0; z0 < nz; z0 += Q) {
 #pragma unroll
-    for (int i = 0; i < 2 * R; ++i) q[i] = q[i + 1];
-    q[2 * R] = *reinterpret_cast<const VT*>(ce + cofs);
-    const VT vz = *reinterpret_cast<const VT*>(ce + csz + cofs);
-    const VT yp = pv ? *reinterpret_cast<const VT*>(ce + 2 * csz + cofs) : VT{};
-    const T* row = win + sl * wsz + (ty + R) * Wd + PAD + x0;
-    T xw[XW];
+    for (int u = 0; u < Q; ++u) {
+      const int z = z0 + u;
+      if (z >= nz) break;                  // the same for every thread
+      cp_async_wait<A - 1>();
+      __syncthreads();     // entry z landed for all; entry z - 1 fully consumed
+      issue(z + A);        // reuses the slot of entry z - 1
+      const int sl = z % (A + 1);
+      const T* ce = cen + sl * 3 * csz;
+      q[(u + 2 * R) % Q] = *reinterpret_cast<const VT*>(ce + cofs);
+      const VT vz = *reinterpret_cast<const VT*>(ce + csz + cofs);
+      const VT yp = pv ? *reinterpret_cast<const VT*>(ce + 2 * csz + cofs) : VT{};
+      const T* row = win + sl * wsz + (ty + R) * Wd + PAD + x0;
+      T xw[XW];
 #pragma unroll
-    for (int j = 0; j < XW / VW; ++j) {
-      const VT t = *reinterpret_cast<const VT*>(row - PAD + j * VW);
-      const T* tp = reinterpret_cast<const T*>(&t);
+      for (int j = 0; j < XW / VW; ++j) {
+        const VT t = *reinterpret_cast<const VT*>(row - PAD + j * VW);
+        const T* tp = reinterpret_cast<const T*>(&t);
 #pragma unroll
-      for (int i = 0; i < VW; ++i) xw[j * VW + i] = tp[i];
-    }
-    T acc[VW];
-    const T* vzp = reinterpret_cast<const T*>(&vz);
-    const T* qc = reinterpret_cast<const T*>(&q[R]);
-#pragma unroll
-    for (int i = 0; i < VW; ++i) acc[i] = (k.diag + vzp[i] - c) * qc[i];
-#pragma unroll
-    for (int p = 1; p <= R; ++p) {
-      const VT up = *reinterpret_cast<const VT*>(row + p * Wd);
-      const VT dn = *reinterpret_cast<const VT*>(row - p * Wd);
-      const T* upp = reinterpret_cast<const T*>(&up);
-      const T* dnp = reinterpret_cast<const T*>(&dn);
-      const T* zp = reinterpret_cast<const T*>(&q[R + p]);
-      const T* zm = reinterpret_cast<const T*>(&q[R - p]);
-#pragma unroll
-      for (int i = 0; i < VW; ++i) {
-        acc[i] += k.ax[p] * (xw[PAD + i + p] + xw[PAD + i - p]);
-        acc[i] += k.ay[p] * (upp[i] + dnp[i]);
-        acc[i] += k.az[p] * (zp[i] + zm[i]);
+        for (int i = 0; i < VW; ++i) xw[j * VW + i] = tp[i];
       }
-    }
-    VT o;
-    T* op = reinterpret_cast<T*>(&o);
-    const T* ypp = reinterpret_cast<const T*>(&yp);
+      T acc[VW];
+      const T* vzp = reinterpret_cast<const T*>(&vz);
+      const T* qc = reinterpret_cast<const T*>(&q[(u + R) % Q]);
 #pragma unroll
-    for (int i = 0; i < VW; ++i) op[i] = s1 * acc[i] + s2 * ypp[i];
-    *reinterpret_cast<VT*>(ov + (long long)z * plane + col) = o;
+      for (int i = 0; i < VW; ++i) acc[i] = (k.diag + vzp[i] - c) * qc[i];
+#pragma unroll
+      for (int p = 1; p <= R; ++p) {
+        const VT up = *reinterpret_cast<const VT*>(row + p * Wd);
+        const VT dn = *reinterpret_cast<const VT*>(row - p * Wd);
+        const T* upp = reinterpret_cast<const T*>(&up);
+        const T* dnp = reinterpret_cast<const T*>(&dn);
+        const T* zp = reinterpret_cast<const T*>(&q[(u + R + p) % Q]);
+        const T* zm = reinterpret_cast<const T*>(&q[(u + R - p) % Q]);
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+          acc[i] += k.ax[p] * (xw[PAD + i + p] + xw[PAD + i - p]);
+          acc[i] += k.ay[p] * (upp[i] + dnp[i]);
+          acc[i] += k.az[p] * (zp[i] + zm[i]);
+        }
+      }
+      VT o;
+      T* op = reinterpret_cast<T*>(&o);
+      const T* ypp = reinterpret_cast<const T*>(&yp);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) op[i] = s1 * acc[i] + s2 * ypp[i];
+      *reinterpret_cast<VT*>(ov + (long long)z * plane + col) = o;
+    }
   }
   cp_async_wait<0>();
 }

@@ -154,18 +154,28 @@ def projectors(n: int, L: float, positions: np.ndarray, seed: int = 0,
     """Seeded s/p Gaussian projectors, 4 per atom, minimum image."""
     h = L / n
     dV = h ** 3
-    pts = grid_points(n, L)
     rng = np.random.default_rng(seed + 7919)
     ptr, idx, val, gam = [0], [], [], []
     for R in positions:
-        d = pts - R
+        # the grid points of the cube of half-width rcut around R (wrapped,
+        # each index once), in ascending grid order
+        ax = []
+        for a in range(3):
+            lo, hi = int(np.floor((R[a] - rcut) / h)), int(np.ceil((R[a] + rcut) / h))
+            ax.append(np.unique(np.mod(np.arange(lo, hi + 1), n)))
+        kz, ky, kx = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        cand = (kx + n * ky + n * n * kz).ravel()
+        order = np.argsort(cand, kind="stable")
+        cand = cand[order]
+        d = np.stack([kx.ravel()[order], ky.ravel()[order], kz.ravel()[order]], axis=1) * h - R
         d -= L * np.round(d / L)
         r2 = np.einsum("ij,ij->i", d, d)
-        sel = np.nonzero(r2 < rcut * rcut)[0]
-        env = np.exp(-r2[sel] / (rc * rc))
+        keep = np.nonzero(r2 < rcut * rcut)[0]
+        sel, d, r2 = cand[keep], d[keep], r2[keep]
+        env = np.exp(-r2 / (rc * rc))
         g_s, g_p = rng.uniform(0.1, 1.0, size=2)
-        for chi, g in ((env, g_s), (d[sel, 0] * env, g_p),
-                       (d[sel, 1] * env, g_p), (d[sel, 2] * env, g_p)):
+        for chi, g in ((env, g_s), (d[:, 0] * env, g_p),
+                       (d[:, 1] * env, g_p), (d[:, 2] * env, g_p)):
             chi = chi / np.sqrt(np.sum(chi * chi) * dV)
             idx.append(sel.astype(np.int32))
             val.append(chi)
