@@ -44,7 +44,16 @@ from __future__ import annotations
 
 import numpy as np
 
+import scipy.sparse.linalg as sla
+
 from . import fd, fermi, hamiltonian
+
+
+def _as_operator(parts):
+    """H of hamiltonian_sparse as a scipy LinearOperator."""
+    Hloc = parts[0]
+    return sla.LinearOperator(Hloc.shape, matvec=lambda v: hamiltonian.apply(parts, v[:, None])[:, 0],
+                              dtype=float)
 
 # Perdew-Wang 1992 parameters of the spin-unpolarised correlation energy
 # (A, alpha1, beta1..beta4; p = 1)
@@ -274,8 +283,11 @@ def scf_sq3(n: int, L: float, positions: np.ndarray, X0: np.ndarray, sigma: floa
     Chebyshev density kernel with exact spectral bounds, rho) `passes[0]`
     times in the first iteration and `passes[1]` times after, from the
     starting block X0 (N x Ns, e.g. seeded random); filt = (a, b, a0) are the
-    filter's cutoff, upper bound and lower estimate.  Stops when the L1 change of rho per electron is below
-    `tol`; F by Eq. (FreeEnergy:NewForm) from the last output density."""
+    filter's cutoff, upper bound and lower estimate; every iteration checks
+    that b lies above the spectrum of its H (a ValueError otherwise: the
+    filter would amplify the top of the spectrum).  Stops when the L1 change
+    of rho per electron is below `tol`; F by Eq. (FreeEnergy:NewForm) from
+    the last output density."""
     from . import subspace
     natoms = len(positions)
     Ne = Z * natoms
@@ -291,6 +303,13 @@ def scf_sq3(n: int, L: float, positions: np.ndarray, X0: np.ndarray, sigma: floa
         _, vxc = lda_xc(rho)
         parts = hamiltonian.hamiltonian_sparse(n, L, phi + vxc, proj, order)
         apply_H = lambda Y: hamiltonian.apply(parts, Y)
+        # the filter needs b_up above the spectrum of this iteration's H: the
+        # largest eigenvalue of the sparse H by a few Lanczos steps of scipy
+        lam_max = float(sla.eigsh(_as_operator(parts), k=1, which="LA", tol=1e-6,
+                                  return_eigenvectors=False)[0])
+        if lam_max > b_up:
+            raise ValueError(f"filter upper bound {b_up} below the spectrum of H "
+                             f"({lam_max}) at SCF iteration {it}")
         for _ in range(passes[0] if it == 0 else passes[1]):
             out = subspace.sq3_iteration(apply_H, X, degree, a, b_up, a0, npl, sigma, Ne, dV)
             X = out["X"]

@@ -211,3 +211,15 @@ def test_scf_in_the_papers_order_reaches_the_diagonalisation_scf():
     assert np.sum(np.abs(got["rho"] - ref["rho"])) * dV / 12.0 < 1e-10
     assert abs(got["F"] - ref["F"]) / 4 < 1e-10
     assert abs(got["mu"] - ref["mu"]) < 1e-10
+
+
+def test_scf_in_the_papers_order_rejects_a_filter_bound_below_the_spectrum():
+    """An upper filter bound below the top of H's spectrum (here the FD
+    kinetic maximum alone is 24 Ha at 12^3) is caught at the first
+    iteration instead of letting the filter amplify the top states."""
+    n, L, Ns = 12, inputs.A0_FCC, 20
+    pos = inputs.fcc_positions(1, disp_sigma=0.05, seed=0)
+    X0 = inputs.random_block(n ** 3, Ns, seed=0).T
+    with pytest.raises(ValueError, match="below the spectrum"):
+        scf.scf_sq3(n, L, pos, X0, inputs.ev_to_ha(10.0), inputs.Z_VALENCE, inputs.RC_LOCAL,
+                    (1.0, 5.0, -2.0), npl=40, max_iter=2)
