@@ -91,6 +91,11 @@ def parse():
     p.add_argument("--no-compare-starts", dest="compare_starts", action="store_false")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false",
+                   help="skip the oracle's CPU timing (profiling runs)")
+    p.add_argument("--ns", type=int, default=None,
+                   help="iteration mode: number of vectors other than the workload's "
+                        "(a smaller footprint of the same kernels, for profiling)")
     return p.parse_args()
 
 
@@ -189,6 +194,10 @@ def _setup(args, rank):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cfg = inputs.CONFIGS[args.config]
+    if getattr(args, "ns", None):
+        # a smaller block on the same cell (profiling captures)
+        import dataclasses
+        cfg = dataclasses.replace(cfg, Ns=args.ns)
     cell = inputs.make_cell(cfg)
     ctx = sq3.Context(dev)
     ctx.setup_grid(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L, 12)
@@ -324,6 +333,32 @@ def run_solve(args, rank, world):
         e2e_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.median(e2e_t))
+    # one more end-to-end step, with a synchronisation after each phase, for
+    # the breakdown of its time (not part of the timed steps)
+    phases = {}
+
+    def mark(name, t0):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        phases[name] = round(t1 - t0, 4)
+        return t1
+
+    t = time.perf_counter()
+    cell.X.copy_(Xh, non_blocking=True)
+    t = mark("h2d_block", t)
+    cell.bounds, cell.rho_prev, cell.pos_prev = bounds_prev, rho_prev, pos_prev
+    pr1 = inputs.projectors(cfg.n, cfg.L, R1, seed=cell.proj_seed)
+    t = mark("projector_values_host", t)
+    cell.ctx.set_projectors(pr1.ptr, pr1.idx, pr1.val, pr1.gamma)
+    t = mark("set_projectors", t)
+    cell.ctx.pseudocharge(R1, inputs.Z_VALENCE, inputs.RC_LOCAL, out=cell.b)
+    cell.pos = R1.copy()
+    cell.start_density(args.start, model)
+    t = mark("pseudocharge_and_start", t)
+    cell.solve(SCF_TOL, raise_on_noconv=False)
+    t = mark("scf_solve", t)
+    rho_h.copy_(cell.rho, non_blocking=True)
+    mark("d2h_rho", t)
     h2d = Xh.numel() * Xh.element_size() + cfg.natoms * 3 * 8
     d2h = cfg.N * 8
 
@@ -395,7 +430,8 @@ def run_solve(args, rank, world):
                 "per_iteration": [{k: (round(v, 9) if isinstance(v, float) else v)
                                    for k, v in h.items()} for h in hist]},
         "e2e": {"value": round(e2e_s, 6), "unit": "s", "stat": f"median of {len(e2e_t)} solves",
-                "steps_s": [round(x, 4) for x in e2e_t], "h2d_bytes_per_step": int(h2d),
+                "steps_s": [round(x, 4) for x in e2e_t], "phases_s": phases,
+                "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
         "stage_ms_per_step": _stage_summary(prof, args.steps),
@@ -753,6 +789,8 @@ def main():
     else:
         res, passes = run_iteration(args, rank, world)
     if rank == 0 and args.mode == "batch":
+        print(json.dumps(res))
+    elif rank == 0 and not args.cpu_baseline:
         print(json.dumps(res))
     elif rank == 0:
         v, cores, sample, parts = run_oracle_sample(args.config, passes)

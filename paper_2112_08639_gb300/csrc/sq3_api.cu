@@ -553,170 +553,51 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   }
   free_projectors(c->proj);
   if (n_proj == 0) return SQ3_OK;
-  const double sq = sqrt(c->dV);
-  // group consecutive projectors with identical index lists (<= 4 per ball)
-  std::vector<int> bptr{0}, bidx, bp0, bnp, boff;
-  std::vector<double> bval;
-  int p = 0;
-  while (p < n_proj) {
-    int q = p + 1;
-    const int len = ptr[p + 1] - ptr[p];
-    while (q < n_proj && q - p < 4 && ptr[q + 1] - ptr[q] == len &&
-           memcmp(idx + ptr[q], idx + ptr[p], sizeof(int) * len) == 0)
-      ++q;
-    bp0.push_back(p);
-    bnp.push_back(q - p);
-    boff.push_back((int)bval.size());
-    for (int e = 0; e < len; ++e) bidx.push_back(idx[ptr[p] + e]);
-    for (int r = p; r < q; ++r)
-      for (int e = 0; e < len; ++e) bval.push_back(val[ptr[r] + e] * sq);
-    bptr.push_back((int)bidx.size());
-    p = q;
-  }
+  ProjectorHostTables T;
+  projector_host_tables(c->grid.nx, c->grid.ny, c->grid.nz, c->dV, n_proj, ptr, idx, val,
+                        gamma, T);
   Projectors P;
   P.n_proj = n_proj;
-  P.n_ball = (int)bp0.size();
+  P.n_ball = (int)T.bp0.size();
+  P.vnl_lo = T.vnl_lo;
+  P.vnl_hi = T.vnl_hi;
+  P.max_brick_balls = T.max_brick_balls;
+  P.max_brick_entries = T.max_brick_entries;
   int rc = SQ3_OK;
+  // shared memory of the nonlocal pass, FP64 variant (two boxes of 8
+  // vectors, two coefficient buffers, both entry orders, barriers, alignment)
+  if (nl_pass_smem_bytes(8, 8, 2, T.max_brick_balls, T.max_brick_entries) > 227 * 1024)
+    rc = SQ3_EINVAL;
   rc = rc ? rc : upload(&P.gamma, gamma, (size_t)n_proj);
-  // brick tables for the nonlocal pass (8 x 8 x NL_BZ bricks, x fastest),
-  // grouped by ball: the <= 4 projectors of one ball share its points
-  {
-    const int nx = c->grid.nx, ny = c->grid.ny, nz = c->grid.nz;
-    const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8, nbz = (nz + NL_BZ - 1) / NL_BZ;
-    const long long nb = (long long)nbx * nby * nbz;
-    const int nballs = (int)bp0.size();
-    // point -> (ball, position in the ball's point list), balls ascending
-    std::vector<int> kptr(N + 1, 0);
-    for (int B = 0; B < nballs; ++B)
-      for (int e = bptr[B]; e < bptr[B + 1]; ++e) kptr[bidx[e] + 1]++;
-    for (long long k = 0; k < N; ++k) kptr[k + 1] += kptr[k];
-    std::vector<int> kfill(kptr.begin(), kptr.end() - 1), kball(bptr[nballs]), kpos(bptr[nballs]);
-    for (int B = 0; B < nballs; ++B)
-      for (int e = bptr[B]; e < bptr[B + 1]; ++e) {
-        const int k = bidx[e];
-        kball[kfill[k]] = B;
-        kpos[kfill[k]] = e - bptr[B];
-        kfill[k]++;
-      }
-    auto ball_val4 = [&](int B, int pos, double* v4) {
-      const int len = bptr[B + 1] - bptr[B];
-      for (int q = 0; q < 4; ++q)
-        v4[q] = (q < bnp[B]) ? bval[(size_t)boff[B] + (size_t)q * len + pos] : 0.0;
-    };
-    // Gershgorin bounds of V_nl: its nonzero eigenvalues are those of
-    // Gamma S, S_pq = c_p . c_q the overlaps of the projectors (formed per
-    // pair of balls that share a grid point)
-    {
-      std::vector<std::vector<std::pair<int, std::array<double, 16>>>> ov(nballs);
-      double v4a[4], v4b[4];
-      for (long long k = 0; k < N; ++k)
-        for (int i = kptr[k]; i < kptr[k + 1]; ++i) {
-          ball_val4(kball[i], kpos[i], v4a);
-          for (int j = kptr[k]; j < kptr[k + 1]; ++j) {
-            ball_val4(kball[j], kpos[j], v4b);
-            auto& row = ov[kball[i]];
-            size_t t = 0;
-            while (t < row.size() && row[t].first != kball[j]) ++t;
-            if (t == row.size()) row.push_back({kball[j], {}});
-            for (int q = 0; q < 4; ++q)
-              for (int r = 0; r < 4; ++r) row[t].second[4 * q + r] += v4a[q] * v4b[r];
-          }
-        }
-      double lo = 0.0, hi = 0.0;
-      for (int B = 0; B < nballs; ++B)
-        for (int q = 0; q < bnp[B]; ++q) {
-          const int pq = bp0[B] + q;
-          double diag = 0.0, rad = 0.0;
-          for (auto& e : ov[B])
-            for (int r = 0; r < bnp[e.first]; ++r) {
-              const double v = gamma[pq] * e.second[4 * q + r];
-              if (e.first == B && r == q) diag = v;
-              else rad += fabs(v);
-            }
-          lo = std::min(lo, diag - rad);
-          hi = std::max(hi, diag + rad);
-        }
-      P.vnl_lo = lo;
-      P.vnl_hi = hi;
+  rc = rc ? rc : upload(&P.nb_ball_ptr, T.sptr.data(), T.sptr.size());
+  rc = rc ? rc : upload(&P.nb_slot_pid, T.spid.data(), T.spid.size());
+  rc = rc ? rc : upload(&P.nb_pt_ptr, T.qptr.data(), T.qptr.size());
+  rc = rc ? rc : upload(&P.nb_pt_lb, T.qlb.data(), T.qlb.size());
+  rc = rc ? rc : upload(&P.nb_pt_val, T.qval.data(), T.qval.size());
+  rc = rc ? rc : upload(&P.nb_bl_ptr, T.zptr.data(), T.zptr.size());
+  rc = rc ? rc : upload(&P.nb_bl_pt, T.zpt.data(), T.zpt.size());
+  rc = rc ? rc : upload(&P.nb_bl_val, T.zval.data(), T.zval.size());
+  // FP32 copies of the values, converted on the device
+  for (int w = 0; w < 2 && rc == SQ3_OK; ++w) {
+    const double* src = w ? P.nb_bl_val : P.nb_pt_val;
+    float** dst = w ? &P.nb_bl_valf : &P.nb_pt_valf;
+    const long long n = (long long)(w ? T.zval.size() : T.qval.size());
+    if (n == 0) continue;
+    if (cudaMalloc((void**)dst, (size_t)n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      *dst = nullptr;
+      rc = SQ3_ENOMEM;
+      break;
     }
-    std::vector<int> qptr{0}, sptr{0}, spid, zptr{0};
-    std::vector<short> qlb, zpt;
-    std::vector<double> qval, zval;
-    std::vector<int> ids;
-    std::vector<std::vector<std::pair<short, int>>> lists;   // (t, kfill index)
-    int maxb = 0, maxe = 0;
-    for (long long b = 0; b < nb; ++b) {
-      const int ebeg = (int)qlb.size();
-      const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby),
-                bz = (int)(b / ((long long)nbx * nby));
-      auto gidx = [&](int t) -> long long {
-        const int ix = bx * 8 + (t & 7), iy = by * 8 + ((t >> 3) & 7),
-                  iz = bz * NL_BZ + (t >> 6);
-        if (ix >= nx || iy >= ny || iz >= nz) return -1;
-        return (long long)ix + (long long)nx * (iy + (long long)ny * iz);
-      };
-      ids.clear();
-      for (int t = 0; t < NL_BRICK_PTS; ++t) {
-        const long long k = gidx(t);
-        if (k < 0) continue;
-        for (int j = kptr[k]; j < kptr[k + 1]; ++j) ids.push_back(kball[j]);
-      }
-      std::sort(ids.begin(), ids.end());
-      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
-      lists.assign(ids.size(), {});
-      double v4[4];
-      for (int t = 0; t < NL_BRICK_PTS; ++t) {
-        const long long k = gidx(t);
-        if (k >= 0) {
-          for (int j = kptr[k]; j < kptr[k + 1]; ++j) {
-            const int lb = (int)(std::lower_bound(ids.begin(), ids.end(), kball[j]) - ids.begin());
-            qlb.push_back((short)lb);
-            ball_val4(kball[j], kpos[j], v4);
-            qval.insert(qval.end(), v4, v4 + 4);
-            lists[lb].push_back({(short)t, j});
-          }
-        }
-        qptr.push_back((int)qlb.size());
-      }
-      for (size_t lb = 0; lb < ids.size(); ++lb) {
-        const int B = ids[lb];
-        for (int q = 0; q < 4; ++q) spid.push_back(q < bnp[B] ? bp0[B] + q : -1);
-        for (auto& pr : lists[lb]) {
-          zpt.push_back(pr.first);
-          ball_val4(B, kpos[pr.second], v4);
-          zval.insert(zval.end(), v4, v4 + 4);
-        }
-        zptr.push_back((int)zpt.size());
-      }
-      sptr.push_back((int)(spid.size() / 4));
-      maxb = std::max(maxb, (int)ids.size());
-      maxe = std::max(maxe, (int)qlb.size() - ebeg);
-    }
-    P.max_brick_balls = maxb;
-    P.max_brick_entries = maxe;
-    // shared memory of the nonlocal pass, FP64 variant (two boxes of 8
-    // vectors, two coefficient buffers, both entry orders, barriers, alignment)
-    const size_t need = nl_pass_smem_bytes(8, 8, 2, maxb, maxe);
-    (void)nbz;
-    if (need > 227 * 1024) rc = SQ3_EINVAL;
-    std::vector<float> qvalf(qval.begin(), qval.end()), zvalf(zval.begin(), zval.end());
-    rc = rc ? rc : upload(&P.nb_ball_ptr, sptr.data(), sptr.size());
-    rc = rc ? rc : upload(&P.nb_slot_pid, spid.data(), spid.size());
-    rc = rc ? rc : upload(&P.nb_pt_ptr, qptr.data(), qptr.size());
-    rc = rc ? rc : upload(&P.nb_pt_lb, qlb.data(), qlb.size());
-    rc = rc ? rc : upload(&P.nb_pt_val, qval.data(), qval.size());
-    rc = rc ? rc : upload(&P.nb_pt_valf, qvalf.data(), qvalf.size());
-    rc = rc ? rc : upload(&P.nb_bl_ptr, zptr.data(), zptr.size());
-    rc = rc ? rc : upload(&P.nb_bl_pt, zpt.data(), zpt.size());
-    rc = rc ? rc : upload(&P.nb_bl_val, zval.data(), zval.size());
-    rc = rc ? rc : upload(&P.nb_bl_valf, zvalf.data(), zvalf.size());
+    to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(src, *dst, n);
   }
-  P.h_bptr = std::move(bptr);
-  P.h_bidx = std::move(bidx);
-  P.h_bp0 = std::move(bp0);
-  P.h_bnp = std::move(bnp);
-  P.h_boff = std::move(boff);
-  P.h_bval = std::move(bval);
+  if (rc == SQ3_OK) rc = cuda_err(cudaStreamSynchronize(c->stream));
+  P.h_bptr = std::move(T.bptr);
+  P.h_bidx = std::move(T.bidx);
+  P.h_bp0 = std::move(T.bp0);
+  P.h_bnp = std::move(T.bnp);
+  P.h_boff = std::move(T.boff);
+  P.h_bval = std::move(T.bval);
   P.h_gamma.assign(gamma, gamma + n_proj);
   c->proj = std::move(P);
   if (rc) { free_projectors(c->proj); return rc; }

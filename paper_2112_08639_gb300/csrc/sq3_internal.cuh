@@ -201,6 +201,22 @@ void launch_cheb_step(const sq3_ctx* ctx, const T* y, const T* yprev, T* out, in
 // Dynamic shared memory of the nonlocal pass for element size es, VB vectors
 // per box, NBUF boxes, and the largest brick (balls, entries).
 size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entries);
+// Host tables of a projector set (projector_tables.cu): the balls (the
+// Projectors host copies), the brick tables (the nb_* arrays: sptr, spid,
+// qptr, qlb, qval, zptr, zpt, zval) and the Gershgorin bounds of V_nl.  The
+// CSR input must already be validated; repeated indices are merged.
+struct ProjectorHostTables {
+  std::vector<int> bptr, bidx, bp0, bnp, boff;
+  std::vector<double> bval;
+  std::vector<int> sptr, spid, qptr, zptr;
+  std::vector<short> qlb, zpt;
+  std::vector<double> qval, zval;
+  int max_brick_balls = 0, max_brick_entries = 0;
+  double vnl_lo = 0.0, vnl_hi = 0.0;
+};
+void projector_host_tables(int nx, int ny, int nz, double dV, int n_proj, const int* ptr,
+                           const int* idx, const double* val, const double* gamma,
+                           ProjectorHostTables& T);
 // With gC == nullptr the pass only projects (gC_next += gamma c^T out) and
 // leaves out untouched.  Returns an SQ3_* status (EINVAL when a brick's
 // tables exceed shared memory or out is not 16-byte aligned).

@@ -458,10 +458,11 @@ cheb_step_ring_kernel(int nx, int ny, int nz, int TY, StepCoef<T> k,
       const VT vz = *reinterpret_cast<const VT*>(ce + csz + cofs);
       const VT yp = pv ? *reinterpret_cast<const VT*>(ce + 2 * csz + cofs) : VT{};
       const T* row = win + sl * wsz + (ty + R) * Wd + PAD + x0;
+      // the x-window; its centre vector is the queue's centre entry
       T xw[XW];
 #pragma unroll
       for (int j = 0; j < XW / VW; ++j) {
-        const VT t = *reinterpret_cast<const VT*>(row - PAD + j * VW);
+        const VT t = (j == PV) ? q[(u + R) % Q] : *reinterpret_cast<const VT*>(row - PAD + j * VW);
         const T* tp = reinterpret_cast<const T*>(&t);
 #pragma unroll
         for (int i = 0; i < VW; ++i) xw[j * VW + i] = tp[i];
