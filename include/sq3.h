@@ -351,10 +351,12 @@ int sq3_verlet(int natoms, const double* masses, double dt, double* R, double* V
  * counterpart: throughput for many uneven cells on one GPU).  Each cell has
  * its own periodic grid (12th-order FD Laplacian), local potential and FP32
  * block; one Chebyshev filter (as sq3_cheb_filter with SQ3_MIXED and no
- * projectors) of every cell runs as one persistent launch per filter step
- * (CTAs claim (cell, vector, row tile) items from a device counter; no
- * CTA waits on another), the launches captured once into a CUDA graph and
- * replayed; the tile height and the resident CTAs per SM are chosen by
+ * projectors, equal up to FP32 rounding) of every cell runs as ONE
+ * persistent launch: CTAs claim (cell, vector) items from a device counter,
+ * largest cells first, and take the vector through all of its filter
+ * steps, so its iterates stay in L2 between steps (no CTA waits on
+ * another); the launch is captured once into a CUDA graph and replayed;
+ * the tile height and the resident CTAs per SM are chosen by
  * sq3_batch_autotune. ---- */
 typedef struct sq3_batch sq3_batch;
 int sq3_batch_create(int device, void* cuda_stream, sq3_batch** out);

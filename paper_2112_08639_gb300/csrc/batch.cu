@@ -1,18 +1,24 @@
 // Batched Chebyshev filtering of many independent cells (not in the paper:
 // throughput for many uneven cells on one GPU).  Every cell has its own
-// periodic grid, FP32 potential and FP32 block of Ns vectors; one filter
-// step of every cell runs in ONE persistent launch: the CTAs (a multiple of
-// the SM count) take work items from a device counter, an item being one
-// (cell, vector, row tile) march along z of the local Hamiltonian step
+// periodic grid, FP32 potential and FP32 block of Ns vectors; the whole
+// filter of every cell runs in ONE persistent launch: the CTAs (a multiple
+// of the SM count) take work items from a device counter, an item being one
+// vector of one cell, which the CTA takes through all of the cell's filter
+// steps.  Each step marches the vector's row tiles along z of the local
+// Hamiltonian step
 //   out = s1 (H y - c y) + s2 yprev,   H = -1/2 L_12 + V,
-// the same arithmetic, in the same order, as the single-cell FP32 ring
-// stencil.  The m_max launches of a filter (cells with smaller degrees take
-// no items in their missing steps) and the final copies back into the cells'
-// blocks are captured once into a CUDA graph and replayed; the per-cell
+// with the single-cell FP32 ring stencil's tiling, rings and register
+// queue; the taps are summed per axis with the twelfth-order weights as
+// compile-time constants and then scaled by the cell's -1/2 / h^2, so a cell
+// carries five scalars instead of 19 coefficients (equal to the single-cell
+// step up to FP32 rounding).  A vector's filter needs nothing from other
+// vectors, so its steps follow each other inside one CTA with no grid-wide
+// synchronisation, and its two live iterates stay in L2 from step to step.
+// The launch is captured once into a CUDA graph and replayed; the per-cell
 // recurrence coefficients live in a device table that the host refreshes
 // before each replay, so new filter bounds need no new capture.  The tile
-// height (rows per item) and the number of resident CTAs are picked by a
-// small autotuner that times each candidate on the batch itself.
+// height and the number of resident CTAs are picked by a small autotuner
+// that times each candidate on the batch itself.
 //
 // Work items are claimed with one atomicAdd each; nothing waits on another
 // CTA, so there is no spin-wait anywhere in this file.
@@ -33,6 +39,7 @@ constexpr int BVW = 4;             // floats per thread along x
 constexpr int BPAD = 8;            // wrapped columns per side (R rounded up to VW)
 constexpr int BA = 4;              // planes in flight
 constexpr int BTHREADS = 256;
+constexpr int BKC = 3;             // precomputed window copies per thread
 constexpr int BMAX_CELLS = 256;
 constexpr int BMAX_STEPS = 256;
 
@@ -42,7 +49,8 @@ struct BCell {
   long long N;
   const float* V;
   float* buf[2];                       // [0] the cell's block X, [1] work block
-  float kdiag, kx[BR + 1], ky[BR + 1], kz[BR + 1];
+  float kdiag;                         // -1/2 w_0 (1/hx^2 + 1/hy^2 + 1/hz^2)
+  float hx2, hy2, hz2;                 // -1/2 / h^2 per axis
   float c;                             // filter centre
 };
 
@@ -52,147 +60,223 @@ struct BStep {
   int y, prev, out;                    // buffer ids (-1: no yprev)
 };
 
+// Second-derivative weights w_1..w_R of order 2R (R = 6), the closed form
+// 2 (-1)^(p+1) (R!)^2 / (p^2 (R-p)! (R+p)!), as compile-time constants: the
+// taps of every cell are w_p times its -1/2 / h^2, so a cell carries only its
+// three spacings.
+__host__ __device__ constexpr double bfact(int k) { return k <= 1 ? 1.0 : k * bfact(k - 1); }
+__host__ __device__ constexpr float bw(int p) {
+  return (float)(2.0 * ((p % 2) ? 1.0 : -1.0) * bfact(BR) * bfact(BR) /
+                 ((double)p * p * bfact(BR - p) * bfact(BR + p)));
+}
+
+// w_p as an immediate for an index that unrolling makes constant
+__device__ __forceinline__ float bwc(int p) {
+  constexpr float w1 = bw(1), w2 = bw(2), w3 = bw(3), w4 = bw(4), w5 = bw(5), w6 = bw(6);
+  switch (p) {
+    case 1: return w1;
+    case 2: return w2;
+    case 3: return w3;
+    case 4: return w4;
+    case 5: return w5;
+    default: return w6;
+  }
+}
+
 __host__ __device__ inline int bwidth(int nx) {
   // row stride congruent to nx modulo the 128-byte bank cycle (32 floats)
   return nx + 2 * BPAD + ((32 - (2 * BPAD) % 32) % 32);
 }
 
-__global__ void __launch_bounds__(BTHREADS, 1)
-batch_step_kernel(const BCell* __restrict__ cells, const BStep* __restrict__ steps,
-                  const long long* __restrict__ item0, int ncells, long long total,
-                  unsigned long long* counter) {
+// One item = one vector of one cell through ALL its filter steps: the CTA
+// marches the vector's row tiles along z for step 1, then step 2, ..., so a
+// step reads what the same CTA wrote in the step before (visible after the
+// CTA barrier; every read of the block goes to L2, none through L1) and a
+// vector's two live iterates (2 N words) stay in L2 between steps instead of
+// streaming through HBM once per step.  Items are claimed largest cell
+// first (the host orders them), so the small ones fill the tail.
+__global__ void __launch_bounds__(BTHREADS, 2)
+batch_filter_kernel(const BCell* __restrict__ cells, const BStep* __restrict__ steps,
+                    const long long* __restrict__ item0, const int* __restrict__ cell_of,
+                    int ncells, long long total, unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_item;
   const int tid = threadIdx.x;
+  const int nthr = blockDim.x;       // >= the largest tile's thread count
   for (;;) {
     if (tid == 0) s_item = (long long)atomicAdd(counter, 1ull);
     __syncthreads();
     const long long it = s_item;
     __syncthreads();
     if (it >= total) return;
-    // the cell of this item: item0 is the prefix sum over cells
-    int ci = 0;
-    while (ci + 1 < ncells && item0[ci + 1] <= it) ++ci;
+    // position of the item's cell in the claim order (binary search of the
+    // prefix sums), then the cell
+    int lo = 0, hi = ncells - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item0[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const int ci = cell_of[lo];
     const BCell& C = cells[ci];
-    const BStep S = steps[ci];
-    const long long local = it - item0[ci];
-    const long long vec = local / C.tiles;
-    const int tile = (int)(local - vec * C.tiles);
+    const long long vec = it - item0[lo];
     const int nx = C.nx, ny = C.ny, nz = C.nz, TY = C.TY, TX = C.TX, Wd = C.Wd;
+    const float kdiag = C.kdiag, kc = C.c, hx2 = C.hx2, hy2 = C.hy2, hz2 = C.hz2;
     const int nact = TX * TY;                         // threads with points
     const bool act = tid < nact;
     const int tx = act ? tid % TX : 0, ty = act ? tid / TX : 0;
     const int x0 = tx * BVW;
-    const int y0 = tile * TY;
     const int plane = nx * ny;
-    const float* yv = C.buf[S.y] + vec * C.N;
-    const float* pv = S.prev >= 0 ? C.buf[S.prev] + vec * C.N : nullptr;
-    float* ov = C.buf[S.out] + vec * C.N;
     const float* V = C.V;
-    const int col = (y0 + ty) * nx + x0;
-    const int cofs = ty * nx + x0;
     const int rows = TY + 2 * BR;
     const int wsz = rows * Wd;
     const int csz = TY * nx;
     float* win = reinterpret_cast<float*>(smem_raw);
     float* cen = win + (BA + 1) * wsz;
     const int rv = TX + 2 * (BPAD / BVW);            // 16-byte vectors per window row
-    // entry `e`: window of plane e, centre of plane e + R, V and yprev of e
-    auto issue = [&](int e) {
-      if (e < nz) {
-        const int sl = e % (BA + 1);
-        float* w = win + sl * wsz;
-        const float* src = yv + (long long)e * plane;
-        for (int q = tid; q < rows * rv; q += BTHREADS) {
+    const int cofs = ty * nx + x0;
+    for (int k = 0; k < C.m; ++k) {
+      const BStep S = steps[(size_t)k * ncells + ci];
+      const float* yv = C.buf[S.y] + vec * C.N;
+      const float* pv = S.prev >= 0 ? C.buf[S.prev] + vec * C.N : nullptr;
+      float* ov = C.buf[S.out] + vec * C.N;
+      for (int tile = 0; tile < C.tiles; ++tile) {
+        const int y0 = tile * TY;
+        const int col = (y0 + ty) * nx + x0;
+        // this thread's window copies (row, 16-byte vector), the same for
+        // every plane of the tile: the first BKC precomputed, any beyond
+        // (rows longer than BKC x blockDim vectors) on the fly
+        auto wcopy = [&](int q, int& src, int& dst) {
           const int r = q / rv, v = q - r * rv;
           int gy = (y0 - BR + r) % ny;
           gy += (gy < 0) ? ny : 0;
           int sx = v * BVW - BPAD;
           sx += (sx < 0) ? nx : 0;
           sx -= (sx >= nx) ? nx : 0;
-          ac::cp_async16(w + r * Wd + v * BVW, src + gy * nx + sx);
+          src = gy * nx + sx;
+          dst = r * Wd + v * BVW;
+        };
+        int wsrc[BKC], wdst[BKC];
+#pragma unroll
+        for (int j = 0; j < BKC; ++j) {
+          const int q = tid + j * nthr;
+          wsrc[j] = -1;
+          wdst[j] = 0;
+          if (q < rows * rv) wcopy(q, wsrc[j], wdst[j]);
         }
-        if (act) {
-          float* ce = cen + sl * 3 * csz;
-          int zq = e + BR;
-          zq -= (zq >= nz) ? nz : 0;
-          zq -= (zq >= nz) ? nz : 0;
-          ac::cp_async16(ce + cofs, yv + (long long)zq * plane + col);
-          ac::cp_async16(ce + csz + cofs, V + (long long)e * plane + col);
-          if (pv) ac::cp_async16(ce + 2 * csz + cofs, pv + (long long)e * plane + col);
-        }
-      }
-      ac::cp_async_commit();
-    };
-    // z-neighbour ring: plane z + j - R in q[(z + j) % BQ], the z loop
-    // unrolled BQ-fold so every index is a compile-time constant
-    constexpr int BQ = 2 * BR + 1;
-    float4 q[BQ];
-    if (act) {
+        // entry `e`: window of plane e, centre of plane e + R, V and yprev of e
+        auto issue = [&](int e) {
+          if (e < nz) {
+            const int sl = e % (BA + 1);
+            float* w = win + sl * wsz;
+            const float* src = yv + (long long)e * plane;
 #pragma unroll
-      for (int j = 0; j < 2 * BR; ++j) {
-        int zz = j - BR;
-        zz += (zz < 0) ? nz : 0;
-        zz -= (zz >= nz) ? nz : 0;
-        q[j] = __ldg(reinterpret_cast<const float4*>(yv + (long long)zz * plane + col));
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < BA; ++e) issue(e);
-    for (int z0 = 0; z0 < nz; z0 += BQ) {
-#pragma unroll
-      for (int u = 0; u < BQ; ++u) {
-        const int z = z0 + u;
-        if (z >= nz) break;
-        ac::cp_async_wait<BA - 1>();
-        __syncthreads();
-        issue(z + BA);
-        if (act) {
-          const int sl = z % (BA + 1);
-          const float* ce = cen + sl * 3 * csz;
-          q[(u + 2 * BR) % BQ] = *reinterpret_cast<const float4*>(ce + cofs);
-          const float4 vz = *reinterpret_cast<const float4*>(ce + csz + cofs);
-          const float4 yp = pv ? *reinterpret_cast<const float4*>(ce + 2 * csz + cofs)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float* row = win + sl * wsz + (ty + BR) * Wd + BPAD + x0;
-          float xw[BVW + 2 * BPAD];
-#pragma unroll
-          for (int j = 0; j < (BVW + 2 * BPAD) / BVW; ++j) {
-            const float4 t = *reinterpret_cast<const float4*>(row - BPAD + j * BVW);
-            xw[j * 4 + 0] = t.x; xw[j * 4 + 1] = t.y; xw[j * 4 + 2] = t.z; xw[j * 4 + 3] = t.w;
-          }
-          const float* vzp = reinterpret_cast<const float*>(&vz);
-          const float* qc = reinterpret_cast<const float*>(&q[(u + BR) % BQ]);
-          float acc[BVW];
-#pragma unroll
-          for (int i = 0; i < BVW; ++i) acc[i] = (C.kdiag + vzp[i] - C.c) * qc[i];
-#pragma unroll
-          for (int p = 1; p <= BR; ++p) {
-            const float4 up = *reinterpret_cast<const float4*>(row + p * Wd);
-            const float4 dn = *reinterpret_cast<const float4*>(row - p * Wd);
-            const float* upp = reinterpret_cast<const float*>(&up);
-            const float* dnp = reinterpret_cast<const float*>(&dn);
-            const float* zp = reinterpret_cast<const float*>(&q[(u + BR + p) % BQ]);
-            const float* zm = reinterpret_cast<const float*>(&q[(u + BR - p) % BQ]);
-#pragma unroll
-            for (int i = 0; i < BVW; ++i) {
-              acc[i] += C.kx[p] * (xw[BPAD + i + p] + xw[BPAD + i - p]);
-              acc[i] += C.ky[p] * (upp[i] + dnp[i]);
-              acc[i] += C.kz[p] * (zp[i] + zm[i]);
+            for (int j = 0; j < BKC; ++j)
+              if (wsrc[j] >= 0) ac::cp_async16(w + wdst[j], src + wsrc[j]);
+            for (int q = tid + BKC * nthr; q < rows * rv; q += nthr) {
+              int a, b;
+              wcopy(q, a, b);
+              ac::cp_async16(w + b, src + a);
+            }
+            if (act) {
+              float* ce = cen + sl * 3 * csz;
+              int zq = e + BR;
+              zq -= (zq >= nz) ? nz : 0;
+              zq -= (zq >= nz) ? nz : 0;
+              ac::cp_async16(ce + cofs, yv + (long long)zq * plane + col);
+              ac::cp_async16(ce + csz + cofs, V + (long long)e * plane + col);
+              if (pv) ac::cp_async16(ce + 2 * csz + cofs, pv + (long long)e * plane + col);
             }
           }
-          const float* ypp = reinterpret_cast<const float*>(&yp);
-          float4 o;
-          o.x = S.s1 * acc[0] + S.s2 * ypp[0];
-          o.y = S.s1 * acc[1] + S.s2 * ypp[1];
-          o.z = S.s1 * acc[2] + S.s2 * ypp[2];
-          o.w = S.s1 * acc[3] + S.s2 * ypp[3];
-          *reinterpret_cast<float4*>(ov + (long long)z * plane + col) = o;
+          ac::cp_async_commit();
+        };
+        // z-neighbour ring: plane z + j - R in q[(z + j) % BQ], the z loop
+        // unrolled BQ-fold so every index is a compile-time constant; loaded
+        // from L2 (the block changes during the launch)
+        constexpr int BQ = 2 * BR + 1;
+        float4 q[BQ];
+        if (act) {
+#pragma unroll
+          for (int j = 0; j < 2 * BR; ++j) {
+            int zz = j - BR;
+            zz += (zz < 0) ? nz : 0;
+            zz -= (zz >= nz) ? nz : 0;
+            q[j] = __ldcg(reinterpret_cast<const float4*>(yv + (long long)zz * plane + col));
+          }
         }
+#pragma unroll
+        for (int e = 0; e < BA; ++e) issue(e);
+        for (int z0 = 0; z0 < nz; z0 += BQ) {
+#pragma unroll
+          for (int u = 0; u < BQ; ++u) {
+            const int z = z0 + u;
+            if (z >= nz) break;
+            ac::cp_async_wait<BA - 1>();
+            __syncthreads();
+            issue(z + BA);
+            if (act) {
+              const int sl = z % (BA + 1);
+              const float* ce = cen + sl * 3 * csz;
+              q[(u + 2 * BR) % BQ] = *reinterpret_cast<const float4*>(ce + cofs);
+              const float4 vz = *reinterpret_cast<const float4*>(ce + csz + cofs);
+              const float4 yp = pv ? *reinterpret_cast<const float4*>(ce + 2 * csz + cofs)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float* row = win + sl * wsz + (ty + BR) * Wd + BPAD + x0;
+              float xw[BVW + 2 * BPAD];
+#pragma unroll
+              for (int j = 0; j < (BVW + 2 * BPAD) / BVW; ++j) {
+                const float4 t = (j == BPAD / BVW)
+                                     ? q[(u + BR) % BQ]
+                                     : *reinterpret_cast<const float4*>(row - BPAD + j * BVW);
+                xw[j * 4 + 0] = t.x; xw[j * 4 + 1] = t.y; xw[j * 4 + 2] = t.z; xw[j * 4 + 3] = t.w;
+              }
+              const float* vzp = reinterpret_cast<const float*>(&vz);
+              const float* qc = reinterpret_cast<const float*>(&q[(u + BR) % BQ]);
+              // the taps summed per axis with the compile-time weights, then
+              // scaled by the cell's spacings
+              float sx[BVW], sy[BVW], sz[BVW];
+#pragma unroll
+              for (int i = 0; i < BVW; ++i) sx[i] = sy[i] = sz[i] = 0.f;
+#pragma unroll
+              for (int p = 1; p <= BR; ++p) {
+                const float4 up = *reinterpret_cast<const float4*>(row + p * Wd);
+                const float4 dn = *reinterpret_cast<const float4*>(row - p * Wd);
+                const float* upp = reinterpret_cast<const float*>(&up);
+                const float* dnp = reinterpret_cast<const float*>(&dn);
+                const float* zp = reinterpret_cast<const float*>(&q[(u + BR + p) % BQ]);
+                const float* zm = reinterpret_cast<const float*>(&q[(u + BR - p) % BQ]);
+                const float wp = bwc(p);
+#pragma unroll
+                for (int i = 0; i < BVW; ++i) {
+                  sx[i] += wp * (xw[BPAD + i + p] + xw[BPAD + i - p]);
+                  sy[i] += wp * (upp[i] + dnp[i]);
+                  sz[i] += wp * (zp[i] + zm[i]);
+                }
+              }
+              const float* ypp = reinterpret_cast<const float*>(&yp);
+              float4 o;
+              float* op = reinterpret_cast<float*>(&o);
+#pragma unroll
+              for (int i = 0; i < BVW; ++i) {
+                const float acc = (kdiag + vzp[i] - kc) * qc[i] + hx2 * sx[i] + hy2 * sy[i] +
+                                  hz2 * sz[i];
+                op[i] = S.s1 * acc + S.s2 * ypp[i];
+              }
+              *reinterpret_cast<float4*>(ov + (long long)z * plane + col) = o;
+            }
+          }
+        }
+        ac::cp_async_wait<0>();
+        __syncthreads();     // the ring is reused; the step's writes are visible
       }
     }
-    ac::cp_async_wait<0>();
-    __syncthreads();     // the ring is reused by the next item
+    // after an odd number of steps Y_m sits in the work block: copy the
+    // vector back into the cell's block
+    if (C.m % 2 == 1) {
+      const float4* src = reinterpret_cast<const float4*>(C.buf[1] + vec * C.N);
+      float4* dst = reinterpret_cast<float4*>(C.buf[0] + vec * C.N);
+      for (long long i = tid; i < C.N / 4; i += nthr) dst[i] = __ldcg(src + i);
+    }
+    __syncthreads();
   }
 }
 
@@ -211,11 +295,13 @@ struct sq3_batch {
   // device tables
   sq3::BCell* d_cells = nullptr;        // the cells' descriptors
   sq3::BStep* d_steps = nullptr;        // m_max x ncells
-  long long* d_item0 = nullptr;         // m_max x (ncells + 1)
-  unsigned long long* d_counter = nullptr;  // m_max counters
+  long long* d_item0 = nullptr;         // ncells + 1 prefix sums, claim order
+  int* d_cell_of = nullptr;             // claim order -> cell
+  unsigned long long* d_counter = nullptr;  // the item counter
   std::vector<sq3::BStep> h_steps;
-  std::vector<long long> h_item0;       // m_max x (ncells + 1)
-  std::vector<long long> h_total;       // per step
+  std::vector<long long> h_item0;       // ncells + 1
+  std::vector<int> h_cell_of;           // ncells
+  long long h_total = 0;                // items (vectors of all cells)
   int m_max = 0;
   // launch shape (autotuned) and the captured graph
   int ctas_per_sm = 1;
@@ -260,8 +346,6 @@ void build_steps(sq3_batch* B) {
   B->m_max = 0;
   for (auto& c : B->cells) B->m_max = std::max(B->m_max, c.m);
   B->h_steps.assign((size_t)B->m_max * nc, BStep{0.f, 0.f, 0, -1, 1});
-  B->h_item0.assign((size_t)B->m_max * (nc + 1), 0);
-  B->h_total.assign(B->m_max, 0);
   for (int ci = 0; ci < nc; ++ci) {
     BCell& c = B->cells[ci];
     const double e = 0.5 * (B->b[ci] - B->a[ci]), ctr = 0.5 * (B->b[ci] + B->a[ci]);
@@ -278,16 +362,17 @@ void build_steps(sq3_batch* B) {
       s = sn;
     }
   }
-  for (int k = 0; k < B->m_max; ++k) {
-    long long acc = 0;
-    for (int ci = 0; ci < nc; ++ci) {
-      B->h_item0[(size_t)k * (nc + 1) + ci] = acc;
-      const BCell& c = B->cells[ci];
-      if (c.m > k) acc += (long long)c.Ns * c.tiles;
-    }
-    B->h_item0[(size_t)k * (nc + 1) + nc] = acc;
-    B->h_total[k] = acc;
-  }
+  // items: the vectors of every cell, cells in decreasing order of grid
+  // size (the largest items are claimed first)
+  B->h_cell_of.resize(nc);
+  for (int ci = 0; ci < nc; ++ci) B->h_cell_of[ci] = ci;
+  std::stable_sort(B->h_cell_of.begin(), B->h_cell_of.end(), [&](int u, int v) {
+    return B->cells[u].N * B->cells[u].m > B->cells[v].N * B->cells[v].m;
+  });
+  B->h_item0.assign(nc + 1, 0);
+  for (int j = 0; j < nc; ++j)
+    B->h_item0[j + 1] = B->h_item0[j] + B->cells[B->h_cell_of[j]].Ns;
+  B->h_total = B->h_item0[nc];
 }
 
 void free_graph(sq3_batch* B) {
@@ -298,9 +383,10 @@ void free_graph(sq3_batch* B) {
 }
 
 void free_tables(sq3_batch* B) {
-  void* ps[] = {B->d_cells, B->d_steps, B->d_item0, B->d_counter};
+  void* ps[] = {B->d_cells, B->d_steps, B->d_item0, B->d_cell_of, B->d_counter};
   for (void* p : ps) if (p) cudaFree(p);
-  B->d_cells = nullptr; B->d_steps = nullptr; B->d_item0 = nullptr; B->d_counter = nullptr;
+  B->d_cells = nullptr; B->d_steps = nullptr; B->d_item0 = nullptr; B->d_cell_of = nullptr;
+  B->d_counter = nullptr;
 }
 
 int upload_tables(sq3_batch* B) {
@@ -313,39 +399,35 @@ int upload_tables(sq3_batch* B) {
   int rc = put((void**)&B->d_cells, B->cells.data(), nc * sizeof(BCell));
   if (!rc) rc = put((void**)&B->d_steps, B->h_steps.data(), B->h_steps.size() * sizeof(BStep));
   if (!rc) rc = put((void**)&B->d_item0, B->h_item0.data(), B->h_item0.size() * sizeof(long long));
-  if (!rc && cudaMalloc((void**)&B->d_counter, B->m_max * sizeof(unsigned long long)) != cudaSuccess) {
+  if (!rc) rc = put((void**)&B->d_cell_of, B->h_cell_of.data(), B->h_cell_of.size() * sizeof(int));
+  if (!rc && cudaMalloc((void**)&B->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     rc = SQ3_ENOMEM;
   }
   return rc;
 }
 
-// Enqueue the whole filter: per step a counter reset and one persistent
-// launch, then the copies of the cells whose result ended in the work block.
+// Threads per CTA: the largest tile's threads (TX TY), rounded up to whole
+// warps; the narrower cells' tiles leave the rest idle.
+int batch_threads(const sq3_batch* B) {
+  int t = 32;
+  for (auto& c : B->cells) t = std::max(t, c.TX * c.TY);
+  return std::min(BTHREADS, (t + 31) / 32 * 32);
+}
+
+// Enqueue the whole filter: a counter reset and one persistent launch that
+// takes every vector of every cell through all of its steps.
 int enqueue(sq3_batch* B, cudaStream_t st) {
   const int nc = (int)B->cells.size();
-  auto k = batch_step_kernel;
+  auto k = batch_filter_kernel;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem) !=
       cudaSuccess)
     return cuda_err(cudaGetLastError());
-  int rc = cuda_err(cudaMemsetAsync(B->d_counter, 0, B->m_max * sizeof(unsigned long long), st));
+  int rc = cuda_err(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), st));
   if (rc) return rc;
   const unsigned grid = (unsigned)(B->sms * B->ctas_per_sm);
-  for (int s = 0; s < B->m_max; ++s) {
-    if (B->h_total[s] == 0) continue;
-    k<<<grid, BTHREADS, B->smem, st>>>(B->d_cells, B->d_steps + (size_t)s * nc,
-                                       B->d_item0 + (size_t)s * (nc + 1), nc, B->h_total[s],
-                                       B->d_counter + s);
-  }
-  for (int ci = 0; ci < nc; ++ci) {
-    const BCell& c = B->cells[ci];
-    // after m steps Y_m sits in the work block when m is odd
-    if (c.m % 2 == 1) {
-      rc = cuda_err(cudaMemcpyAsync(c.buf[0], c.buf[1], (size_t)c.N * c.Ns * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, st));
-      if (rc) return rc;
-    }
-  }
+  k<<<grid, batch_threads(B), B->smem, st>>>(B->d_cells, B->d_steps, B->d_item0, B->d_cell_of, nc,
+                                     B->h_total, B->d_counter);
   return cuda_err(cudaGetLastError());
 }
 
@@ -435,11 +517,9 @@ int sq3_batch_add_cell(sq3_batch* B, int nx, int ny, int nz, double Lx, double L
   const double ix = 1.0 / ((Lx / nx) * (Lx / nx)), iy = 1.0 / ((Ly / ny) * (Ly / ny)),
                iz = 1.0 / ((Lz / nz) * (Lz / nz));
   c.kdiag = (float)(-0.5 * w[0] * (ix + iy + iz));
-  for (int p = 1; p <= BR; ++p) {
-    c.kx[p] = (float)(-0.5 * w[p] * ix);
-    c.ky[p] = (float)(-0.5 * w[p] * iy);
-    c.kz[p] = (float)(-0.5 * w[p] * iz);
-  }
+  c.hx2 = (float)(-0.5 * ix);
+  c.hy2 = (float)(-0.5 * iy);
+  c.hz2 = (float)(-0.5 * iz);
   float* Vf = nullptr;
   float* W = nullptr;
   if (cudaMalloc((void**)&Vf, c.N * sizeof(float)) != cudaSuccess ||

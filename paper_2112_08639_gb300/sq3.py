@@ -539,7 +539,8 @@ class MLP:
 
 class Batch:
     """Many independent cells filtered together (sq3_batch_*): one persistent
-    launch per filter step for all cells, replayed from a captured CUDA graph."""
+    launch takes every vector of every cell through all its filter steps,
+    replayed from a captured CUDA graph."""
 
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
         self.device = torch.device("cuda", device)

@@ -2,11 +2,13 @@
 FP32 filter of the same library (sq3_cheb_filter, SQ3_MIXED, no
 projectors) and against the oracle's filter by its plain definition.
 
-The batched launch computes each cell with the same FP32 arithmetic in the
-same order as the single-cell ring stencil, so the two agree to FP32
-rounding of the whole filter (1e-6 of the block's largest value); against
-the FP64 oracle the FP32 filter of degree <= 12 stays within 1e-5 relative
-(L2).  Cells of different grids (cubic and not), numbers of vectors and
+The batched launch computes each cell with the single-cell ring stencil's
+tiling in FP32; its taps are summed per axis with the weights as constants
+and scaled by the spacings afterwards (the single-cell step multiplies each
+tap by its own rounded coefficient), so the two agree to FP32 rounding of
+the whole filter: 1e-5 of the block's largest value after up to 12 steps
+(a few ulps per step, carried along by the recurrence).  Against the FP64
+oracle the FP32 filter of degree <= 12 stays within 1e-5 relative (L2).  Cells of different grids (cubic and not), numbers of vectors and
 degrees share the launches; the autotuner keeps the results unchanged."""
 import numpy as np
 import pytest
@@ -77,7 +79,7 @@ def test_batched_filter_matches_single_cell_filter_and_oracle():
     batch.filter()
     for Xb, (Xs, X0, V, n, L, deg, (a, b, a0)) in zip(blocks, refs):
         got = Xb.cpu().numpy()
-        assert np.max(np.abs(got - Xs)) <= 1e-6 * np.max(np.abs(Xs))
+        assert np.max(np.abs(got - Xs)) <= 1e-5 * np.max(np.abs(Xs))
     # the cubic cell against the oracle's plain filter in FP64
     Xs, X0, V, n, L, deg, (a, b, a0) = refs[0]
     parts = hamiltonian.hamiltonian_sparse(n[0], L[0], V)
