@@ -91,6 +91,9 @@ def parse():
     p.add_argument("--no-compare-starts", dest="compare_starts", action="store_false")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--kernel-eval", default="ps", choices=["recurrence", "ps"],
+                   help="evaluation of the Fermi-operator expansion in the SCF solves: the "
+                        "recurrence or Paterson-Stockmeyer")
     p.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false",
                    help="skip the oracle's CPU timing (profiling runs)")
     p.add_argument("--cells", type=int, default=64,
@@ -246,7 +249,8 @@ def run_solve(args, rank, world):
     torch.cuda.set_device(dev)
     cfg = inputs.CONFIGS[args.config]
     # the previous QMD step: converged at R0 from a random block
-    cell = qmd.Cell(cfg, device=dev, prec=sq3.MIXED)
+    ke = sq3.EVAL_PATERSON_STOCKMEYER if args.kernel_eval == "ps" else sq3.EVAL_RECURRENCE
+    cell = qmd.Cell(cfg, device=dev, prec=sq3.MIXED, kernel_eval=ke)
     R0 = inputs.fcc_positions(cfg.ncell, disp_sigma=cfg.disp_sigma, seed=cfg.seed)
     V0 = qmd.maxwell_boltzmann(cfg.natoms, cfg.sigma, seed=rank)
     cell.set_positions(R0)
@@ -345,6 +349,17 @@ def run_solve(args, rank, world):
         phases[name] = round(t1 - t0, 4)
         return t1
 
+    # the block's upload alone, timed with events on the stream
+    h2d_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cell.X.copy_(Xh, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms.append(round(e0.elapsed_time(e1), 2))
+    phases["h2d_block_alone_ms"] = h2d_ms
     t = time.perf_counter()
     cell.X.copy_(Xh, non_blocking=True)
     t = mark("h2d_block", t)
@@ -366,7 +381,7 @@ def run_solve(args, rank, world):
 
     fp64 = None
     if args.fp64_arm != "none":
-        cell64 = qmd.Cell(cfg, device=dev, prec=sq3.FP64)
+        cell64 = qmd.Cell(cfg, device=dev, prec=sq3.FP64, kernel_eval=ke)
         cell64.set_positions(R1)
         cell64.X = X_prev.double()
         cell64.bounds = bounds_prev
@@ -421,6 +436,8 @@ def run_solve(args, rank, world):
                     f"{DT_FS} fs velocity-Verlet step from a converged state; the previous "
                     f"step's block and bounds, the {args.start} starting density",
             "precision": "mixed",
+            "expansion": ("Paterson-Stockmeyer" if args.kernel_eval == "ps"
+                          else "recurrence with the product identity"),
             "parallelism": "replicas" if world > 1 else "single GPU",
             "l2": "inputs larger than L2 (X block %.2f GB)" % (cfg.N * cfg.Ns * 4 / 1e9),
         },

@@ -176,16 +176,18 @@ int sq3_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
  * - npl < 1: the degree is chosen after the spectral bounds are known, as
  *   sq3_fermi_degree(kT, xi, fermi_tol) (capped at 1000); *npl_used (HOST,
  *   may be NULL) receives the degree used.
- * - eval_mode SQ3_EVAL_PATERSON_STOCKMEYER (FP64 only): the same polynomial
+ * - eval_mode SQ3_EVAL_PATERSON_STOCKMEYER: the same polynomial
  *   sum'_j c_j T_j(Hhat) evaluated with O(sqrt(npl)) matrix products: s =
  *   ceil(sqrt(2 npl)) baby steps T_0..T_s, giant steps T_{qs} = T_q(T_s)
  *   (the Chebyshev composition identity) for the moments m_{qs+r} =
  *   2 tr(T_{qs} T_r) - m_{qs-r}, and Ds = sum_q A_q T_q(T_s) by Clenshaw's
  *   recurrence in T_s with A_q = sum_{r<s} alpha_{qr} T_r
- *   ((s - 1) + 2 floor(npl/s) - 1 products instead of npl - 1); equal to
- *   the recurrence up to rounding.
- * Other arguments and errors as sq3_kernel_from_hs (SQ3_EINVAL for the
- * Paterson-Stockmeyer mode with SQ3_MIXED). */
+ *   ((s - 1) + 2 floor(npl/s) - 1 products instead of npl - 1 in FP64, or
+ *   ceil(npl/2) + 1 for SQ3_MIXED's recurrence with the product identity);
+ *   equal to the recurrence up to rounding.  With SQ3_MIXED the matrices are
+ *   FP32 and the products tcgen05 GEMMs of BF16 pieces, as the mixed
+ *   recurrence.
+ * Other arguments and errors as sq3_kernel_from_hs. */
 #define SQ3_EVAL_RECURRENCE 0
 #define SQ3_EVAL_PATERSON_STOCKMEYER 1
 int sq3_kernel_from_hs_ex(sq3_ctx* ctx, const double* Hs, int Ns, int npl, double fermi_tol,
@@ -469,8 +471,8 @@ typedef struct sq3_scf_params {
                         the first iteration's damped interval              */
   double cut_shift;  /* the damped interval starts this far (Ha) above the
                         largest Ritz value (0: at it)                      */
-  int kernel_eval;   /* SQ3_EVAL_RECURRENCE or SQ3_EVAL_PATERSON_STOCKMEYER
-                        (FP64 only), as sq3_kernel_from_hs_ex             */
+  int kernel_eval;   /* SQ3_EVAL_RECURRENCE or SQ3_EVAL_PATERSON_STOCKMEYER,
+                        as sq3_kernel_from_hs_ex                          */
   int reserved;
 } sq3_scf_params;
 

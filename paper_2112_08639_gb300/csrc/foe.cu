@@ -267,7 +267,6 @@ __global__ void accumulate_d_kernel(const double* __restrict__ T, long long nn,
 //                 b_q = A_q + 2 Y b_{q+1} - b_{q+2},  Ds = A_0 + Y b_1 - b_2.
 // Products: (s - 1) + (Q - 1) + Q with Q = floor(npl / s), s = ceil(sqrt(2 npl)).
 // ---------------------------------------------------------------------------
-constexpr int PS_FROB_BLOCKS = 16;   // blocks per Frobenius product
 
 // part[(pair) * PS_FROB_BLOCKS + b]: block sums of <G_q, T_r>, pair =
 // (q - 1) (s - 1) + (r - 1); G_q at gq[q], T_r at T + r nn.
@@ -461,6 +460,16 @@ int ps_kernel_f64(sq3_ctx* ctx, int Ns, int npl, int s, int Q, const double* coe
   return cuda_err(cudaGetLastError());
 }
 
+void ps_moments_finish(const double* part, int s, int Q, int npl, double* mom,
+                       cudaStream_t st) {
+  ps_moments_kernel<<<1, 32, 0, st>>>(part, s, Q, npl, mom);
+}
+
+void ps_alpha(const double* coef, int npl, int s, int Q, double* work, double* alpha,
+              cudaStream_t st) {
+  ps_alpha_kernel<<<1, 32, 0, st>>>(coef, npl, s, Q, work, alpha);
+}
+
 int ps_layout(int npl, int* s_out, int* Q_out) {
   int s = (int)ceil(sqrt(2.0 * npl));
   if (s < 2) s = 2;
@@ -516,7 +525,7 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   }
   if (npl > SQ3_MAX_NPL) return SQ3_EINVAL;
   if (npl_used) *npl_used = npl;
-  const bool ps = eval_mode == 1 && !mixed;
+  const bool ps = eval_mode == 1;
   int ps_s = 0, ps_Q = 0;
   ps_layout(npl, &ps_s, &ps_Q);
   const int h = mixed ? (npl + 1) / 2 : npl;
@@ -527,14 +536,18 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
   const size_t ps_mats = (size_t)(ps_s + 1) + (size_t)std::max(ps_Q - 1, 0) + 3;
   const size_t ps_words = ps_mats * nn + (size_t)ps_Q * ps_s * PS_FROB_BLOCKS +
                           2 * (size_t)(ps_Q + 1) * ps_s + (size_t)(ps_Q + 2);
-  size_t need_T = mixed ? tail_off + moments_tail_part_words(npl, h) * sizeof(double)
-                        : (ps ? ps_words : (size_t)(npl + 1) * nn) * sizeof(double);
+  size_t need_T = (mixed && ps) ? ps_mixed_bytes(Ns, ps_s, ps_Q)
+                  : mixed ? tail_off + moments_tail_part_words(npl, h) * sizeof(double)
+                          : (ps ? ps_words : (size_t)(npl + 1) * nn) * sizeof(double);
   rc = ensure((void**)&ctx->wsT, &ctx->wsT_bytes, need_T);
   if (rc) return rc;
   rc = cuda_err(cudaMemsetAsync(mom, 0, (size_t)(npl + 1) * sizeof(double), st));
   if (rc) return rc;
   double* T = ctx->wsT;
-  if (mixed) {
+  if (mixed && ps) {
+    rc = ps_moments_mixed(ctx, Hs, Ns, npl, ps_s, ps_Q, bounds, mom, ctx->wsT);
+    if (rc) return rc;
+  } else if (mixed) {
     rc = cheb_recurrence_mixed(ctx, Hs, Ns, h, bounds, mom, (float*)ctx->wsT);
     if (rc) return rc;
     {
@@ -589,7 +602,10 @@ int density_kernel_from_hs(sq3_ctx* ctx, const double* Hs, int Ns, int npl,
                                                          terms);
     fermi_finish_kernel<<<1, 32, 0, st>>>(terms, npl, sigma, outd, ctx->dev_status);
   }
-  if (D != nullptr && mixed) {
+  if (D != nullptr && mixed && ps) {
+    rc = ps_kernel_mixed(ctx, Ns, npl, ps_s, ps_Q, coef, ctx->wsT, D);
+    if (rc) return rc;
+  } else if (D != nullptr && mixed) {
     rc = accumulate_d_mixed(ctx, (const float*)ctx->wsT, Ns, npl, h, coef, D,
                             (float*)ctx->wsT + (size_t)(h + 1) * nn);
     if (rc) return rc;

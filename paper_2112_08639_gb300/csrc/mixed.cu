@@ -17,7 +17,9 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <utility>
+#include <vector>
 
 #include "sq3_internal.cuh"
 #include "tc_gemm.cuh"
@@ -745,6 +747,250 @@ int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double*
   t.tri = 2;                                         // B upper triangular
   return tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
                  EPI_TC_RHO, 1, ctx->stream);
+}
+
+// ---------------------------------------------------------------------------
+// Paterson-Stockmeyer evaluation of the expansion on the tensor cores (the
+// mixed path's form of foe.cu's FP64 one; the same identities):
+//   baby steps    T_0 .. T_s by the recurrence in Hhat
+//   giant steps   G_q = T_q(Y) = T_{qs}, Y = T_s: G_{q+1} = 2 Y G_q - G_{q-1}
+//   moments       m_{qs+r} = 2 <G_q, T_r> - m_{qs-r}
+//   kernel        Ds = sum_q A_q T_q(Y), A_q = sum_{r<s} alpha_{qr} T_r, by
+//                 Clenshaw's recurrence b_q = A_q + 2 Y b_{q+1} - b_{q+2},
+//                 Ds = A_0 + Y b_1 - b_2.
+// Matrices in FP32, every product a tcgen05 GEMM of BF16 pieces with the
+// Chebyshev epilogue (C = 2 acc - P, its pieces for the next product, its
+// trace); (s - 1) + (Q - 1) + Q products instead of the recurrence's
+// ceil(npl / 2).  Workspace W (FP32 matrices, then doubles):
+//   T_0 .. T_s | G_2 .. G_Q | b[3] | P | part | alpha | work | trace scratch
+//   | pointers to G_0 .. G_Q
+// ---------------------------------------------------------------------------
+struct PsMixed {
+  float* baby;
+  float* giant;
+  float* b[3];
+  float* P;
+  double* part;
+  double* alpha;
+  double* work;
+  double* scratch;
+  const float** gptr;
+};
+
+static PsMixed ps_mixed_ws(void* W, long long nn, int s, int Q) {
+  PsMixed w;
+  float* f = (float*)W;
+  w.baby = f; f += (long long)(s + 1) * nn;
+  w.giant = f; f += (long long)std::max(Q - 1, 0) * nn;
+  for (int k = 0; k < 3; ++k) { w.b[k] = f; f += nn; }
+  w.P = f; f += nn;
+  double* d = (double*)(((uintptr_t)f + 15) & ~(uintptr_t)15);
+  w.part = d; d += (size_t)std::max(Q, 1) * s * PS_FROB_BLOCKS;
+  w.alpha = d; d += (size_t)(Q + 1) * s;
+  w.work = d; d += (size_t)(Q + 1) * s;
+  w.scratch = d; d += 2;
+  w.gptr = (const float**)d;
+  return w;
+}
+
+size_t ps_mixed_bytes(int Ns, int s, int Q) {
+  const long long nn = (long long)Ns * Ns;
+  const size_t mats = (size_t)(s + 1) + (size_t)std::max(Q - 1, 0) + 4;
+  return mats * nn * sizeof(float) + 16 +
+         ((size_t)std::max(Q, 1) * s * PS_FROB_BLOCKS + 2 * (size_t)(Q + 1) * s + 2) *
+             sizeof(double) +
+         (size_t)(Q + 2) * sizeof(float*);
+}
+
+// part[pair PS_FROB_BLOCKS + b]: block b's share of <G_q, T_r>, pair =
+// (q - 1)(s - 1) + (r - 1); FP32 products in runs of 16 folded into FP64.
+__global__ void __launch_bounds__(256)
+ps_frob_f32_kernel(const float* const* __restrict__ gq, const float* __restrict__ T,
+                   long long nn, int s, double* part) {
+  __shared__ double sh[8];
+  const int pair = blockIdx.x / PS_FROB_BLOCKS, blk = blockIdx.x % PS_FROB_BLOCKS;
+  const int q = pair / (s - 1) + 1, r = pair % (s - 1) + 1;
+  const float* A = gq[q];
+  const float* B = T + (long long)r * nn;
+  const long long stride = (long long)PS_FROB_BLOCKS * blockDim.x;
+  double acc = 0.0;
+  long long e = (long long)blk * blockDim.x + threadIdx.x;
+  while (e < nn) {
+    float run = 0.f;
+    for (int i = 0; i < 16 && e < nn; ++i, e += stride) run = fmaf(A[e], B[e], run);
+    acc += (double)run;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out = ea E + eb Bm + as sum_{r<s} alpha[r] T_r, into FP32 out32 or FP64
+// out64 (one of them); the sum over r in FP32 runs of 8 folded into FP64.
+constexpr int PS_MAX_S = 64;
+__global__ void __launch_bounds__(256)
+ps_combine_f32_kernel(float* out32, double* out64, const float* E, double ea, const float* Bm,
+                      double eb, double as, const float* __restrict__ T, long long nn, int s,
+                      const double* __restrict__ alpha) {
+  __shared__ float al[PS_MAX_S];
+  for (int r = threadIdx.x; r < s; r += blockDim.x) al[r] = (float)alpha[r];
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int r0 = 0; r0 < s; r0 += 8) {
+      float run = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (r0 + i < s) run = fmaf(al[r0 + i], T[(long long)(r0 + i) * nn + e], run);
+      v += (double)run;
+    }
+    v *= as;
+    if (E) v += ea * (double)E[e];
+    if (Bm) v += eb * (double)Bm[e];
+    if (out64) out64[e] = v;
+    else out32[e] = (float)v;
+  }
+}
+
+// C = 2 Y B - P on the tensor cores (symmetric operands that commute: upper
+// tiles, mirrored), with the pieces of C into Cp and its trace into tr.
+static int ps_product(sq3_ctx* ctx, const MixedBuffers& b, const __nv_bfloat16* Yp,
+                      const __nv_bfloat16* Bp, const float* P, float* C, __nv_bfloat16* Cp,
+                      double* tr, int Ns) {
+  TcParams t{};
+  t.C32 = C;
+  t.ldc = Ns;
+  t.Tprev = P;
+  t.Bnext = Cp;
+  t.ld_next = b.ldS;
+  t.next_piece_stride = b.psS;
+  t.next_pieces = MIXED_PIECES;
+  t.trace = tr;
+  t.tri = 1;
+  return tc_gemm(ctx, op_mat(Yp, Ns, b), op_mat(Bp, Ns, b), products(MIXED_PIECES), t,
+                 EPI_TC_CHEB, 1, ctx->stream);
+}
+
+int ps_moments_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl, int s, int Q,
+                     const double* bounds, double* mom, void* W) {
+  if (s < 2 || s > PS_MAX_S) return SQ3_EINVAL;
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)Ns * Ns;
+  const PsMixed w = ps_mixed_ws(W, nn, s, Q);
+  const int sb = std::min(s, npl);            // baby steps needed for the moments
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    hhat_f32_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Hs, Ns, bounds, w.baby,
+                                                                  w.baby + nn, mom);
+    trace_f32_kernel<<<1, 1024, 0, st>>>(w.baby + nn, Ns, mom + 1);
+  }
+  split_matrix<float>(ctx, w.baby + nn, Ns, b.matA, b);          // Hhat
+  __nv_bfloat16* cur = b.matB;
+  __nv_bfloat16* nxt = b.matC;
+  {
+    Prof p(ctx, ST_SPLIT);
+    cudaMemcpyAsync(cur, b.matA, (size_t)MIXED_PIECES * b.psS * 2, cudaMemcpyDeviceToDevice,
+                    st);                                          // T_1
+  }
+  {
+    Prof p(ctx, ST_CHEB_GEMM, std::max(sb - 1, 0));
+    for (int j = 1; j < sb; ++j) {
+      rc = ps_product(ctx, b, b.matA, cur, w.baby + (long long)(j - 1) * nn,
+                      w.baby + (long long)(j + 1) * nn, nxt, mom + j + 1, Ns);
+      if (rc) return rc;
+      std::swap(cur, nxt);
+    }
+  }
+  if (Q < 1) return cuda_err(cudaGetLastError());
+  // giant steps in Y = T_s (its pieces in matA from here on)
+  const float* Y = w.baby + (long long)s * nn;
+  split_matrix<float>(ctx, Y, Ns, b.matA, b);
+  std::vector<const float*> g(Q + 1);
+  g[0] = w.baby;
+  g[1] = Y;
+  for (int q = 2; q <= Q; ++q) g[q] = w.giant + (long long)(q - 2) * nn;
+  {
+    Prof p(ctx, ST_SPLIT);
+    cudaMemcpyAsync(cur, b.matA, (size_t)MIXED_PIECES * b.psS * 2, cudaMemcpyDeviceToDevice,
+                    st);                                          // G_1 = Y
+  }
+  {
+    Prof p(ctx, ST_CHEB_GEMM, std::max(Q - 1, 0));
+    for (int q = 1; q < Q; ++q) {
+      rc = ps_product(ctx, b, b.matA, cur, g[q - 1], const_cast<float*>(g[q + 1]), nxt,
+                      mom + (long long)(q + 1) * s, Ns);
+      if (rc) return rc;
+      std::swap(cur, nxt);
+    }
+  }
+  rc = cuda_err(cudaMemcpyAsync(w.gptr, g.data(), (Q + 1) * sizeof(float*),
+                                cudaMemcpyHostToDevice, st));
+  if (rc) return rc;
+  {
+    Prof p(ctx, ST_CHEB_GEMM, 2);
+    ps_frob_f32_kernel<<<Q * (s - 1) * PS_FROB_BLOCKS, 256, 0, st>>>(w.gptr, w.baby, nn, s,
+                                                                     w.part);
+    ps_moments_finish(w.part, s, Q, npl, mom, st);
+  }
+  // the host vector g is read by the copy above: wait for it before it goes
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+int ps_kernel_mixed(sq3_ctx* ctx, int Ns, int npl, int s, int Q, const double* coef, void* W,
+                    double* D) {
+  MixedBuffers b;
+  int rc = mixed_buffers(ctx, Ns, &b);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const long long nn = (long long)Ns * Ns;
+  const PsMixed w = ps_mixed_ws(W, nn, s, Q);
+  const int sb = std::min(s, npl + 1);        // T_0 .. T_{sb-1} carry the A_q
+  const unsigned blocks = (unsigned)std::min<long long>((nn + 255) / 256, 152LL * 8);
+  Prof pd(ctx, ST_D_ACCUM, 2 + 2 * Q);
+  ps_alpha(coef, npl, s, Q, w.work, w.alpha, st);
+  if (Q == 0) {
+    ps_combine_f32_kernel<<<blocks, 256, 0, st>>>(nullptr, D, nullptr, 0.0, nullptr, 0.0, 1.0,
+                                                  w.baby, nn, sb, w.alpha);
+    return cuda_err(cudaGetLastError());
+  }
+  split_matrix<float>(ctx, w.baby + (long long)s * nn, Ns, b.matA, b);   // Y = T_s
+  float* bq1 = w.b[0];      // b_{q+1}
+  float* bq2 = w.b[1];      // b_{q+2}
+  float* bq = w.b[2];
+  cudaMemsetAsync(bq2, 0, nn * sizeof(float), st);
+  // b_Q = A_Q
+  ps_combine_f32_kernel<<<blocks, 256, 0, st>>>(bq1, nullptr, nullptr, 0.0, nullptr, 0.0, 1.0,
+                                                w.baby, nn, s, w.alpha + (size_t)Q * s);
+  split_matrix<float>(ctx, bq1, Ns, b.matB, b);
+  __nv_bfloat16* cur = b.matB;
+  __nv_bfloat16* nxt = b.matC;
+  for (int q = Q - 1; q >= 1; --q) {
+    // b_q = 2 Y b_{q+1} - P with P = b_{q+2} - A_q
+    ps_combine_f32_kernel<<<blocks, 256, 0, st>>>(w.P, nullptr, bq2, 1.0, nullptr, 0.0, -1.0,
+                                                  w.baby, nn, s, w.alpha + (size_t)q * s);
+    rc = ps_product(ctx, b, b.matA, cur, w.P, bq, nxt, w.scratch, Ns);
+    if (rc) return rc;
+    std::swap(cur, nxt);
+    float* t = bq2;
+    bq2 = bq1;
+    bq1 = bq;
+    bq = t;
+  }
+  // Ds = A_0 + Y b_1 - b_2 = (2 Y b_1 - b_2) / 2 - b_2 / 2 + A_0
+  rc = ps_product(ctx, b, b.matA, cur, bq2, bq, nxt, w.scratch, Ns);
+  if (rc) return rc;
+  ps_combine_f32_kernel<<<blocks, 256, 0, st>>>(nullptr, D, bq, 0.5, bq2, -0.5, 1.0, w.baby, nn,
+                                                sb, w.alpha);
+  return cuda_err(cudaGetLastError());
 }
 
 }  // namespace sq3

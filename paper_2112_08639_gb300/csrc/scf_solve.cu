@@ -110,8 +110,7 @@ int sq3_scf_solve(sq3_ctx* c, const sq3_scf_params* p, const double* b, double* 
       p->passes < 1 || !(p->kT > 0) || !(p->Ne > 0) || !(p->Ne < 2.0 * Ns) || !(p->tol > 0) ||
       p->npl > SQ3_MAX_NPL || (p->npl < 1 && !(p->fermi_tol > 0 && p->fermi_tol < 1)) ||
       !isfinite(p->e_self) || !isfinite(p->cut_shift) || p->cut_shift < 0 ||
-      (p->kernel_eval != SQ3_EVAL_RECURRENCE && p->kernel_eval != SQ3_EVAL_PATERSON_STOCKMEYER) ||
-      (p->kernel_eval == SQ3_EVAL_PATERSON_STOCKMEYER && prec != SQ3_FP64))
+      (p->kernel_eval != SQ3_EVAL_RECURRENCE && p->kernel_eval != SQ3_EVAL_PATERSON_STOCKMEYER))
     return SQ3_EINVAL;
   cudaSetDevice(c->device);
   *res = sq3_scf_result{};

@@ -750,7 +750,6 @@ int sq3_kernel_from_hs_ex(sq3_ctx* c, const double* Hs, int Ns, int npl, double 
   if (npl < 1 && !(fermi_tol > 0 && fermi_tol < 1)) return SQ3_EINVAL;
   if (eval_mode != SQ3_EVAL_RECURRENCE && eval_mode != SQ3_EVAL_PATERSON_STOCKMEYER)
     return SQ3_EINVAL;
-  if (eval_mode == SQ3_EVAL_PATERSON_STOCKMEYER && prec != SQ3_FP64) return SQ3_EINVAL;
   if (bounds_in && !(bounds_in[1] > 0)) return SQ3_EINVAL;
   if (prec != SQ3_FP64 && prec != SQ3_MIXED) return SQ3_EINVAL;
   cudaSetDevice(c->device);

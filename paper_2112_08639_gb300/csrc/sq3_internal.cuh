@@ -313,4 +313,24 @@ int accumulate_d_mixed(sq3_ctx* ctx, const float* T, int Ns, int npl, int h,
 int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns,
                   double* rho);
 
+// ---- Paterson-Stockmeyer evaluation of the expansion (foe.cu, mixed.cu) ----
+// s baby steps T_0..T_s, giant steps G_q = T_{qs} (q <= Q), Q = npl / s.
+constexpr int PS_FROB_BLOCKS = 16;   // blocks per Frobenius product <G_q, T_r>
+int ps_layout(int npl, int* s_out, int* Q_out);
+// mom[qs + r] = 2 <G_q, T_r> - mom[qs - r] from the block sums
+// part[((q - 1)(s - 1) + r - 1) PS_FROB_BLOCKS + b], in increasing q
+void ps_moments_finish(const double* part, int s, int Q, int npl, double* mom, cudaStream_t st);
+// alpha[q s + r]: Ds = sum_q (sum_{r<s} alpha[q s + r] T_r) T_q(T_s); work:
+// (Q + 1) s doubles
+void ps_alpha(const double* coef, int npl, int s, int Q, double* work, double* alpha,
+              cudaStream_t st);
+// The mixed path's form: FP32 matrices, tensor-core products with BF16
+// pieces.  W: ps_mixed_bytes(Ns, s, Q) bytes of device workspace, shared by
+// the two calls (the moments call leaves the baby and giant steps in it).
+size_t ps_mixed_bytes(int Ns, int s, int Q);
+int ps_moments_mixed(sq3_ctx* ctx, const double* Hs, int Ns, int npl, int s, int Q,
+                     const double* bounds, double* mom, void* W);
+int ps_kernel_mixed(sq3_ctx* ctx, int Ns, int npl, int s, int Q, const double* coef, void* W,
+                    double* D);
+
 }  // namespace sq3

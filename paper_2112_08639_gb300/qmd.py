@@ -40,9 +40,10 @@ class Cell:
     the per-step state (block X, density, last spectral bounds)."""
 
     def __init__(self, cfg: inputs.CellConfig, device: int = 0, prec=sq3.MIXED,
-                 proj_seed: int | None = None):
+                 proj_seed: int | None = None, kernel_eval: int = sq3.EVAL_RECURRENCE):
         self.cfg = cfg
         self.prec = prec
+        self.kernel_eval = kernel_eval
         self.ctx = sq3.Context(device)
         self.ctx.setup_grid(cfg.n, cfg.n, cfg.n, cfg.L, cfg.L, cfg.L, 12)
         self.proj_seed = cfg.seed if proj_seed is None else proj_seed
@@ -109,7 +110,7 @@ class Cell:
         args = dict(degree=cfg.m, npl=cfg.npl, kT=cfg.sigma, Ne=cfg.Ne, e_self=self.e_self,
                     tol=tol, prec=self.prec, first_passes=4 if first else 1, passes=1,
                     max_iter=100, bounds0=self.bounds, D=self.D, mix_history=7,
-                    mix_period=1, mix_beta=0.5)
+                    mix_period=1, mix_beta=0.5, kernel_eval=self.kernel_eval)
         args.update(kw)
         res, hist = self.ctx.scf_solve(self.b, self.rho, self.X, **args)
         self.bounds = (res["chi"], res["xi"])

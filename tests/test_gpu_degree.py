@@ -2,8 +2,9 @@
 the Paterson-Stockmeyer evaluation against the plain recurrence and the
 oracle's Fermi-operator expansion (Sec. 4) at the same degree, and the
 degree chosen from a tolerance against the library's rule and the oracle
-at that degree.  FP64 throughout: the two evaluations are the same
-polynomial, so they agree to rounding (1e-12 of the largest entry)."""
+at that degree.  In FP64 the two evaluations are the same polynomial, so
+they agree to rounding (1e-12 of the largest entry); the mixed path's
+Paterson-Stockmeyer form is held to the mixed recurrence's bar."""
 import numpy as np
 import pytest
 import torch
@@ -56,14 +57,36 @@ def test_paterson_stockmeyer_equals_the_recurrence_and_the_oracle(npl, Ns):
     assert abs(outp["mu"] - ref["mu"]) < 1e-11
 
 
-def test_paterson_stockmeyer_rejects_the_mixed_path():
+@pytest.mark.parametrize("npl,Ns", [(5, 40), (60, 150), (120, 200), (121, 131), (120, 2200)])
+def test_mixed_paterson_stockmeyer_matches_the_oracle_and_the_mixed_recurrence(npl, Ns):
+    """The mixed path's Paterson-Stockmeyer form (FP32 matrices, BF16-split
+    tensor-core products, Clenshaw in T_s) against the FP64 oracle expansion
+    at the same degree and bounds, with the mixed recurrence's bar (D within
+    2e-5, mu within 1e-5), and against the mixed recurrence itself; Ns = 2200, n_pl = 120 is the 108-atom workload's
+    expansion (s = 16 baby steps, 7 giant steps, 28 products)."""
     m = sq3()
     ctx = _ctx()
-    Hs, _ = _hs(40, 1)
-    with pytest.raises(m.SQ3Error) as e:
-        ctx.kernel_from_hs_ex(torch.from_numpy(Hs).cuda(), 20, 0.3, 10.0, prec=m.MIXED,
-                              eval_mode=m.EVAL_PATERSON_STOCKMEYER)
-    assert e.value.code == m.EINVAL
+    Hs, lam = _hs(Ns, npl + Ns)
+    chi, xi = 0.5 * (lam[0] + lam[-1]), 0.5 * (lam[-1] - lam[0]) * 1.001
+    sigma, Ne = inputs.ev_to_ha(10.0), 0.3 * Ns
+    Hg = torch.from_numpy(Hs).cuda()
+    Dp, outp, npp = ctx.kernel_from_hs_ex(Hg, npl, sigma, Ne, bounds=(chi, xi), prec=m.MIXED,
+                                          eval_mode=m.EVAL_PATERSON_STOCKMEYER)
+    Dr, outr, _ = ctx.kernel_from_hs_ex(Hg, npl, sigma, Ne, bounds=(chi, xi), prec=m.MIXED)
+    assert npp == npl
+    Dp, Dr = Dp.cpu().numpy(), Dr.cpu().numpy()
+    ref = chebyshev.foe_density_kernel(Hs, npl, sigma, Ne, chi, xi)
+    assert np.max(np.abs(Dp - ref["D"])) < 2e-5
+    assert np.max(np.abs(Dp - Dr)) < 2e-5
+    assert abs(outp["mu"] - ref["mu"]) < 1e-5
+    # the energies are sums over Ns states: 1e-4 absolute or 1e-5 relative
+    # (the FP32 moments' rounding grows with Ns), and no worse than the
+    # mixed recurrence's own error
+    for k in ("e_band", "e_ent"):
+        err_p, err_r = abs(outp[k] - ref[k]), abs(outr[k] - ref[k])
+        assert err_p < max(1e-4, 1e-5 * abs(ref[k])), k
+        assert err_p < 2.0 * err_r + 1e-4, k
+    assert abs(outp["two_tr_D"] - Ne) < 1e-9
 
 
 @pytest.mark.parametrize("kT_ev,tol", [(10.0, 1e-8), (50.0, 1e-10), (250.0, 1e-12)])
