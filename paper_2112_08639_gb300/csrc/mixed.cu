@@ -429,6 +429,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   bool have_pieces = false;
   __nv_bfloat16* rowA = b.rowX;       // rows of the current X
   __nv_bfloat16* rowB = b.rowX2;      // rows of the next X
+  ctx->pieces_X = nullptr;
   while (plain_left > 0) {
     if (!have_pieces) split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
@@ -510,6 +511,9 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     if (!have_pieces) split_block_rows(ctx, X, Ns, b, rowA);
     // another pass follows this one: its inputs' pieces come from this product
     const bool follows = shift_now || again || plain_left > 1;
+    // the final product also writes the pieces of the result for the
+    // projection and the density, when the SCF driver will reuse them
+    const bool keep = !follows && ctx->reuse_pieces;
     {
       // the product reads X only through its pieces, so it overwrites X
       Prof p(ctx, ST_XRINV);
@@ -518,7 +522,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       t.C32 = X;
       t.ldc = N;
       t.alpha = 1.f;
-      if (follows) {
+      if (follows || keep) {
         t.colP = b.colX;
         t.col_ld = b.ldN;
         t.col_ps = b.psN;
@@ -531,12 +535,23 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
     }
     if (rc) return rc;
     have_pieces = follows;
+    if (keep) {
+      ctx->pieces_X = X;
+      ctx->pieces_Ns = Ns;
+      ctx->pieces_rows = rowB;
+    }
     if (follows) std::swap(rowA, rowB);
     if (shift_now) shift_now = false;
     else if (again) extra = true;       // the last pass once more
     else --plain_left;
   }
   return check_device_status(ctx);
+}
+
+// The pieces of X kept by the last Cholesky QR are still those of X.
+static bool pieces_of(const sq3_ctx* ctx, const float* X, int Ns) {
+  return ctx->reuse_pieces && ctx->pieces_X == X && ctx->pieces_Ns == Ns &&
+         ctx->pieces_rows != nullptr;
 }
 
 int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs) {
@@ -549,7 +564,7 @@ int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs) {
   float* HX = (float*)ctx->wsX;
   rc = hamiltonian_apply_f32(ctx, X, HX, Ns);
   if (rc) return rc;
-  split_block_cols(ctx, X, Ns, b.colX, b);
+  if (!pieces_of(ctx, X, Ns)) split_block_cols(ctx, X, Ns, b.colX, b);
   split_block_cols(ctx, HX, Ns, b.colY, b);
   return gram_mixed(ctx, b.colX, b.colY, Ns, Hs, b, ST_HS_GEMM);
 }
@@ -736,7 +751,9 @@ int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double*
     split_upper_twice_kernel<<<grid_for((long long)Ns * Ns), 256, 0, ctx->stream>>>(
         D, Ns, b.matA, b.ldS, b.psS, MIXED_PIECES);
   }
-  split_block_rows(ctx, X, Ns, b);
+  const __nv_bfloat16* rows = b.rowX;
+  if (pieces_of(ctx, X, Ns)) rows = (const __nv_bfloat16*)ctx->pieces_rows;
+  else split_block_rows(ctx, X, Ns, b);
   Prof p(ctx, ST_RHO);
   cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), ctx->stream);
   TcParams t{};
@@ -745,7 +762,7 @@ int density_mixed(sq3_ctx* ctx, const float* X, const double* D, int Ns, double*
   t.rho = rho;
   t.rho_alpha = 2.0 / ctx->dV;
   t.tri = 2;                                         // B upper triangular
-  return tc_gemm(ctx, op_rows(b, N, Ns), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
+  return tc_gemm(ctx, op_rows(b, N, Ns, rows), op_mat(b.matA, Ns, b), products(MIXED_PIECES), t,
                  EPI_TC_RHO, 1, ctx->stream);
 }
 

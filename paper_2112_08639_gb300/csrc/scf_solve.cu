@@ -113,6 +113,13 @@ int sq3_scf_solve(sq3_ctx* c, const sq3_scf_params* p, const double* b, double* 
       (p->kernel_eval != SQ3_EVAL_RECURRENCE && p->kernel_eval != SQ3_EVAL_PATERSON_STOCKMEYER))
     return SQ3_EINVAL;
   cudaSetDevice(c->device);
+  // the driver alone knows that X is unchanged between its Cholesky QR, the
+  // projection and the density: only inside it are the kept pieces reused
+  struct ReuseGuard {
+    sq3_ctx* c;
+    explicit ReuseGuard(sq3_ctx* cc) : c(cc) { c->reuse_pieces = true; c->pieces_X = nullptr; }
+    ~ReuseGuard() { c->reuse_pieces = false; c->pieces_X = nullptr; }
+  } reuse_guard(c);
   *res = sq3_scf_result{};
   const long long N = c->grid.N;
   const size_t nn = (size_t)Ns * Ns;

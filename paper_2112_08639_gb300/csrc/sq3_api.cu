@@ -228,6 +228,7 @@ int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns) {
 template <typename T>
 static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
                          double b, double a0) {
+  ctx->pieces_X = nullptr;                 // X changes: its kept pieces are stale
   const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
@@ -659,6 +660,7 @@ int sq3_selftest_timeout(sq3_ctx* c) {
 
 int sq3_cheb_filter_from_host(sq3_ctx* c, const void* X_host, void* X, int Ns, int degree,
                               double a, double b, double a0, sq3_prec prec) {
+  if (c) c->pieces_X = nullptr;
   if (!ready(c)) return SQ3_ENOTSETUP;
   if (!X_host || !X || Ns <= 0 || Ns > 65535 || degree < 1 || !(a0 < a) || !(a < b))
     return SQ3_EINVAL;

@@ -111,6 +111,16 @@ struct ProfRec { int stage; int launches; cudaEvent_t a, b; };
 struct sq3_ctx {
   int device = 0;
   bool prof = false;
+  // BF16 pieces of an orthonormalised block X, written by the last X R^-1
+  // product of the mixed Cholesky QR: cols in the split workspace's colX,
+  // rows at pieces_rows.  Used (instead of splitting X again) by the mixed
+  // projection and density only while reuse_pieces is set, i.e. inside the
+  // SCF driver, which alone knows that X has not changed in between; any
+  // library call that writes X clears pieces_X.
+  bool reuse_pieces = false;
+  const void* pieces_X = nullptr;
+  int pieces_Ns = 0;
+  void* pieces_rows = nullptr;
   std::vector<sq3::ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;
   cudaStream_t stream = nullptr;
