@@ -103,14 +103,18 @@ class Cell:
     def solve(self, tol: float = 1e-6, **kw):
         cfg = self.cfg
         first = self.bounds is None
-        # mixing: a Pulay step every iteration with beta 0.5 (at 108 atoms a
-        # QMD step converged in 7 iterations against 9 with every second
-        # step and beta 0.3); from a random block the first iteration runs
-        # four filter passes, later ones one
+        # mixing: a Pulay step every iteration (Kerker-preconditioned) with
+        # beta 0.5 for a solve from scratch and 0.8 for a QMD step that starts
+        # near the previous step's state (at 108 atoms, two consecutive QMD
+        # steps: 6 iterations with beta 0.5 or 0.6, 5 with 0.7 .. 1.0, 7 with
+        # k0 = 0.5 or 1.2; every second Pulay step with beta 0.3 took 9); from
+        # a random block the first iteration runs four filter passes, later
+        # ones one
         args = dict(degree=cfg.m, npl=cfg.npl, kT=cfg.sigma, Ne=cfg.Ne, e_self=self.e_self,
                     tol=tol, prec=self.prec, first_passes=4 if first else 1, passes=1,
                     max_iter=100, bounds0=self.bounds, D=self.D, mix_history=7,
-                    mix_period=1, mix_beta=0.5, kernel_eval=self.kernel_eval)
+                    mix_period=1, mix_beta=0.5 if first else 0.8,
+                    kernel_eval=self.kernel_eval)
         args.update(kw)
         res, hist = self.ctx.scf_solve(self.b, self.rho, self.X, **args)
         self.bounds = (res["chi"], res["xi"])
