@@ -99,14 +99,14 @@ def test_scf_solve_fp64_matches_the_dense_oracle_scf():
     assert hist[0]["err"] > 1e-3
 
 
-def _solve(ctx, cfg, b, rho0, X0, prec, iters):
+def _solve(ctx, cfg, b, rho0, X0, prec, iters, passes=1):
     rho = rho0.clone()
     X = X0.clone() if prec == sq3().MIXED else X0.double()
     res, hist = ctx.scf_solve(b, rho, X, degree=cfg.m, npl=cfg.npl, kT=cfg.sigma, Ne=cfg.Ne,
                               e_self=scf.self_energy(cfg.natoms, inputs.Z_VALENCE,
                                                      inputs.RC_LOCAL),
-                              tol=1e-12, prec=prec, first_passes=4, passes=1, max_iter=iters,
-                              raise_on_noconv=False)
+                              tol=1e-12, prec=prec, first_passes=4, passes=passes,
+                              max_iter=iters, raise_on_noconv=False)
     return rho, res, hist
 
 
