@@ -738,7 +738,7 @@ def roofline(dominant, prof, cfg, esize, fp64, pk, pk_src, n_covered):
 # the 108-atom configuration with the learned start, as this bench's GPU
 # arm measured it; the reference arm scales the oracle's per-iteration cost
 # by it
-PASSES_PER_SOLVE = {"al108_72": 6, "al32_48": 6}
+PASSES_PER_SOLVE = {"al108_72": 5, "al32_48": 5}
 
 
 def run_oracle_sample(cfg_name: str, passes: int):
