@@ -430,6 +430,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   __nv_bfloat16* rowA = b.rowX;       // rows of the current X
   __nv_bfloat16* rowB = b.rowX2;      // rows of the next X
   ctx->pieces_X = nullptr;
+  ctx->hx_X = nullptr;                // X changes: a kept H X is stale
   while (plain_left > 0) {
     if (!have_pieces) split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
@@ -562,8 +563,22 @@ int project_mixed(sq3_ctx* ctx, const float* X, int Ns, double* Hs) {
   rc = ensure(&ctx->wsX, &ctx->wsX_bytes, (size_t)N * Ns * sizeof(float));
   if (rc) return rc;
   float* HX = (float*)ctx->wsX;
+  ctx->hx_X = nullptr;
   rc = hamiltonian_apply_f32(ctx, X, HX, Ns);
   if (rc) return rc;
+  if (ctx->reuse_pieces) {
+    // keep H X (in wsX) and its potential for the next filter of this X
+    if (!ctx->Vf_hx && cudaMalloc((void**)&ctx->Vf_hx, (size_t)N * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->Vf_hx = nullptr;
+    }
+    if (ctx->Vf_hx) {
+      cudaMemcpyAsync(ctx->Vf_hx, ctx->Vf, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice,
+                      ctx->stream);
+      ctx->hx_X = X;
+      ctx->hx_Ns = Ns;
+    }
+  }
   if (!pieces_of(ctx, X, Ns)) split_block_cols(ctx, X, Ns, b.colX, b);
   split_block_cols(ctx, HX, Ns, b.colY, b);
   return gram_mixed(ctx, b.colX, b.colY, Ns, Hs, b, ST_HS_GEMM);

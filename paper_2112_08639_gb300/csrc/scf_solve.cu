@@ -117,8 +117,16 @@ int sq3_scf_solve(sq3_ctx* c, const sq3_scf_params* p, const double* b, double* 
   // projection and the density: only inside it are the kept pieces reused
   struct ReuseGuard {
     sq3_ctx* c;
-    explicit ReuseGuard(sq3_ctx* cc) : c(cc) { c->reuse_pieces = true; c->pieces_X = nullptr; }
-    ~ReuseGuard() { c->reuse_pieces = false; c->pieces_X = nullptr; }
+    explicit ReuseGuard(sq3_ctx* cc) : c(cc) {
+      c->reuse_pieces = true;
+      c->pieces_X = nullptr;
+      c->hx_X = nullptr;
+    }
+    ~ReuseGuard() {
+      c->reuse_pieces = false;
+      c->pieces_X = nullptr;
+      c->hx_X = nullptr;
+    }
   } reuse_guard(c);
   *res = sq3_scf_result{};
   const long long N = c->grid.N;

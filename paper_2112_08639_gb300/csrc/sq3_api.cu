@@ -217,6 +217,44 @@ static int hamiltonian_apply_t(sq3_ctx* ctx, const T* X, T* Y, int Ns) {
   return cuda_err(cudaGetLastError());
 }
 
+// W = sc1 (W + (Vf - Vf_hx - c) X) over N x Ns (column v at v N), W holding
+// H X applied with the potential Vf_hx: the first filter step from a kept
+// H X.  Block row y: vector y; 16-byte vectors when N is a multiple of 4.
+__global__ void filter_first_from_hx_kernel(float* W, const float* __restrict__ X,
+                                            const float* __restrict__ V,
+                                            const float* __restrict__ Vhx, long long N,
+                                            float sc1, float c) {
+  const long long off = (long long)blockIdx.y * N;
+  if ((N & 3) == 0) {
+    const long long n4 = N / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+      float4 w = reinterpret_cast<float4*>(W + off)[i];
+      const float4 x = reinterpret_cast<const float4*>(X + off)[i];
+      const float4 v = reinterpret_cast<const float4*>(V)[i];
+      const float4 h = reinterpret_cast<const float4*>(Vhx)[i];
+      w.x = sc1 * (w.x + ((v.x - h.x) - c) * x.x);
+      w.y = sc1 * (w.y + ((v.y - h.y) - c) * x.y);
+      w.z = sc1 * (w.z + ((v.z - h.z) - c) * x.z);
+      w.w = sc1 * (w.w + ((v.w - h.w) - c) * x.w);
+      reinterpret_cast<float4*>(W + off)[i] = w;
+    }
+  } else {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x)
+      W[off + k] = sc1 * (W[off + k] + ((V[k] - Vhx[k]) - c) * X[off + k]);
+  }
+}
+
+static void filter_first_from_hx(sq3_ctx* ctx, float* W, const float* X, int Ns, double sc1,
+                                 double c) {
+  const long long N = ctx->grid.N;
+  const long long per = (N % 4 == 0) ? N / 4 : N;
+  const unsigned bx = (unsigned)std::min<long long>((per + 255) / 256, 64);
+  filter_first_from_hx_kernel<<<dim3(bx, Ns), 256, 0, ctx->stream>>>(W, X, ctx->Vf, ctx->Vf_hx,
+                                                                      N, (float)sc1, (float)c);
+}
+
 int hamiltonian_apply_f32(sq3_ctx* ctx, const float* X, float* Y, int Ns) {
   return hamiltonian_apply_t<float>(ctx, X, Y, Ns);
 }
@@ -229,6 +267,11 @@ template <typename T>
 static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
                          double b, double a0) {
   ctx->pieces_X = nullptr;                 // X changes: its kept pieces are stale
+  // H X kept by the driver's last projection of this same X (mixed path)
+  const bool from_hx = sizeof(T) == 4 && ctx->reuse_pieces && ctx->hx_X == (const void*)X &&
+                       ctx->hx_Ns == Ns && ctx->Vf_hx != nullptr && ctx->wsX != nullptr &&
+                       ctx->wsX_bytes >= (size_t)ctx->grid.N * Ns * sizeof(T);
+  ctx->hx_X = nullptr;
   const size_t blk = (size_t)ctx->grid.N * Ns * sizeof(T);
   int rc = ensure(&ctx->wsX, &ctx->wsX_bytes, blk);
   if (rc) return rc;
@@ -261,13 +304,27 @@ static int cheb_filter_t(sq3_ctx* ctx, T* X, int Ns, int m, double a,
       nrc = launch_nl_pass<T>(ctx, out, gC, want_next ? gN : nullptr, Ns, sc1, ctx->stream);
     }
   };
-  if (nl) {
-    // projections of the input block (projection-only nonlocal pass)
-    Prof p(ctx, ST_NL_PROJECT);
-    cudaMemsetAsync(gC, 0, gbytes, ctx->stream);
-    nrc = launch_nl_pass<T>(ctx, X, nullptr, gC, Ns, 0.0, ctx->stream);
+  if (from_hx) {
+    // Y_1 = (s1/e)(H X - c X) from the kept H X: W = (s1/e)(W + (V - V_hx - c) X),
+    // then the projections of Y_1 for the second step
+    {
+      Prof p(ctx, ST_STENCIL);
+      filter_first_from_hx(ctx, (float*)W, (const float*)X, Ns, s1 / e, c);
+    }
+    if (nl && m > 1) {
+      Prof p(ctx, ST_NL_PROJECT);
+      cudaMemsetAsync(gN, 0, gbytes, ctx->stream);
+      nrc = launch_nl_pass<T>(ctx, W, nullptr, gN, Ns, 0.0, ctx->stream);
+    }
+  } else {
+    if (nl) {
+      // projections of the input block (projection-only nonlocal pass)
+      Prof p(ctx, ST_NL_PROJECT);
+      cudaMemsetAsync(gC, 0, gbytes, ctx->stream);
+      nrc = launch_nl_pass<T>(ctx, X, nullptr, gC, Ns, 0.0, ctx->stream);
+    }
+    step(X, nullptr, W, s1 / e, 0.0, m > 1);
   }
-  step(X, nullptr, W, s1 / e, 0.0, m > 1);
   for (int k = 2; k <= m; ++k) {
     const double sn = 1.0 / (tau - s);
     if (nl) std::swap(gC, gN);
@@ -468,6 +525,7 @@ void sq3_destroy(sq3_ctx* c) {
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (auto e : c->upload_ev) if (e) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->Vf_hx) cudaFree(c->Vf_hx);
   void* ptrs[] = {c->V, c->Vf, c->dev_status, c->dev_scal, c->wsX, c->wsX2,
                   c->wsMat, c->wsT, c->wsProj, c->wsSplit, c->wsFoe, c->wsLin32,
                   c->scfTab, c->wsScf, c->wsMix, c->wsDrv, c->wsAtoms};
@@ -480,6 +538,12 @@ int sq3_setup_grid(sq3_ctx* c, int nx, int ny, int nz, double Lx, double Ly,
                    double Lz, int fd_order) {
   if (!c || fd_order < 2 || fd_order > 2 * SQ3_MAX_FD_RADIUS || fd_order % 2)
     return SQ3_EINVAL;
+  c->hx_X = nullptr;
+  if (c->Vf_hx) {                          // sized for the previous grid
+    cudaSetDevice(c->device);
+    cudaFree(c->Vf_hx);
+    c->Vf_hx = nullptr;
+  }
   const int R = fd_order / 2;
   if (nx < R || ny < R || nz < R || nx > 512 ||
       !(Lx > 0) || !(Ly > 0) || !(Lz > 0))
@@ -553,6 +617,7 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
       if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
   }
   free_projectors(c->proj);
+  c->hx_X = nullptr;
   if (n_proj == 0) return SQ3_OK;
   ProjectorHostTables T;
   projector_host_tables(c->grid.nx, c->grid.ny, c->grid.nz, c->dV, n_proj, ptr, idx, val,

@@ -121,6 +121,13 @@ struct sq3_ctx {
   const void* pieces_X = nullptr;
   int pieces_Ns = 0;
   void* pieces_rows = nullptr;
+  // H X of the mixed projection, kept in the work block wsX with the FP32
+  // potential it was applied with (Vf_hx), for the next filter of the same
+  // X inside the SCF driver: its first step is then (s1/e)(H X + (V - V_hx) X
+  // - c X), elementwise, instead of a stencil and a nonlocal pass
+  const void* hx_X = nullptr;
+  int hx_Ns = 0;
+  float* Vf_hx = nullptr;
   std::vector<sq3::ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;
   cudaStream_t stream = nullptr;
