@@ -18,8 +18,8 @@ that the same code runs on NCCL ranks (one GPU each) or on gloo ranks
 * the density kernel's column blocks are all-gathered before the slab-local
   density rho = 2 rowdot(X, X Ds) / dV.
 
-Every box of this build has one GPU, so the path runs unsharded; this is
-the design, exercised by two gloo ranks on the CPU (tests/test_sharding_gloo.py).
+On one GPU the path runs unsharded; this module is the partitioning,
+exercised by two and three gloo ranks on the CPU (tests/test_sharding_gloo.py).
 """
 from __future__ import annotations
 
