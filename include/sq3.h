@@ -105,6 +105,21 @@ int sq3_set_potential(sq3_ctx* ctx, const double* V);
 int sq3_set_projectors(sq3_ctx* ctx, int n_proj, const int* ptr,
                        const int* idx, const double* val, const double* gamma);
 
+/* Host-only: the tables sq3_set_projectors would build from the same CSR
+ * arguments on an nx x ny x nz grid of cell volume element dV, without a
+ * context or a device.  info (HOST, 6 ints): {balls (runs of <= 4
+ * projectors sharing an index list), (point, ball) entries after repeated
+ * indices are merged, 8 x 8 x 4 bricks, most balls in one brick, most
+ * entries in one brick, shared-memory bytes of the FP32 nonlocal pass};
+ * bounds (HOST, 2 doubles): Gershgorin bounds lo <= lambda <= hi of the
+ * spectrum of V_nl = sum_p gamma_p c_p c_p^T, c_p = chi_p sqrt(dV) (from the
+ * projectors' overlap matrix; 0 is always inside).  Errors: SQ3_EINVAL as
+ * sq3_set_projectors' table checks (and for a bad grid, dV <= 0 or a NULL
+ * output). */
+int sq3_projector_table_info(int nx, int ny, int nz, double dV, int n_proj, const int* ptr,
+                             const int* idx, const double* val, const double* gamma, int* info,
+                             double* bounds);
+
 /* Y = H X for a block of Ns vectors (Sec. 2, Eq. (KSeqn)); X and Y are N x Ns
  * column-major of the precision's element type and must not overlap.
  * Errors: SQ3_ENOTSETUP, SQ3_EINVAL. */

@@ -601,6 +601,43 @@ int sq3_set_potential(sq3_ctx* c, const double* V) {
   return SQ3_OK;
 }
 
+// The CSR projector table's own checks (indices inside the grid of N
+// points, ptr monotone from 0, every value and energy finite).
+static int check_projector_table(long long N, int n_proj, const int* ptr, const int* idx,
+                                 const double* val, const double* gamma) {
+  if (n_proj < 0) return SQ3_EINVAL;
+  if (n_proj == 0) return SQ3_OK;
+  if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
+  for (int p = 0; p < n_proj; ++p)
+    if (ptr[p + 1] < ptr[p] || !isfinite(gamma[p])) return SQ3_EINVAL;
+  for (long long e = 0; e < (long long)ptr[n_proj]; ++e)
+    if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
+  return SQ3_OK;
+}
+
+int sq3_projector_table_info(int nx, int ny, int nz, double dV, int n_proj, const int* ptr,
+                             const int* idx, const double* val, const double* gamma, int* info,
+                             double* bounds) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(dV > 0) || !info || !bounds) return SQ3_EINVAL;
+  const long long N = (long long)nx * ny * nz;
+  int rc = check_projector_table(N, n_proj, ptr, idx, val, gamma);
+  if (rc) return rc;
+  for (int i = 0; i < 6; ++i) info[i] = 0;
+  bounds[0] = bounds[1] = 0.0;
+  if (n_proj == 0) return SQ3_OK;
+  ProjectorHostTables T;
+  projector_host_tables(nx, ny, nz, dV, n_proj, ptr, idx, val, gamma, T);
+  info[0] = (int)T.bp0.size();
+  info[1] = (int)T.qlb.size();
+  info[2] = (int)(T.sptr.size() - 1);
+  info[3] = T.max_brick_balls;
+  info[4] = T.max_brick_entries;
+  info[5] = (int)nl_pass_smem_bytes(4, 16, 3, T.max_brick_balls, T.max_brick_entries);
+  bounds[0] = T.vnl_lo;
+  bounds[1] = T.vnl_hi;
+  return SQ3_OK;
+}
+
 int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
                        const double* val, const double* gamma) {
   if (!c || !c->grid_ok) return SQ3_ENOTSETUP;
@@ -608,14 +645,8 @@ int sq3_set_projectors(sq3_ctx* c, int n_proj, const int* ptr, const int* idx,
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   const long long N = c->grid.N;
-  if (n_proj > 0) {
-    // a rejected table leaves the context's projectors as they were
-    if (!ptr || !idx || !val || !gamma || ptr[0] != 0) return SQ3_EINVAL;
-    for (int p = 0; p < n_proj; ++p)
-      if (ptr[p + 1] < ptr[p] || !isfinite(gamma[p])) return SQ3_EINVAL;
-    for (long long e = 0; e < (long long)ptr[n_proj]; ++e)
-      if (idx[e] < 0 || idx[e] >= N || !isfinite(val[e])) return SQ3_EINVAL;
-  }
+  // a rejected table leaves the context's projectors as they were
+  if (check_projector_table(N, n_proj, ptr, idx, val, gamma)) return SQ3_EINVAL;
   free_projectors(c->proj);
   c->hx_X = nullptr;
   if (n_proj == 0) return SQ3_OK;

@@ -39,6 +39,7 @@ _sigs = {
     "sq3_setup_grid": (_i, [_p, _i, _i, _i, _d, _d, _d, _i]),
     "sq3_set_potential": (_i, [_p, _p]),
     "sq3_set_projectors": (_i, [_p, _i, _p, _p, _p, _p]),
+    "sq3_projector_table_info": (_i, [_i, _i, _i, _d, _i, _p, _p, _p, _p, _p, _p]),
     "sq3_hamiltonian_apply": (_i, [_p, _p, _p, _i, _i]),
     "sq3_cheb_filter": (_i, [_p, _p, _i, _i, _d, _d, _d, _i]),
     "sq3_cheb_filter_from_host": (_i, [_p, _p, _p, _i, _i, _d, _d, _d, _i]),
@@ -151,6 +152,25 @@ def fermi_degree(sigma: float, xi: float, tol: float) -> int:
     if n < 0:
         raise SQ3Error(n, "sq3_fermi_degree")
     return n
+
+
+def projector_table_info(grid, dV: float, ptr, idx, val, gamma) -> dict:
+    """The tables a context would build from this projector table on the
+    grid (nx, ny, nz) (sq3_projector_table_info; host only, no device)."""
+    p = np.ascontiguousarray(ptr, dtype=np.int32)
+    ix = np.ascontiguousarray(idx, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    info = (ctypes.c_int * 6)()
+    bounds = (ctypes.c_double * 2)()
+    _check(lib.sq3_projector_table_info(int(grid[0]), int(grid[1]), int(grid[2]), float(dV),
+                                        len(g), p.ctypes.data, ix.ctypes.data, v.ctypes.data,
+                                        g.ctypes.data, info, bounds),
+           "sq3_projector_table_info")
+    keys = ("balls", "entries", "bricks", "max_brick_balls", "max_brick_entries", "smem_bytes")
+    out = dict(zip(keys, list(info)))
+    out["vnl_lo"], out["vnl_hi"] = bounds[0], bounds[1]
+    return out
 
 
 def verlet(masses, dt: float, R: np.ndarray, V: np.ndarray, F: np.ndarray, phase: int,

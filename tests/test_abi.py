@@ -75,6 +75,9 @@ def test_argument_errors_before_any_device_work(libpath):
         "sq3_setup_grid": ([p, i, i, i, d, d, d, i], (None, 8, 8, 8, 1.0, 1.0, 1.0, 12), EINVAL),
         "sq3_set_potential": ([p, p], (None, None), ENOTSETUP),
         "sq3_set_projectors": ([p, i, p, p, p, p], (None, 0, None, None, None, None), ENOTSETUP),
+        "sq3_projector_table_info": ([i, i, i, d, i, p, p, p, p, p, p],
+                                     (8, 8, 8, 0.1, 4, None, None, None, None, None, None),
+                                     EINVAL),
         "sq3_hamiltonian_apply": ([p, p, p, i, i], (None, None, None, 4, 0), ENOTSETUP),
         "sq3_cheb_filter": ([p, p, i, i, d, d, d, i], (None, None, 4, 3, 1.0, 2.0, 0.0, 0),
                             ENOTSETUP),
