@@ -647,7 +647,8 @@ size_t nl_pass_smem_bytes(int es, int VB, int NBUF, int max_balls, int max_entri
          (size_t)NL_BRICK_PTS * (VB + 16 / es) * es +
          (size_t)NBUF * max_balls * (4 * (VB + 4) + 16 / es) * es +
          (size_t)2 * max_entries * 4 * es +
-         (size_t)2 * max_entries * sizeof(short) + 8 + (size_t)NBUF * 8;
+         (size_t)2 * max_entries * sizeof(short) + 8 + (size_t)NBUF * 8 +
+         (size_t)4 * max_balls * (es + sizeof(int)) + (size_t)(max_balls + 1) * sizeof(int);
 }
 
 template <typename T, int VB, int NBUF, int MINB>
@@ -691,6 +692,11 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   short* zpt = qlb + max_entries;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
       (reinterpret_cast<uintptr_t>(zpt + max_entries) + 7) & ~uintptr_t(7));
+  // the brick's per-ball metadata, read in every group: projector ids and
+  // energies of the ball slots, ball-major entry ranges
+  T* s_gam = reinterpret_cast<T*>(bars + NBUF);
+  int* s_pid = reinterpret_cast<int*>(s_gam + 4 * max_balls);
+  int* s_bptr = s_pid + 4 * max_balls;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
@@ -707,6 +713,12 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
   const int fb = bl_ptr[s0];
   const int nrows = 4 * nlb;
   const uint32_t bar0 = smem_u32(bars);
+  for (int i = tid; i < 4 * nlb; i += PTS) {
+    const int pid = slot_pid[4 * s0 + i];
+    s_pid[i] = pid;
+    s_gam[i] = pid >= 0 ? T(gamma[pid]) : T(0);
+  }
+  for (int i = tid; i <= nlb; i += PTS) s_bptr[i] = bl_ptr[s0 + i] - fb;
   if (tid == 0) {
     abort_flag = 0;
 #pragma unroll
@@ -728,7 +740,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       for (int i = tid; i < nrows * VB; i += PTS) {
         const int r = i / VB, v = i - r * VB;
         const int vg = g * VB + v;
-        const int pid = slot_pid[4 * s0 + r];
+        const int pid = s_pid[r];
         const bool ok = pid >= 0 && vg < Ns;
         const T* src = gC + (ok ? (long long)pid * Ns + vg : 0);
         cp_async_zfill<(int)sizeof(T)>(gl + (r >> 2) * BST + (r & 3) * GS + v, src,
@@ -844,7 +856,7 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
       static_assert(NQ == 4 && NR * NSL == NA, "four quarters, eight slots");
       const int qd = lane % NQ, sl = lane / NQ;
       for (int lb = warp; lb < nlb; lb += PTS / 32) {
-        const int f0 = bl_ptr[s0 + lb] - fb, f1 = bl_ptr[s0 + lb + 1] - fb;
+        const int f0 = s_bptr[lb], f1 = s_bptr[lb + 1];
         T a[NA];
 #pragma unroll
         for (int i = 0; i < NA; ++i) a[i] = T(0);
@@ -882,10 +894,10 @@ nl_brick_kernel(const __grid_constant__ CUtensorMap omap, int nx, int ny, int Ns
         for (int i = 0; i < NR; ++i) {
           const int idx = sl * NR + i;
           const int q = idx / EV, v = qd * EV + idx % EV;
-          const int pid = slot_pid[4 * (s0 + lb) + q];
+          const int pid = s_pid[4 * lb + q];
           const int vg = g * VB + v;
           if (pid >= 0 && vg < Ns && a[i] != T(0))
-            atomicAdd(gC_next + (long long)pid * Ns + vg, T(gamma[pid]) * a[i]);
+            atomicAdd(gC_next + (long long)pid * Ns + vg, s_gam[4 * lb + q] * a[i]);
         }
       }
     }
