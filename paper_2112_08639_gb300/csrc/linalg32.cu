@@ -443,10 +443,10 @@ int deviation_cholesky_f32(sq3_ctx* ctx, const double* S, float* F, int n, cudaS
 }
 
 int rinv_from_lower_f32(const float* L, int n, bool dev, float* W, float* tmp, float* Rinv,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool add_identity) {
   const int launches = tri_inverse(L, W, n, dev, tmp, st);
   dim3 grid((n + 31) / 32, (n + 31) / 32);
-  transpose_add_identity_kernel<<<grid, dim3(32, 8), 0, st>>>(W, n, dev, Rinv);
+  transpose_add_identity_kernel<<<grid, dim3(32, 8), 0, st>>>(W, n, dev && add_identity, Rinv);
   return launches + 1;
 }
 

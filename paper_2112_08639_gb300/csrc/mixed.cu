@@ -266,7 +266,9 @@ static int mixed_buffers(sq3_ctx* ctx, int Ns, MixedBuffers* b) {
 
 static Products products(int pieces) {
   Products pr{};
-  if (pieces == 3) {
+  if (pieces == 1) {
+    pr.n = 1;                           // x0 y0 only
+  } else if (pieces == 3) {
     // terms down to 2^-16 relative: x0y0, x0y1, x1y0, x0y2, x1y1, x2y0
     const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
     pr.n = 6;
@@ -328,11 +330,12 @@ static Operand op_cols(const __nv_bfloat16* base, int Ns, long long N, const Mix
   return Operand{base, Ns, (int)N, b.ldN, b.psN, MIXED_PIECES};
 }
 static Operand op_rows(const MixedBuffers& b, long long N, int Ns,
-                       const __nv_bfloat16* base = nullptr) {
-  return Operand{base ? base : b.rowX, (int)N, Ns, b.ldS, N * b.ldS, MIXED_PIECES};
+                       const __nv_bfloat16* base = nullptr, int pieces = MIXED_PIECES) {
+  return Operand{base ? base : b.rowX, (int)N, Ns, b.ldS, N * b.ldS, pieces};
 }
-static Operand op_mat(const __nv_bfloat16* base, int Ns, const MixedBuffers& b) {
-  return Operand{base, Ns, Ns, b.ldS, b.psS, MIXED_PIECES};
+static Operand op_mat(const __nv_bfloat16* base, int Ns, const MixedBuffers& b,
+                      int pieces = MIXED_PIECES) {
+  return Operand{base, Ns, Ns, b.ldS, b.psS, pieces};
 }
 
 // Split-K factor for `tiles` output tiles: each CTA keeps >= 4096 of K, and
@@ -424,6 +427,8 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   double* devpart = ctx->dev_scal + 24;  // its 32 block sums (slots 24 .. 55)
   bool shift_now = false, shifted = false, extra = false;
   int plain_left = 2;
+  // pieces of the last pass's product X + X (R^-1 - I), 0: the plain X R^-1
+  int dev_pieces = 0;
   // the pieces of X for the next pass, written by the X R^-1 product of the
   // pass before (colX for the Gram, rows for the next X R^-1)
   bool have_pieces = false;
@@ -432,6 +437,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
   ctx->pieces_X = nullptr;
   ctx->hx_X = nullptr;                // X changes: a kept H X is stale
   while (plain_left > 0) {
+    dev_pieces = 0;
     if (!have_pieces) split_block_cols(ctx, X, Ns, b.colX, b);
     rc = gram_mixed(ctx, b.colX, b.colX, Ns, S, b, ST_GRAM);
     if (rc) return rc;
@@ -451,9 +457,22 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       // a block still far from orthonormal (|X^T X - I|_F > 0.3) gets one
       // more pass: the orthogonality a pass leaves grows with cond(X)^2
       again = !extra && ctx->host_scal[16] > 0.09;
+      // The product of the final pass as X + X G with G = R^-1 - I, whose
+      // norm is about |E|_F / 2: the piece products left out (order k in
+      // the BF16 pieces, 2^-9k relative each) then cost at most about
+      // 2 2^-9k |G| per element, so one piece of each operand suffices when
+      // |E|_F <= 1.6e-5 and two (three products) when |E|_F <= 2.6e-3, both
+      // within 3e-8; a larger deviation takes the full product.
+      dev_pieces = 0;
+      if (!again) {
+        const double e2 = ctx->host_scal[16];
+        if (e2 <= 2.5e-10) dev_pieces = 1;
+        else if (e2 <= 6.8e-6) dev_pieces = 2;
+      }
       if (rc == SQ3_OK) {
         Prof p(ctx, ST_TRINV);
-        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream);
+        p.launches = rinv_from_lower_f32(F32, Ns, true, W32, tmp32, R32, ctx->stream,
+                                         dev_pieces == 0);
         have_r32 = true;
       } else if (rc != SQ3_ENOTPD) {
         return rc;
@@ -480,6 +499,7 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
       }
     }
     if (!have_r32) {
+      dev_pieces = 0;                   // the FP64 fallback: the full product
       if (shift_now) {
         Prof p(ctx, ST_CHOL);
         add_shift_maxdiag_kernel<<<1, 1024, 0, ctx->stream>>>(S, Ns, 1e-6);
@@ -531,8 +551,15 @@ int orthonormalise_mixed(sq3_ctx* ctx, float* X, int Ns) {
         t.row_ld = b.ldS;
         t.row_ps = N * b.ldS;
       }
-      rc = tc_gemm(ctx, op_rows(b, N, Ns, rowA), op_mat(b.matA, Ns, b), products(MIXED_PIECES),
-                   t, EPI_TC_STORE, 1, ctx->stream);
+      const int pieces = dev_pieces > 0 ? dev_pieces : MIXED_PIECES;
+      if (dev_pieces > 0) {
+        t.beta = 1.f;                     // X <- X + X (R^-1 - I), in place
+        // the correction is |G| ~ 1e-5 of X: its FP32 accumulation over the
+        // whole K range of a tile costs far less than FP32 rounding of X
+        t.one_partial = 1;
+      }
+      rc = tc_gemm(ctx, op_rows(b, N, Ns, rowA, pieces), op_mat(b.matA, Ns, b, pieces),
+                   products(pieces), t, EPI_TC_STORE, 1, ctx->stream);
     }
     if (rc) return rc;
     have_pieces = follows;

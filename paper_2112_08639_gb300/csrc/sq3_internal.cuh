@@ -290,10 +290,11 @@ void deviation_norm_f64(const double* S, int n, double* out, double* part, cudaS
 // R(i, :) *= dinv[i] (column-major n x n)
 void scale_rows_f32(float* R, int n, const float* dinv, cudaStream_t st);
 // Rinv = L^{-T} (upper, column-major FP32) of the lower-triangular L, or of
-// I + L when dev.  W: n*n floats, tmp: n*n/2 floats of workspace.  Returns
+// I + L when dev (then without its identity part, Rinv - I, when
+// !add_identity).  W: n*n floats, tmp: n*n/2 floats of workspace.  Returns
 // the number of kernel launches.
 int rinv_from_lower_f32(const float* L, int n, bool dev, float* W, float* tmp, float* Rinv,
-                         cudaStream_t st);
+                        cudaStream_t st, bool add_identity = true);
 void convert_f64_to_f32(const double* A, long long tot, float* B, cudaStream_t st);
 void mirror_upper_f64(double* A, int n, cudaStream_t st);
 // Words of Lanczos scratch for vectors of length n and `steps` (<= 64)

@@ -18,7 +18,7 @@
 // 32 lanes its index allows) and
 // fed to a fused epilogue:
 //   EPI_TC_ATOMIC  C(m,n) += acc (FP64 atomics; split-K Gram and X^T (H X))
-//   EPI_TC_STORE   C(m,n)  = alpha acc (FP32)
+//   EPI_TC_STORE   C(m,n)  = alpha acc (+ beta C(m,n)) (FP32)
 //   EPI_TC_CHEB    T_{j+1} = 2 acc - T_{j-1}; stores T_{j+1} (FP32), its bf16
 //                  pieces for the next product, and its trace
 //   EPI_TC_RHO     rho(m) += alpha sum_n X(m,n) acc(m,n)   (FP64 atomics)
@@ -157,7 +157,9 @@ __device__ __forceinline__ void store_row_pieces(const float (&v)[8], __nv_bfloa
 // warp 1 issues the MMAs; warps 2..17 accumulate and run the epilogue.  Each
 // K-block (KPP stages, 128 of K) of piece products goes into a fresh TMEM
 // accumulator (two of them, alternating), so the tensor core never adds into
-// a long running sum; the accumulation warps add every finished K-block
+// a long running sum (unless one_partial: a product whose result is a small
+// correction, where the whole K range of a tile goes into one accumulator);
+// the accumulation warps add every finished K-block
 // partial into a Kahan-compensated FP32 sum that is kept in TMEM as well
 // (columns 2 BN .. 4 BN: sum and compensation; an 18-warp CTA has at most
 // 96 registers per thread).  Warp w owns lanes 32 (w % 4) .. + 31, the lanes
@@ -170,6 +172,8 @@ __device__ __forceinline__ void store_row_pieces(const float (&v)[8], __nv_bfloa
 constexpr int ACC_WARPS = 16;
 constexpr int THREADS = 64 + 32 * ACC_WARPS;
 constexpr int ACC_COLS = BN / (ACC_WARPS / 4);   // columns per accumulation thread
+constexpr int STG_BYTES = ACC_WARPS * 32 * ACC_COLS * 2;   // row-piece staging
+static_assert(ACC_COLS == 32, "four 16-byte chunks per staged row");
 
 template <int PA, int PB, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -294,8 +298,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % STAGES;
         const int buf = part & 1;
-        const bool first = (kb % KPP) == 0;
-        const bool last = (kb % KPP) == KPP - 1 || kb == nk - 1;
+        const bool first = p.one_partial ? kb == 0 : (kb % KPP) == 0;
+        const bool last = p.one_partial ? kb == nk - 1 : ((kb % KPP) == KPP - 1 || kb == nk - 1);
         // the accumulator used two partials ago must have been drained
         if (first && part >= 2 && !mbar_wait(acce0 + 8 * buf, ((part - 2) >> 1) & 1)) {
           ok = false;
@@ -339,12 +343,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16);
     const uint32_t tsum = trow + (uint32_t)(2 * BN + half * ACC_COLS);
     const uint32_t tcmp = trow + (uint32_t)(3 * BN + half * ACC_COLS);
+    // this warp's staging rows for the row-major pieces (EPI_TC_STORE): 32
+    // rows x ACC_COLS bf16 past the tile stages
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(
+        smem_raw + (base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES +
+        (warp - 2) * 32 * ACC_COLS * 2);
     int part = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
       int m0, n0, kbeg, nk;
       decode(t, m0, n0, kbeg, nk);
-      const int ngrp = (nk + KPP - 1) / KPP;
+      const int ngrp = p.one_partial ? (nk > 0 ? 1 : 0) : (nk + KPP - 1) / KPP;
       bool have = ngrp > 0;
       float ksum[ACC_COLS];
 #pragma unroll
@@ -459,7 +468,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             if (EPI == EPI_TC_ATOMIC) {
               atomicAdd(p.C64 + e, acc);
             } else if (EPI == EPI_TC_STORE) {
-              const float v = (float)((double)p.alpha * acc);
+              double a = (double)p.alpha * acc;
+              if (p.beta != 0.f) a += (double)p.beta * (double)p.C32[e];
+              const float v = (float)a;
               p.C32[e] = v;
               tvs[i] = v;
               if (p.colP) split_store(v, p.colP, (long long)n * p.col_ld + m, p.col_ps, 3);
@@ -490,12 +501,54 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             store_row_pieces(tvs, p.Bnext + (long long)m * p.ld_next + nb, p.next_piece_stride,
                              p.N - nb, (p.ld_next & 7) == 0);
           }
-          if (EPI == EPI_TC_STORE && p.rowP) {
-            // the pieces of row m of the result, this lane's 8 columns
-            const int nb = n0 + half * ACC_COLS + c * 8;
-            store_row_pieces(tvs, p.rowP + (long long)m * p.row_ld + nb, p.row_ps, p.N - nb,
-                             (p.row_ld & 7) == 0);
+          if (EPI == EPI_TC_STORE) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ksum[c * 8 + i] = tvs[i];   // kept for the row pieces
           }
+        }
+      }
+      if (EPI == EPI_TC_STORE && p.rowP) {
+        // The pieces of the tile's rows, row-major: a lane's 32 values (its
+        // row, this warp's columns) go to the warp's staging rows in shared
+        // memory (16-byte chunks swizzled by row, conflict-free both ways),
+        // then four lanes store one row's 64 bytes, so every store writes 8
+        // rows x 64 contiguous bytes instead of 32 rows x 16.  Piece q is
+        // bf16 of what pieces 0 .. q-1 left (ksum keeps the rest).
+        const int nb0 = n0 + half * ACC_COLS;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+#pragma unroll
+          for (int c = 0; c < ACC_COLS / 8; ++c) {
+            __align__(16) __nv_bfloat16 pc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float x = ksum[c * 8 + i];
+              pc[i] = __float2bfloat16_rn(x);
+              ksum[c * 8 + i] = x - __bfloat162float(pc[i]);
+            }
+            *reinterpret_cast<uint4*>(stg + lane * ACC_COLS + 8 * (c ^ ((lane >> 1) & 3))) =
+                *reinterpret_cast<const uint4*>(pc);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = 8 * i + (lane >> 2), cc = lane & 3;
+            const int mr = m0 + q4 * 32 + r, nb = nb0 + cc * 8;
+            const uint4 val =
+                *reinterpret_cast<const uint4*>(stg + r * ACC_COLS + 8 * (cc ^ ((r >> 1) & 3)));
+            if (mr < p.M && nb < p.N) {
+              __nv_bfloat16* dst = p.rowP + q * p.row_ps + (long long)mr * p.row_ld + nb;
+              if (nb + 8 <= p.N && (p.row_ld & 7) == 0) {
+                *reinterpret_cast<uint4*>(dst) = val;
+              } else {
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&val);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                  if (nb + k < p.N) dst[k] = e[k];
+              }
+            }
+          }
+          __syncwarp();
         }
       }
       if (EPI == EPI_TC_RHO && have && mrow) atomicAdd(p.rho + m, p.rho_alpha * rsum);
@@ -585,7 +638,8 @@ static int launch_t(const CUtensorMap& a, const CUtensorMap& b, const TcParams& 
                     dim3 grid, cudaStream_t st) {
   constexpr int STAGE_BYTES = (PA + PB) * TILE_BYTES;
   constexpr int STAGES = SMEM_BUDGET / STAGE_BYTES;
-  const int smem = STAGES * STAGE_BYTES + 1024;
+  // + the accumulation warps' staging rows of EPI_TC_STORE
+  const int smem = STAGES * STAGE_BYTES + 1024 + (EPI == EPI_TC_STORE ? STG_BYTES : 0);
   auto k = tc_gemm_kernel<PA, PB, EPI>;
   // per launch (about a microsecond), so that every device the process uses
   // has the attribute set

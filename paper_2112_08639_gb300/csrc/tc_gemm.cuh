@@ -30,13 +30,15 @@ struct TcParams {
   int nprod;
   int prod_a[6], prod_b[6];
   int tri;               // 1: upper output tiles only; 2: B upper triangular
+  int one_partial;       // 1: the whole K range of a tile in one TMEM accumulator
   int splits;            // K splits (set by tc_gemm)
   int* status;
   // outputs (column-major with leading dimension ldc)
   double* C64;           // EPI_TC_ATOMIC
   float* C32;            // EPI_TC_STORE, EPI_TC_CHEB (T_{j+1})
   long long ldc;
-  float alpha;           // EPI_TC_STORE
+  float alpha;           // EPI_TC_STORE: C = alpha acc (+ beta C, read first,
+  float beta;            //   when beta != 0; C may then be updated in place)
   // EPI_TC_CHEB
   const float* Tprev;
   __nv_bfloat16* Bnext;  // pieces of T_{j+1}, row n at Bnext[n*ld_next + m]
