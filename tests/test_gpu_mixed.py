@@ -104,6 +104,30 @@ def test_orthonormalise_mixed(Ns, cond):
     assert np.max(np.abs(resid)) < 1e-5 * cond
 
 
+@pytest.mark.parametrize("Ns,cond", [(40, 1.0), (300, 1.0), (40, 3.0), (300, 10.0),
+                                     (130, 1e2)])
+def test_orthonormalise_mixed_matches_the_oracle_q(Ns, cond):
+    """The orthonormal factor of a full-rank block is unique (Q = X R^-1 with
+    R upper triangular, positive diagonal), so the mixed Cholesky QR 2 must
+    reproduce the FP64 oracle's Q of the same FP32 input elementwise, to
+    FP32 accuracy times the condition number.  Inputs from orthonormal (the
+    last pass then corrects X by one BF16 piece of R^-1 - I) to cond 1e2
+    (two pieces or the full product); Ns = 300 spans three tiles and a
+    ragged one."""
+    cell = c1_cell()
+    ctx = context_for(cell)
+    rng = np.random.default_rng(Ns + int(cond))
+    Q0 = subspace.cholqr(rng.normal(size=(cell.cfg.N, Ns)))
+    X = _f32(Q0 @ np.diag(np.logspace(0, np.log10(cond), Ns)) @ ortho_group.rvs(Ns, random_state=2)
+             if cond > 1.0 else Q0)
+    ref = subspace.cholqr(X)
+    Xg = to_gpu_block(X, torch.float32)
+    ctx.orthonormalise(Xg, prec=sq3().MIXED)
+    got = from_gpu_block(Xg)
+    assert np.max(np.abs(got.T @ got - np.eye(Ns))) < 2e-6
+    assert np.max(np.abs(got - ref)) < 2e-6 * cond * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("Ns,npl", [(64, 60), (130, 25)])
 def test_kernel_from_hs_mixed(Ns, npl):
     """The recurrence on the tensor cores (FP32 T_j, BF16-split products)
