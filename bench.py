@@ -66,7 +66,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # them to the bench's workload by points x vectors.
 MEASURED_TRAFFIC = {
     "stencil": (1181.7e6 / (373248 * 256), "ncu dram__bytes, 72^3 x 256 capture of the 108-atom cell"),
-    "nl_pass": (785.5e6 / (373248 * 256), "ncu dram__bytes, 72^3 x 256 capture of the 108-atom cell"),
+    "nl_pass": (785.2e6 / (373248 * 256), "ncu dram__bytes, 72^3 x 256 capture of the 108-atom cell"),
 }
 # SCF tolerance: sum |rho_out - rho_in| dV / Ne.  At the configured Ns the
 # Ns-th state lies inside a near-degenerate shell whose members converge
