@@ -802,6 +802,23 @@ def run_oracle_sample(cfg_name: str, passes: int):
                                   "dense": t_dense, "foe": t_foe, "scf": t_scf}
 
 
+def run_oracle_sample_one_thread(cfg_name: str, passes: int):
+    """The same oracle sample in a fresh process with every BLAS/OpenMP pool
+    at one thread (set before numpy loads); returns its seconds per solve,
+    or None if the child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    root = os.path.dirname(os.path.abspath(__file__))
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.run_oracle_sample(%r, %d)[0]))" % (root, cfg_name, passes))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=900)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -851,7 +868,10 @@ def main():
     elif rank == 0:
         v, cores, sample, parts = run_oracle_sample(args.config, passes)
         res["cpu_baseline"] = {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample, "blas_threads": cores}
+        v1 = run_oracle_sample_one_thread(args.config, passes)
+        if v1 is not None:
+            res["cpu_baseline"]["one_thread"] = {"value": round(v1, 3), "unit": "s", "threads": 1}
         print(json.dumps(res))
     if world > 1:
         import torch.distributed as dist

@@ -75,3 +75,10 @@ def test_symmetric_gemm_flops_against_the_tile_schedule(Ns):
     assert issued >= exact_upper
     pad = nt * 128
     assert issued <= 2 * N * pad * (pad + 128) / 2 + 1
+
+
+def test_one_thread_oracle_sample_runs_in_a_child_process():
+    """The 1-thread CPU figure: the same oracle sample in a fresh process
+    with the BLAS pools at one thread (32-atom cell, one pass)."""
+    v = bench.run_oracle_sample_one_thread("al32_48", 1)
+    assert v is not None and v > 0.0
