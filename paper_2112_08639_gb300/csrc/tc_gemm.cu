@@ -457,34 +457,43 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
             }
           }
           if (!mrow) continue;
+          // The FP32 epilogues (REG: cm = 0) compute in FP32: one fma
+          // rounds the exact alpha acc + beta C or 2 acc - T_{j-1} once, as
+          // the FP64 forms did (the FP64 pipe, a small fraction of the FP32
+          // rate on this part, had bound the X R^-1 products); the row-dot
+          // adds 8 FP32 products per FP64 addition.
           float tvs[8];
+          float rpart = 0.f;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int n = n0 + half * ACC_COLS + c * 8 + i;
             tvs[i] = 0.f;
             if (n >= p.N) continue;
             const long long e = (long long)m + (long long)n * p.ldc;
-            const double acc = have ? (double)sm[i] - (double)cm[i] : 0.0;
             if (EPI == EPI_TC_ATOMIC) {
+              const double acc = have ? (double)sm[i] - (double)cm[i] : 0.0;
               atomicAdd(p.C64 + e, acc);
             } else if (EPI == EPI_TC_STORE) {
-              double a = (double)p.alpha * acc;
-              if (p.beta != 0.f) a += (double)p.beta * (double)p.C32[e];
-              const float v = (float)a;
+              const float acc = have ? sm[i] : 0.f;
+              const float v = p.beta != 0.f ? fmaf(p.alpha, acc, p.beta * p.C32[e])
+                                            : p.alpha * acc;
               p.C32[e] = v;
               tvs[i] = v;
               if (p.colP) split_store(v, p.colP, (long long)n * p.col_ld + m, p.col_ps, 3);
             } else if (EPI == EPI_TC_CHEB) {
-              const float tv = (float)(2.0 * acc - (double)p.Tprev[e]);
+              const float acc = have ? sm[i] : 0.f;
+              const float tv = fmaf(2.f, acc, -p.Tprev[e]);
               tvs[i] = tv;
               p.C32[e] = tv;
               split_store(tv, p.Bnext, (long long)n * p.ld_next + m, p.next_piece_stride,
                           p.next_pieces);
               if (m == n) atomicAdd(p.trace, (double)tv);
             } else {  // EPI_TC_RHO
-              rsum += (double)p.X[(long long)m + (long long)n * p.ldx] * acc;
+              const float acc = have ? sm[i] : 0.f;
+              rpart = fmaf(p.X[(long long)m + (long long)n * p.ldx], acc, rpart);
             }
           }
+          if (EPI == EPI_TC_RHO) rsum += (double)rpart;
           if (EPI == EPI_TC_CHEB && p.tri == 1 && n0 != m0) {
             // symmetric T_{j+1} from its upper tiles: the mirror of an
             // off-diagonal tile, row m of it holding this lane's 8 columns
