@@ -11,6 +11,9 @@ Verlet halves run in the library.
 """
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -131,37 +134,117 @@ class Cell:
         return np.ascontiguousarray(f)
 
 
+def save_checkpoint(path: str, cell: Cell, step: int, R, V, F, ke0: float, traj: dict) -> None:
+    """Everything a QMD run needs to continue after `step`: the nuclei (R, V
+    and the forces F at R), the target kinetic energy, the trajectory so
+    far, and the SCF state a step hands to the next (the block X, the
+    density kernel D, the converged density with its positions, the last
+    spectral bounds).  Written to path + '.tmp' and renamed, so an existing
+    checkpoint is replaced only by a complete one."""
+    state = {
+        "version": 1, "config": cell.cfg.name, "prec": int(cell.prec), "step": int(step),
+        "R": np.array(R, dtype=np.float64), "V": np.array(V, dtype=np.float64),
+        "F": np.array(F, dtype=np.float64), "ke0": float(ke0),
+        "traj": {k: list(v) for k, v in traj.items()},
+        "X": cell.X.detach().cpu(), "D": cell.D.detach().cpu(),
+        "rho_prev": None if cell.rho_prev is None else cell.rho_prev.detach().cpu(),
+        "pos_prev": None if cell.pos_prev is None else np.array(cell.pos_prev),
+        "bounds": None if cell.bounds is None else tuple(float(b) for b in cell.bounds),
+    }
+    tmp = path + ".tmp"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, cell: Cell) -> dict:
+    """Restores the SCF state of `cell` from a checkpoint written by
+    save_checkpoint for the same configuration and precision; returns the
+    checkpoint (its step, R, V, F, ke0 and trajectory)."""
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    if state.get("version") != 1 or state["config"] != cell.cfg.name or \
+            state["prec"] != int(cell.prec) or tuple(state["X"].shape) != tuple(cell.X.shape):
+        raise ValueError(f"checkpoint {path} is not for this cell ({cell.cfg.name}, prec "
+                         f"{int(cell.prec)}, X {tuple(cell.X.shape)})")
+    cell.X.copy_(state["X"].to(cell.X.device, cell.X.dtype))
+    cell.D.copy_(state["D"].to(cell.D.device))
+    cell.rho_prev = None if state["rho_prev"] is None else state["rho_prev"].to(cell.rho.device)
+    cell.pos_prev = state["pos_prev"]
+    cell.bounds = state["bounds"]
+    return state
+
+
+def write_metrics(f, step: int, res: dict, hist: list, E_kin: float) -> None:
+    """One JSON line per SCF iteration of the step (its history: change of
+    rho, mu, energies, expansion degree, milliseconds, spectral centre and
+    half-width) and one for the step itself."""
+    for i, h in enumerate(hist):
+        f.write(json.dumps({"kind": "scf", "step": step, "iteration": i + 1,
+                            **{k: float(v) for k, v in h.items()}}) + "\n")
+    f.write(json.dumps({"kind": "step", "step": step, "iterations": int(res["iterations"]),
+                        "converged": int(res["converged"]), "F": float(res["F"]),
+                        "mu": float(res["mu"]), "err": float(res["err"]),
+                        "E_kin": float(E_kin)}) + "\n")
+    f.flush()
+
+
 def run(cell: Cell, R0, V0, dt_fs: float, nsteps: int, start: str = "previous",
-        learned=None, isokinetic: bool = True, tol: float = 1e-6, on_step=None) -> dict:
+        learned=None, isokinetic: bool = True, tol: float = 1e-6, on_step=None,
+        checkpoint: str | None = None, checkpoint_every: int = 1, resume: str | None = None,
+        metrics: str | None = None) -> dict:
     """nsteps of velocity Verlet from (R0, V0) with dt_fs femtoseconds per
     step; returns per-step positions, SCF iterations, F and kinetic energy.
     on_step(step, cell, result) is called after each converged solve (for
-    example to collect training densities)."""
-    masses = np.full(len(R0), MASS_AL)
+    example to collect training densities).  checkpoint: a file rewritten
+    after every checkpoint_every-th step (and the last); resume: a
+    checkpoint to continue from instead of (R0, V0) (the trajectory then
+    holds the steps before it as well); metrics: a JSON-lines file that gets
+    the SCF history and a summary of every step (appended)."""
     dt = dt_fs * FS_IN_AU
-    R = np.array(R0, dtype=np.float64)
-    V = np.array(V0, dtype=np.float64)
-    ke0 = 0.5 * float(np.sum(masses[:, None] * V * V))
-    cell.set_positions(R)
-    cell.start_density(start, learned)
-    res, _ = cell.solve(tol)
-    if on_step:
-        on_step(0, cell, res)
-    F = cell.forces()
-    traj = {"R": [R.copy()], "iterations": [res["iterations"]], "F": [res["F"]],
-            "E_kin": [ke0], "converged": [res["converged"]]}
-    for step in range(1, nsteps + 1):
-        sq3.verlet(masses, dt, R, V, F, 0)
-        cell.set_positions(R)
-        cell.start_density(start, learned)
-        res, _ = cell.solve(tol)
-        if on_step:
-            on_step(step, cell, res)
-        F = cell.forces()
-        sq3.verlet(masses, dt, R, V, F, 1, ke0 if isokinetic else 0.0)
-        traj["R"].append(R.copy())
-        traj["iterations"].append(res["iterations"])
-        traj["F"].append(res["F"])
-        traj["E_kin"].append(0.5 * float(np.sum(masses[:, None] * V * V)))
-        traj["converged"].append(res["converged"])
+    mf = open(metrics, "a") if metrics else None
+    try:
+        if resume:
+            st = load_checkpoint(resume, cell)
+            R, V, F, ke0, first = st["R"], st["V"], st["F"], st["ke0"], st["step"] + 1
+            traj = st["traj"]
+            masses = np.full(len(R), MASS_AL)
+        else:
+            masses = np.full(len(R0), MASS_AL)
+            R = np.array(R0, dtype=np.float64)
+            V = np.array(V0, dtype=np.float64)
+            ke0 = 0.5 * float(np.sum(masses[:, None] * V * V))
+            cell.set_positions(R)
+            cell.start_density(start, learned)
+            res, hist = cell.solve(tol)
+            if on_step:
+                on_step(0, cell, res)
+            F = cell.forces()
+            traj = {"R": [R.copy()], "iterations": [res["iterations"]], "F": [res["F"]],
+                    "E_kin": [ke0], "converged": [res["converged"]]}
+            if mf:
+                write_metrics(mf, 0, res, hist, ke0)
+            if checkpoint:
+                save_checkpoint(checkpoint, cell, 0, R, V, F, ke0, traj)
+            first = 1
+        for step in range(first, nsteps + 1):
+            sq3.verlet(masses, dt, R, V, F, 0)
+            cell.set_positions(R)
+            cell.start_density(start, learned)
+            res, hist = cell.solve(tol)
+            if on_step:
+                on_step(step, cell, res)
+            F = cell.forces()
+            sq3.verlet(masses, dt, R, V, F, 1, ke0 if isokinetic else 0.0)
+            ek = 0.5 * float(np.sum(masses[:, None] * V * V))
+            traj["R"].append(R.copy())
+            traj["iterations"].append(res["iterations"])
+            traj["F"].append(res["F"])
+            traj["E_kin"].append(ek)
+            traj["converged"].append(res["converged"])
+            if mf:
+                write_metrics(mf, step, res, hist, ek)
+            if checkpoint and (step % max(checkpoint_every, 1) == 0 or step == nsteps):
+                save_checkpoint(checkpoint, cell, step, R, V, F, ke0, traj)
+    finally:
+        if mf:
+            mf.close()
     return {k: np.asarray(v) for k, v in traj.items()}

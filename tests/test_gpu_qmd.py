@@ -12,6 +12,8 @@ the previous step's density, and the superposition alone: the learned start
 is the closest to the converged density and needs the fewest SCF
 iterations (the gain the model is built for), and the isokinetic
 thermostat holds the kinetic energy."""
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -108,3 +110,27 @@ def test_qmd_steps_of_the_108_atom_cell_converge_in_few_iterations():
     print("SCF iterations per step:", tr["iterations"].tolist())
     assert np.all(tr["iterations"][1:] <= 6)
     assert np.all(np.abs(tr["E_kin"] - tr["E_kin"][0]) < 1e-12 * tr["E_kin"][0])
+
+
+def test_checkpoint_resume_continues_the_same_trajectory(tmp_path):
+    """A run checkpointed after step 1 and resumed in a fresh cell reaches
+    the same positions and free energy at step 3 as the uninterrupted run
+    (to the SCF tolerance: the mixed path's split-K sums add in no fixed
+    order), and the metrics file holds every SCF iteration and step."""
+    sq3()
+    from paper_2112_08639_gb300 import qmd
+    cfg = inputs.C2
+    R0 = inputs.fcc_positions(cfg.ncell, disp_sigma=0.1, seed=7)
+    V0 = qmd.maxwell_boltzmann(cfg.natoms, cfg.sigma, seed=7)
+    mpath = tmp_path / "m.jsonl"
+    full = qmd.run(qmd.Cell(cfg), R0, V0, 0.5, 3, tol=TOL, metrics=str(mpath))
+    ck = str(tmp_path / "qmd.ckpt")
+    qmd.run(qmd.Cell(cfg), R0, V0, 0.5, 1, tol=TOL, checkpoint=ck)
+    part = qmd.run(qmd.Cell(cfg), None, None, 0.5, 3, tol=TOL, resume=ck)
+    assert len(part["R"]) == 4 and np.all(part["converged"] == 1)
+    assert np.max(np.abs(part["R"][-1] - full["R"][-1])) < 1e-6
+    assert abs(part["F"][-1] - full["F"][-1]) < 1e-5 * cfg.natoms
+    lines = [json.loads(line) for line in open(mpath)]
+    steps = [l for l in lines if l["kind"] == "step"]
+    assert [l["step"] for l in steps] == [0, 1, 2, 3]
+    assert sum(l["kind"] == "scf" for l in lines) == int(full["iterations"].sum())
