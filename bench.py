@@ -531,34 +531,15 @@ def run_iteration(args, rank, world):
 
 
 def batch_cells(ncells: int = 64, seed: int = 0):
-    """The batched workload: uneven Al-like cells of 4 to 32 atoms (FCC
-    supercells 1x1x1, 2x1x1, 2x2x1, 2x2x2 on 0.324-bohr grids of 24 to 48
-    points per side), seeded thermal displacements (0.3 bohr), kT drawn
-    from 5 to 20 eV, Ns = 20 x atoms (80 to 640), filter degree 20."""
+    """The batched workload (C4 of the input module)."""
     from paper_2112_08639_gb300 import inputs
-    rng = np.random.default_rng(seed)
-    shapes = [(1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2)]
-    cells = []
-    for c in range(ncells):
-        sx, sy, sz = shapes[rng.integers(0, 4)]
-        L = np.array([sx, sy, sz], dtype=float) * inputs.A0_FCC
-        n = tuple(int(24 * s) for s in (sx, sy, sz))
-        basis = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
-        pos = np.array([(np.array([i, j, k]) + b) * inputs.A0_FCC
-                        for i in range(sx) for j in range(sy) for k in range(sz) for b in basis])
-        pos = np.mod(pos + rng.normal(0.0, 0.3, size=pos.shape), L)
-        kT = float(rng.uniform(5.0, 20.0))
-        cells.append({"n": n, "L": tuple(L), "pos": pos, "natoms": len(pos),
-                      "Ns": 20 * len(pos), "m": 20, "kT": kT, "seed": seed * 1000 + c})
-    return cells
+    return inputs.batch_cells(ncells, seed)
 
 
 def small_cells(ncells: int = 64, seed: int = 1):
-    """Many small cells: 4-atom FCC cells on 24^3 grids, Ns = 80, degree 20
-    (each cell's filter alone fills a small part of the GPU)."""
-    cells = batch_cells(4 * ncells, seed=seed)
-    small = [c for c in cells if c["natoms"] == 4][:ncells]
-    return small
+    """Many 4-atom cells (the input module's small_cells)."""
+    from paper_2112_08639_gb300 import inputs
+    return inputs.small_cells(ncells, seed)
 
 
 def measure_batch(cells, dev, steps, warmup, clock_sampler=None):

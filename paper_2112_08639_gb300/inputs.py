@@ -92,6 +92,54 @@ C2 = CellConfig("al32_48", ncell=2, n=48, Ns=640, m=25, npl=100, projectors=True
 C3 = CellConfig("al108_72", ncell=3, n=72, Ns=2200, m=30, npl=120, projectors=True)
 CONFIGS = {c.name: c for c in (C1, C2, C3)}
 
+AL_MASS_AMU = 26.9815385
+
+
+@dataclasses.dataclass(frozen=True)
+class QMDConfig:
+    """A QMD run of one cell (Sec. 5: Al at 116,045 K, i.e. kT = 10 eV, in
+    the isokinetic ensemble): velocity Verlet with dt_fs, nsteps steps, the
+    learned start trained on the first train_steps steps' densities."""
+    name: str
+    cell: CellConfig
+    dt_fs: float
+    nsteps: int
+    train_steps: int
+    mass_amu: float = AL_MASS_AMU
+    seed: int = 0
+
+
+# C5: the 32-atom cell of C2, 0.5 fs steps, 300 steps, trained on 0 .. 99
+C5 = QMDConfig("al32_48_qmd", cell=C2, dt_fs=0.5, nsteps=300, train_steps=100)
+
+
+def batch_cells(ncells: int = 64, seed: int = 0):
+    """C4, the batched workload: uneven Al-like cells of 4 to 32 atoms (FCC
+    supercells 1x1x1, 2x1x1, 2x2x1, 2x2x2 on 0.324-bohr grids of 24 to 48
+    points per side), seeded thermal displacements (0.3 bohr), kT drawn
+    from 5 to 20 eV, Ns = 20 x atoms (80 to 640), filter degree 20."""
+    rng = np.random.default_rng(seed)
+    shapes = [(1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2)]
+    basis = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    cells = []
+    for c in range(ncells):
+        sx, sy, sz = shapes[rng.integers(0, 4)]
+        L = np.array([sx, sy, sz], dtype=float) * A0_FCC
+        n = tuple(int(24 * s) for s in (sx, sy, sz))
+        pos = np.array([(np.array([i, j, k]) + b) * A0_FCC
+                        for i in range(sx) for j in range(sy) for k in range(sz) for b in basis])
+        pos = np.mod(pos + rng.normal(0.0, 0.3, size=pos.shape), L)
+        kT = float(rng.uniform(5.0, 20.0))
+        cells.append({"n": n, "L": tuple(L), "pos": pos, "natoms": len(pos),
+                      "Ns": 20 * len(pos), "m": 20, "kT": kT, "seed": seed * 1000 + c})
+    return cells
+
+
+def small_cells(ncells: int = 64, seed: int = 1):
+    """Many small cells: 4-atom FCC cells on 24^3 grids, Ns = 80, degree 20
+    (each cell's filter alone fills a small part of the GPU)."""
+    return [c for c in batch_cells(4 * ncells, seed=seed) if c["natoms"] == 4][:ncells]
+
 
 def fcc_positions(ncell: int, a0: float = A0_FCC, disp_sigma: float = 0.05,
                   seed: int = 0) -> np.ndarray:

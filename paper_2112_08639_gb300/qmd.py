@@ -21,7 +21,7 @@ from . import inputs, sq3
 
 AMU_IN_ME = 1822.888486209             # atomic mass unit / electron mass
 FS_IN_AU = 1.0 / 0.02418884326585747    # femtoseconds in hbar / Ha
-MASS_AL = 26.9815385 * AMU_IN_ME
+MASS_AL = inputs.AL_MASS_AMU * AMU_IN_ME
 # width (bohr) of the atomic-superposition start: the best single width on
 # self-consistent densities of 32-atom cells at kT = 10 eV (L1 error per
 # electron 0.10 at 2.3 bohr against 0.25 at 1.9 and 0.62 at 1.5)
