@@ -435,9 +435,27 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
       const int m = m0 + q4 * 32 + lane;
       const bool mrow = m < p.M;
       double rsum = 0.0;
+      // EPI_TC_STORE with beta reads C back: its values are loaded a chunk
+      // of 8 columns ahead as independent loads (one at a time between the
+      // stores, each waited for a full memory latency; the one-piece
+      // correction product of the last Cholesky QR pass took twice as long)
+      const bool rdc = EPI == EPI_TC_STORE && p.beta != 0.f;
+      float cnext[8];
+      auto load_old = [&](int c, float (&o)[8]) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int n = n0 + half * ACC_COLS + c * 8 + i;
+          o[i] = (mrow && n < p.N) ? p.C32[(long long)m + (long long)n * p.ldc] : 0.f;
+        }
+      };
+      if (rdc) load_old(0, cnext);
       if (have || EPI == EPI_TC_STORE || EPI == EPI_TC_CHEB) {
 #pragma unroll
         for (int c = 0; c < ACC_COLS / 8; ++c) {
+          float cold[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) cold[i] = rdc ? cnext[i] : 0.f;
+          if (rdc && c + 1 < ACC_COLS / 8) load_old(c + 1, cnext);
           float sm[8], cm[8];
           if (REG) {
 #pragma unroll
@@ -475,7 +493,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
               atomicAdd(p.C64 + e, acc);
             } else if (EPI == EPI_TC_STORE) {
               const float acc = have ? sm[i] : 0.f;
-              const float v = p.beta != 0.f ? fmaf(p.alpha, acc, p.beta * p.C32[e])
+              const float v = p.beta != 0.f ? fmaf(p.alpha, acc, p.beta * cold[i])
                                             : p.alpha * acc;
               p.C32[e] = v;
               tvs[i] = v;
